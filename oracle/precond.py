@@ -1,0 +1,87 @@
+"""Preconditioners applied from the right (oracle).
+
+App. D.3 lists the preconditioners; this build uses three of them:
+  * none:   M = I
+  * jacobi: M = diag(A) ("the inverse of the diagonal elements")
+  * ilu0:   M = L U, the incomplete LU factorisation with no fill, i.e. L
+            and U keep exactly the sparsity pattern of A (App. D.3 item 7).
+
+Right preconditioning (a reading; the paper does not state the side): the
+Krylov method solves (A M^-1) x_hat = b and x = M^-1 x_hat, so its residual
+is the unpreconditioned residual b - A x.
+
+ILU(0) follows the textbook row-by-row (IKJ) elimination restricted to the
+pattern of A.  Pins: for a tridiagonal matrix ILU(0) is the exact LU (no
+fill is ever produced), and for any pattern the product L U agrees with A
+at every position of A's pattern.
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+def jacobi_inv_diag(A):
+    """1 / diag(A)."""
+    d = A.diagonal()
+    if np.any(d == 0):
+        raise ZeroDivisionError("zero diagonal entry")
+    return 1.0 / d
+
+
+def ilu0(A):
+    """ILU(0) of a CSR matrix: returns (L unit-lower CSR, U upper CSR).
+
+    For each row i in order, for each k < i in the pattern of row i:
+    a_ik <- a_ik / a_kk, then a_ij <- a_ij - a_ik a_kj for every j > k that
+    is in the pattern of row i.  Entries outside the pattern are never
+    created.
+    """
+    A = sp.csr_matrix(A, dtype=np.float64, copy=True)
+    A.sort_indices()
+    n = A.shape[0]
+    indptr, indices, data = A.indptr, A.indices, A.data
+    diag_pos = np.full(n, -1)
+    for i in range(n):
+        for q in range(indptr[i], indptr[i + 1]):
+            if indices[q] == i:
+                diag_pos[i] = q
+    if np.any(diag_pos < 0):
+        raise ValueError("ILU(0) needs a structurally nonzero diagonal")
+    for i in range(n):
+        row = {indices[q]: q for q in range(indptr[i], indptr[i + 1])}
+        for q in range(indptr[i], indptr[i + 1]):
+            kcol = indices[q]
+            if kcol >= i:
+                break
+            data[q] = data[q] / data[diag_pos[kcol]]
+            aik = data[q]
+            for r in range(indptr[kcol], indptr[kcol + 1]):
+                j = indices[r]
+                if j > kcol and j in row:
+                    data[row[j]] -= aik * data[r]
+    L = sp.tril(A, k=-1, format="csr") + sp.identity(n, format="csr")
+    U = sp.triu(A, k=0, format="csr")
+    return L.tocsr(), U.tocsr()
+
+
+class RightPreconditioner:
+    """M^-1 as an operator, for M in {none, jacobi, ilu0}."""
+
+    def __init__(self, A, kind):
+        self.kind = kind
+        if kind == "none":
+            pass
+        elif kind == "jacobi":
+            self.dinv = jacobi_inv_diag(A)
+        elif kind == "ilu0":
+            self.L, self.U = ilu0(A)
+        else:
+            raise ValueError(kind)
+
+    def apply(self, v):
+        if self.kind == "none":
+            return np.array(v, dtype=np.float64, copy=True)
+        if self.kind == "jacobi":
+            return self.dinv * v
+        y = spla.spsolve_triangular(self.L, v, lower=True, unit_diagonal=True)
+        return spla.spsolve_triangular(self.U, y, lower=False)

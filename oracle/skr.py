@@ -1,0 +1,102 @@
+"""A sorted sequence of systems solved with recycling (oracle, float64).
+
+Fig. 2 steps c-e: sort the systems (Algorithm 1), then solve them in that
+order, carrying U_k from each solve to the next (Algorithm 2, last line)
+and refreshing it against the new matrix (App. B.1).  App. E.2.2 cuts the
+sorted list into independent chains; `solve_sequence` does the same when
+nchains > 1 (contiguous, near-equal pieces).
+
+Each system is solved by residual refinement around GCRO-DR:
+  x = 0; repeat: r = b - A x (float64); stop if ||r|| <= tol ||b||;
+  solve A M^-1 d = r by GCRO-DR to the inner target; x += M^-1 d.
+For the "fp64" form the inner target is tol ||b|| (one pass normally
+suffices; the loop only confirms it on the true residual).  For the
+"mixed" form the inner target is max(inner_tol ||r||, tol ||b||), the
+structure the GPU path runs with single-precision inner solves; the oracle
+runs that same structure in float64.
+"""
+import numpy as np
+
+from . import assembly
+from .precond import RightPreconditioner
+from .krylov import RecycleState, refresh, gcrodr_solve
+
+
+def assemble(system):
+    """Build (A, b) for one system description (a dict from the workload module)."""
+    kind = system["kind"]
+    if kind == "darcy2d":
+        return assembly.darcy2d(system["loga"], rhs=system.get("rhs"))
+    if kind == "darcy3d":
+        return assembly.darcy3d(system["loga"], rhs=system.get("rhs"))
+    if kind == "convdiff2d":
+        return assembly.convdiff2d(system["nu"], system["beta"], system["nside"],
+                                   rhs=system.get("rhs"))
+    if kind == "matrix":
+        return system["A"], system["b"]
+    raise ValueError(kind)
+
+
+def solve_system(A, b, precond, m, k, tol, state, precision="fp64", inner_tol=1e-5,
+                 max_refine=10, max_steps=10**4):
+    """Solve one system, updating the carried recycle state in place.
+
+    Returns (x, info) with info = dict(steps, cycles, matvecs, refinements,
+    relres, converged).  `steps` counts Arnoldi steps (one operator
+    application each); `matvecs` also counts the k products of the refresh.
+    """
+    M = RightPreconditioner(A, precond)
+
+    def op(v):
+        return A @ M.apply(v)
+
+    stats = dict(steps=0, cycles=0, matvecs=0, refinements=0)
+    stats["matvecs"] += refresh(op, state)
+    bnorm = np.linalg.norm(b)
+    x = np.zeros_like(b)
+    if bnorm == 0.0:
+        stats.update(relres=0.0, converged=True)
+        return x, stats
+    for _ in range(max_refine):
+        r = b - A @ x
+        rn = np.linalg.norm(r)
+        if rn <= tol * bnorm or stats["steps"] >= max_steps:
+            break
+        if precision == "fp64":
+            tol_abs = tol * bnorm
+        else:
+            tol_abs = max(inner_tol * rn, tol * bnorm)
+        d, _ = gcrodr_solve(op, r, m, k, tol_abs, state, max_steps, stats)
+        x = x + M.apply(d)
+        stats["refinements"] += 1
+    relres = np.linalg.norm(b - A @ x) / bnorm
+    stats.update(relres=relres, converged=bool(relres <= tol))
+    return x, stats
+
+
+def split_chains(order, nchains):
+    """Cut an order into nchains contiguous, near-equal chains (App. E.2.2)."""
+    order = list(order)
+    N = len(order)
+    nchains = max(1, min(nchains, N)) if N else 1
+    bounds = [(c * N) // nchains for c in range(nchains + 1)]
+    return [order[bounds[c]:bounds[c + 1]] for c in range(nchains)]
+
+
+def solve_sequence(systems, order, precond, m, k, tol, precision="fp64", nchains=1,
+                   inner_tol=1e-5, max_refine=10, max_steps=10**4):
+    """Solve systems[order[0]], systems[order[1]], ... carrying U_k along each chain.
+
+    Returns (xs, infos), lists indexed like `systems`.
+    """
+    xs = [None] * len(systems)
+    infos = [None] * len(systems)
+    for chain in split_chains(order, nchains):
+        state = RecycleState()
+        for idx in chain:
+            A, b = assemble(systems[idx])
+            x, info = solve_system(A, b, precond, m, k, tol, state, precision, inner_tol,
+                                   max_refine, max_steps)
+            xs[idx] = x
+            infos[idx] = info
+    return xs, infos

@@ -1,0 +1,251 @@
+"""Pins for the oracle's preconditioners, Arnoldi, GMRES and GCRO-DR."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import assembly, krylov, precond, skr
+from workloads import darcy2d_sequence
+
+
+def _darcy(N, seed=0, ell=0.2):
+    loga = darcy2d_sequence(N, 1, ell, seed=seed)[0]
+    return assembly.darcy2d(loga)
+
+
+# ---------------------------------------------------------------- preconditioners
+
+def test_ilu0_of_tridiagonal_is_exact_lu():
+    n = 12
+    rng = np.random.default_rng(0)
+    main = 4.0 + rng.uniform(size=n)
+    A = sp.diags([rng.uniform(-1, 0, n - 1), main, rng.uniform(-1, 0, n - 1)], [-1, 0, 1], format="csr")
+    L, U = precond.ilu0(A)
+    np.testing.assert_allclose((L @ U).toarray(), A.toarray(), rtol=1e-14, atol=1e-14)
+
+
+def test_ilu0_matches_a_on_its_pattern_and_has_no_fill():
+    A, _ = assembly.convdiff2d(0.05, (20.0, 7.0), 6)
+    L, U = precond.ilu0(A)
+    LU = (L @ U).toarray()
+    Ad = A.toarray()
+    mask = Ad != 0
+    np.testing.assert_allclose(LU[mask], Ad[mask], rtol=1e-13, atol=1e-12)
+    assert set(zip(*L.nonzero())) <= set(zip(*np.nonzero(np.tril(Ad, -1) + np.eye(36))))
+    assert set(zip(*U.nonzero())) <= set(zip(*np.nonzero(np.triu(Ad))))
+    # and ILU(0) is not the exact LU for the 5-point pattern (fill is dropped)
+    assert np.abs(LU - Ad).max() > 1e-6
+
+
+def test_jacobi_right_preconditioner():
+    A, _ = _darcy(5)
+    M = precond.RightPreconditioner(A, "jacobi")
+    v = np.arange(25.0)
+    np.testing.assert_allclose(M.apply(v), v / A.diagonal(), rtol=1e-15)
+
+
+# ---------------------------------------------------------------- Arnoldi (Eq. 2-4)
+
+def test_arnoldi_relation_and_orthonormality():
+    A, b = _darcy(8)
+    op = lambda v: A @ v
+    ar = krylov.arnoldi(op, b, 20, None, 0.0)
+    V, H = ar["V"], ar["Hbar"]
+    j = ar["j"]
+    assert j == 20
+    AV = np.stack([op(V[:, i]) for i in range(j)], axis=1)
+    np.testing.assert_allclose(AV, V @ H, atol=1e-10 * np.abs(AV).max())
+    np.testing.assert_allclose(V.T @ V, np.eye(j + 1), atol=1e-12)
+
+
+def test_projected_arnoldi_relation_eq4():
+    A, b = _darcy(8)
+    op = lambda v: A @ v
+    rng = np.random.default_rng(1)
+    C, _ = krylov.qr_pos(rng.standard_normal((64, 5)))
+    r = b - C @ (C.T @ b)
+    ar = krylov.arnoldi(op, r, 15, C, 0.0)
+    V, H, B = ar["V"], ar["Hbar"], ar["B"]
+    AV = np.stack([op(V[:, i]) for i in range(15)], axis=1)
+    lhs = AV - C @ (C.T @ AV)
+    np.testing.assert_allclose(lhs, V @ H, atol=1e-10 * np.abs(AV).max())
+    np.testing.assert_allclose(B, C.T @ AV, atol=1e-10 * np.abs(AV).max())
+    assert np.abs(C.T @ V).max() < 1e-12
+
+
+# ---------------------------------------------------------------- GMRES / GCRO-DR solves
+
+@pytest.mark.parametrize("k", [0, 4])
+@pytest.mark.parametrize("pc", ["none", "jacobi", "ilu0"])
+def test_solution_matches_dense_lu(k, pc):
+    A, b = _darcy(10, seed=2)
+    state = krylov.RecycleState()
+    x, info = skr.solve_system(A, b, pc, 12, k, 1e-10, state)
+    xd = np.linalg.solve(A.toarray(), b)
+    assert info["converged"] and info["relres"] <= 1e-10
+    assert np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)
+
+
+def test_k0_is_restarted_gmres_library():
+    # GCRO-DR with k = 0 is GMRES(m) (Sec. 4.2); compare with SciPy's GMRES(m)
+    A, b = _darcy(12, seed=4)
+    m, tol = 10, 1e-9
+    state = krylov.RecycleState()
+    stats = {}
+    d, r = krylov.gcrodr_solve(lambda v: A @ v, b, m, 0, tol * np.linalg.norm(b), state, 5000, stats)
+    count = []
+    xs, _ = spla.gmres(A, b, rtol=tol, atol=0.0, restart=m, maxiter=1000,
+                       callback=lambda pr: count.append(pr), callback_type="pr_norm")
+    assert abs(stats["steps"] - len(count)) <= 2, (stats["steps"], len(count))
+    np.testing.assert_allclose(d, xs, rtol=0, atol=1e-6 * np.linalg.norm(xs))
+
+
+def test_gmres_cycle_residuals_monotone():
+    A, b = _darcy(12, seed=5)
+    for k in (0, 5):
+        stats = {}
+        krylov.gcrodr_solve(lambda v: A @ v, b, 10, k, 1e-9 * np.linalg.norm(b),
+                            krylov.RecycleState(), 5000, stats)
+        h = np.array(stats["history"])
+        assert np.all(np.diff(h) <= 1e-12 * h[:-1]), h
+
+
+def test_recycle_invariants_after_solve():
+    A, b = _darcy(12, seed=6)
+    op = lambda v: A @ v
+    state = krylov.RecycleState()
+    krylov.gcrodr_solve(op, b, 20, 6, 1e-10 * np.linalg.norm(b), state, 5000, {})
+    U, C = state.U, state.C
+    assert U.shape[1] in (5, 6)
+    np.testing.assert_allclose(C.T @ C, np.eye(C.shape[1]), atol=1e-12)
+    AU = np.stack([op(U[:, i]) for i in range(U.shape[1])], axis=1)
+    assert np.linalg.norm(AU - C) <= 1e-10 * np.linalg.norm(C)
+
+
+def test_refresh_gives_orthonormal_c_and_au_equals_c():
+    A1, b1 = _darcy(12, seed=7)
+    A2, _ = _darcy(12, seed=8)
+    state = krylov.RecycleState()
+    krylov.gcrodr_solve(lambda v: A1 @ v, b1, 20, 6, 1e-9 * np.linalg.norm(b1), state, 5000, {})
+    U_old = state.U.copy()
+    krylov.refresh(lambda v: A2 @ v, state)
+    AU = A2 @ state.U
+    np.testing.assert_allclose(AU, state.C, atol=1e-10 * np.abs(AU).max())
+    np.testing.assert_allclose(state.C.T @ state.C, np.eye(state.k), atol=1e-12)
+    # span(U) unchanged by the refresh
+    Qo, _ = np.linalg.qr(U_old)
+    Qn, _ = np.linalg.qr(state.U)
+    s = np.linalg.svd(Qo.T @ Qn, compute_uv=False)
+    assert np.all(s > 1 - 1e-10)
+
+
+def test_identical_consecutive_systems_converge_much_faster():
+    # C spans an approximate invariant subspace of the same matrix: the
+    # delta = gamma = 0 case of the convergence bound (Sec. 5.1)
+    loga = darcy2d_sequence(16, 1, 0.2, seed=11)[0]
+    systems = [dict(kind="darcy2d", loga=loga)] * 3
+    xs, infos = skr.solve_sequence(systems, [0, 1, 2], "none", 20, 8, 1e-8)
+    _, plain = skr.solve_sequence(systems, [0, 1, 2], "none", 20, 0, 1e-8)
+    steps = [i["steps"] for i in infos]
+    assert steps[1] < 0.75 * steps[0], steps
+    assert steps[1] < 0.5 * plain[1]["steps"], (steps, plain[1]["steps"])
+    for i in infos:
+        assert i["converged"]
+
+
+def test_recycling_beats_gmres_on_a_sorted_sequence():
+    L = darcy2d_sequence(16, 6, 0.2, seed=12)
+    systems = [dict(kind="darcy2d", loga=l) for l in L]
+    from oracle import sort
+    order = sort.greedy_sort(L.reshape(6, -1))
+    _, g = skr.solve_sequence(systems, order, "none", 20, 0, 1e-8)
+    _, s = skr.solve_sequence(systems, order, "none", 20, 8, 1e-8)
+    assert sum(i["steps"] for i in s) < 0.7 * sum(i["steps"] for i in g)
+
+
+# ---------------------------------------------------------------- harmonic Ritz
+
+def test_harmonic_ritz_full_space_gives_exact_eigenvalues():
+    # with m = n the Krylov space is the whole space, h_{m+1,m} = 0 and the
+    # harmonic Ritz values are the eigenvalues (closed form for a = 1; a
+    # 3 x 5 grid has distinct eigenvalues, so the Krylov space is complete)
+    nx, ny = 3, 5
+    A, _ = assembly.darcy2d(np.zeros((nx + 2, ny + 2)))
+    n = nx * ny
+    rng = np.random.default_rng(2)
+    ar = krylov.arnoldi(lambda v: A @ v, rng.standard_normal(n), n, None, 0.0)
+    H = ar["Hbar"]
+    assert H.shape[1] == n
+    _, theta = krylov.harmonic_ritz_first(H, 3)
+    hx, hy = 1.0 / (nx + 1), 1.0 / (ny + 1)
+    lx = 4.0 / hx**2 * np.sin(np.arange(1, nx + 1) * np.pi * hx / 2) ** 2
+    ly = 4.0 / hy**2 * np.sin(np.arange(1, ny + 1) * np.pi * hy / 2) ** 2
+    closed = np.sort((lx[:, None] + ly[None, :]).ravel())
+    np.testing.assert_allclose(np.sort(theta.real), closed, rtol=1e-8)
+    assert np.abs(theta.imag).max() < 1e-8 * closed.max()
+
+
+def test_first_cycle_pairs_satisfy_harmonic_petrov_galerkin():
+    A, b = _darcy(10, seed=3)
+    op = lambda v: A @ v
+    ar = krylov.arnoldi(op, b, 15, None, 0.0)
+    V, H = ar["V"], ar["Hbar"]
+    m = H.shape[1]
+    Hm = H[:m, :m]
+    em = np.zeros(m); em[-1] = 1
+    T = Hm + H[m, m - 1] ** 2 * np.outer(np.linalg.solve(Hm.T, em), em)
+    theta, Z = np.linalg.eig(T)
+    AV = np.stack([op(V[:, i]) for i in range(m)], axis=1)
+    for i in range(m):
+        y = V[:, :m] @ Z[:, i]
+        res = AV @ Z[:, i] - theta[i] * y
+        assert np.abs(AV.T @ res).max() <= 1e-8 * np.abs(theta[i]) * np.linalg.norm(AV) * np.linalg.norm(y)
+
+
+def test_general_cycle_pairs_satisfy_harmonic_petrov_galerkin():
+    A, b = _darcy(10, seed=4)
+    op = lambda v: A @ v
+    state = krylov.RecycleState()
+    krylov.gcrodr_solve(op, b, 15, 5, 1e-3 * np.linalg.norm(b), state, 15, {})
+    U, C = state.U, state.C
+    kc = U.shape[1]
+    r = b - C @ (C.T @ b)
+    ar = krylov.arnoldi(op, r, 15 - kc, C, 0.0)
+    j = ar["j"]
+    Dk = 1.0 / np.linalg.norm(U, axis=0)
+    Vhat = np.concatenate([U * Dk, ar["V"][:, :j]], axis=1)
+    What = np.concatenate([C, ar["V"]], axis=1)
+    G = np.zeros((kc + j + 1, kc + j))
+    G[:kc, :kc] = np.diag(Dk); G[:kc, kc:] = ar["B"]; G[kc:, kc:] = ar["Hbar"]
+    AVhat = np.stack([op(Vhat[:, i]) for i in range(Vhat.shape[1])], axis=1)
+    np.testing.assert_allclose(AVhat, What @ G, atol=1e-9 * np.abs(AVhat).max())
+    import scipy.linalg as sla
+    theta, Z = sla.eig(G.T @ G, G.T @ (What.T @ Vhat))
+    for i in range(len(theta)):
+        if not np.isfinite(theta[i]):
+            continue
+        y = Vhat @ Z[:, i]
+        res = AVhat @ Z[:, i] - theta[i] * y
+        assert np.abs(AVhat.T @ res).max() <= 1e-7 * abs(theta[i]) * np.linalg.norm(AVhat) * np.linalg.norm(y)
+
+
+def test_select_smallest_pairs_and_split_rule():
+    theta = np.array([5.0, 1 + 1j, 1 - 1j, 0.5, 3.0])
+    Z = np.eye(5, dtype=complex) + 1j * np.roll(np.eye(5), 1, axis=0)
+    P = krylov.select_smallest(theta, Z, 3)        # 0.5, pair (|.|=1.41) -> 3 cols
+    assert P.shape == (5, 3)
+    np.testing.assert_array_equal(P[:, 0], np.real(Z[:, 3]))
+    P2 = krylov.select_smallest(theta, Z, 2)       # 0.5 then half a pair: drop it
+    assert P2.shape == (5, 1)
+    theta2 = np.array([-1.0, 1.0, 2.0])
+    P3 = krylov.select_smallest(theta2, np.eye(3, dtype=complex), 1)
+    np.testing.assert_array_equal(P3[:, 0], [1.0, 0.0, 0.0])   # tie on |theta|: smaller real part
+
+
+def test_qr_pos_normalisation():
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((10, 4))
+    Q, R = krylov.qr_pos(X)
+    assert np.all(np.diag(R) > 0)
+    np.testing.assert_allclose(Q @ R, X, atol=1e-13)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(4), atol=1e-14)

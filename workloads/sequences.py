@@ -1,0 +1,114 @@
+"""Seeded sequences of PDE problem parameters.
+
+Each generator returns the raw parameters of N problems of one PDE family:
+coefficient fields on the node grid, scalar parameters and right-hand-side
+fields.  They stand in for the paper's generated datasets (App. D.2), which
+are not available; the shapes and distributions follow the workload table in
+the design doc (Darcy with a = exp(GRF), convection-diffusion with random nu and
+beta, batched chains of mixed grid sides, and a Poisson arrival stream).
+"""
+import numpy as np
+
+from .grf import grf_field
+
+
+def darcy2d_sequence(nside, nsys, ell, sigma=1.0, seed=0):
+    """N Darcy problems -div(a grad u) = 1 on an nside x nside interior grid.
+
+    Returns log a at the (nside+2)^2 nodes of every problem, shape
+    (nsys, nside+2, nside+2), float64.  The right-hand side is f = 1.
+    """
+    rng = np.random.default_rng(seed)
+    out = np.empty((nsys, nside + 2, nside + 2))
+    for s in range(nsys):
+        out[s] = grf_field(rng, nside + 2, ell, sigma, ndim=2)
+    return out
+
+
+def darcy3d_sequence(nside, nsys, ell, sigma=1.0, seed=0, pad_factor=2):
+    """N 3D Darcy problems on an nside^3 interior grid: log a at (nside+2)^3 nodes."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((nsys, nside + 2, nside + 2, nside + 2))
+    for s in range(nsys):
+        out[s] = grf_field(rng, nside + 2, ell, sigma, ndim=3, pad_factor=pad_factor)
+    return out
+
+
+def convdiff2d_sequence(nside, nsys, seed=0, nu_range=(0.01, 0.1), beta_max=50.0,
+                        f_ell=0.1):
+    """N convection-diffusion problems -nu lap u + beta . grad u = f.
+
+    nu ~ U[nu_range], beta = U[0, beta_max] * (cos phi, sin phi) with
+    phi ~ U[0, 2 pi), f = GRF(ell = f_ell, sigma = 1) at the interior nodes.
+    Returns (nu[nsys], beta[nsys, 2], f[nsys, nside*nside]).
+    """
+    rng = np.random.default_rng(seed)
+    nu = rng.uniform(nu_range[0], nu_range[1], nsys)
+    mag = rng.uniform(0.0, beta_max, nsys)
+    phi = rng.uniform(0.0, 2.0 * np.pi, nsys)
+    beta = np.stack([mag * np.cos(phi), mag * np.sin(phi)], axis=1)
+    f = np.empty((nsys, nside * nside))
+    for s in range(nsys):
+        g = grf_field(rng, nside + 2, f_ell, 1.0, ndim=2)
+        f[s] = g[1:-1, 1:-1].reshape(-1)
+    return nu, beta, f
+
+
+def batched_chains(nchains, chain_len, sides=(64, 128, 192, 256, 384),
+                   ell_range=(0.05, 0.3), sigma=1.0, seed=0):
+    """Independent Darcy chains of mixed grid sides.
+
+    Every chain draws its side uniformly from `sides` and its correlation
+    length from U[ell_range]; each of its systems is a fresh GRF sample.
+    Returns a list of (side, ell, loga[chain_len, side+2, side+2]).
+    """
+    rng = np.random.default_rng(seed)
+    chains = []
+    for _ in range(nchains):
+        side = int(rng.choice(sides))
+        ell = float(rng.uniform(*ell_range))
+        sub = np.empty((chain_len, side + 2, side + 2))
+        for s in range(chain_len):
+            sub[s] = grf_field(rng, side + 2, ell, sigma, ndim=2)
+        chains.append((side, ell, sub))
+    return chains
+
+
+def serving_stream(nreq, rate, seed=0, sides2d=(128, 256, 512, 1024),
+                   sides3d=(64, 96, 128), frac3d=0.5, ell=0.1, sigma=1.0,
+                   draw_fields=True):
+    """A Poisson arrival stream of Darcy requests.
+
+    Inter-arrival gaps are exponential with mean 1/rate seconds.  Each
+    request is 2D (side from sides2d) or 3D (side from sides3d) with
+    probability frac3d, and carries log a = GRF(ell, sigma) on its node grid.
+    Returns a list of dicts {t, ndim, side, loga}.
+    """
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    reqs = []
+    for _ in range(nreq):
+        t += rng.exponential(1.0 / rate)
+        if rng.uniform() < frac3d:
+            ndim, side = 3, int(rng.choice(sides3d))
+        else:
+            ndim, side = 2, int(rng.choice(sides2d))
+        loga = grf_field(rng, side + 2, ell, sigma, ndim=ndim, pad_factor=1) if draw_fields else None
+        reqs.append({"t": t, "ndim": ndim, "side": side, "loga": loga})
+    return reqs
+
+
+# Named workloads: grid side, number of systems, GRF length scale, solver
+# settings.  Seeds 1..5 in table order.
+CONFIGS = {
+    "darcy32_fp64": dict(kind="darcy2d", nside=32, nsys=20, ell=0.2, sigma=1.0, seed=1,
+                          m=30, k=10, precond="none", precision="fp64", tol=1e-8),
+    "darcy256_mixed": dict(kind="darcy2d", nside=256, nsys=200, ell=0.1, sigma=1.0, seed=2,
+                            m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8),
+    "convdiff512_ilu": dict(kind="convdiff2d", nside=512, nsys=500, seed=3,
+                             m=40, k=20, precond="ilu0", precision="mixed", tol=1e-8),
+    "batched64x50": dict(kind="batched", nchains=64, chain_len=50, seed=4,
+                          m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8),
+    "serving": dict(kind="serving", nreq=2000, rate=200.0, seed=5,
+                     m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8),
+}

@@ -1,0 +1,209 @@
+/*
+ * skr.h -- C ABI of the GB300 sorted-recycling (SKR) solver library.
+ *
+ * The library solves a sequence of sparse linear systems A(i) x(i) = b(i)
+ * that come from one PDE family (Sec. 3.1, Eq. 1 of arXiv 2401.09516).  It
+ * first orders them with the greedy nearest-neighbour sort of Algorithm 1
+ * (Sec. 4.1), then solves them in that order with GCRO-DR (Sec. 4.2,
+ * Algorithm 2), carrying the recycle space U_k, C_k = A U_k from one system
+ * to the next and refreshing it against each new matrix (App. B.1).  k = 0
+ * gives plain restarted GMRES(m), the comparator of Sec. 6.
+ *
+ * Everything runs in hand-written CUDA kernels for sm_103a; there is no CPU
+ * fallback.  All arithmetic is real: the paper allows complex systems, this
+ * library does not.
+ *
+ * Conventions for every entry point:
+ *   - the return value is SKR_OK (0) or a negative SKR_ERR_*; on error,
+ *     skr_last_error() returns a message for the calling thread;
+ *   - "mem" says where the caller's data pointers live: SKR_MEM_DEVICE
+ *     (device memory of the current CUDA device) or SKR_MEM_HOST (host
+ *     memory; the library copies in and out, pinned memory is faster);
+ *   - the caller owns every buffer it passes; the library only borrows them
+ *     for the duration of the call, and the call returns after all of its
+ *     device work has finished;
+ *   - "stream" is a cudaStream_t (NULL = the legacy default stream);
+ *   - arrays are dense, row-major for matrices, 64-bit sizes.
+ */
+#ifndef SKR_H
+#define SKR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t skr_status;
+
+/* call-level status */
+#define SKR_OK                0
+#define SKR_NOT_READY         1   /* skr_poll: the request is still in flight */
+#define SKR_ERR_INVALID_ARG  (-1)
+#define SKR_ERR_OOM          (-2)
+#define SKR_ERR_CUDA         (-3)
+#define SKR_ERR_TIMEOUT      (-4)
+#define SKR_ERR_BUSY         (-5)
+
+/* per-system outcome (skr_result.flag); a system that does not converge
+ * does not fail the call */
+#define SKR_CONVERGED         0   /* true relative residual <= tol */
+#define SKR_NOT_CONVERGED     1   /* Arnoldi step cap (maxit) or refinement cap hit */
+#define SKR_BREAKDOWN         2   /* Arnoldi or QR breakdown without convergence */
+#define SKR_NUMERICAL         3   /* NaN or Inf in a residual */
+
+/* problem formats (skr_system.fmt).  Unknowns are numbered row-major with
+ * the last grid index fastest: p = i*ny + j (2D), p = (i*ny + j)*nz + l (3D),
+ * as in the 2x2 example of Sec. 3.1.  Grids are the unit square / cube with
+ * nx (ny, nz) interior nodes per side and h = 1/(nx+1) per axis. */
+#define SKR_FMT_DARCY2D       1   /* -div(a grad u) = f; coef = log a at the (nx+2)*(ny+2) nodes */
+#define SKR_FMT_DARCY3D       2   /* 3D analogue; coef = log a at (nx+2)*(ny+2)*(nz+2) nodes */
+#define SKR_FMT_CONVDIFF2D    3   /* -nu lap u + beta.grad u = f, upwind; params = {nu, beta_x, beta_y} */
+#define SKR_FMT_STENCIL5      4   /* assembled 2D 5-point matrix; coef = 5 arrays of n doubles:
+                                     diagonal, x-minus (p-ny), x-plus (p+ny), y-minus (p-1), y-plus (p+1) */
+#define SKR_FMT_STENCIL7      5   /* assembled 3D 7-point matrix; coef = 7 arrays: diagonal,
+                                     x-minus, x-plus, y-minus, y-plus, z-minus, z-plus */
+
+/* right preconditioner M (App. D.3): the Krylov method solves A M^-1 y = b, x = M^-1 y */
+#define SKR_PC_NONE           0
+#define SKR_PC_JACOBI         1   /* M = diag(A) */
+#define SKR_PC_ILU0           2   /* M = L U with the pattern of A (reserved) */
+
+/* precision form */
+#define SKR_PREC_FP64         0   /* all vectors and reductions in FP64 */
+#define SKR_PREC_MIXED        1   /* FP32 SpMV/Arnoldi/recycle vectors with FP32 accumulation,
+                                     FP64 true residual, solution, refinement and small dense step */
+
+#define SKR_MEM_DEVICE        0
+#define SKR_MEM_HOST          1
+
+/* compile-time capacity of the small dense step */
+#define SKR_MAX_M            48   /* maximum restart length m */
+#define SKR_MAX_K            24   /* maximum recycle dimension k */
+
+/* One linear system of the sequence (Eq. 1).  Pointers are borrowed for the
+ * call and live where skr_options.mem says. */
+typedef struct skr_system {
+    int32_t fmt;            /* SKR_FMT_* */
+    int32_t nx, ny, nz;     /* interior grid (nz = 1 for 2D) */
+    const double *coef;     /* format data, see SKR_FMT_* (NULL for CONVDIFF2D) */
+    const double *rhs;      /* f at the n unknowns, or NULL for f = 1 */
+    double params[4];       /* CONVDIFF2D: nu, beta_x, beta_y; otherwise unused */
+} skr_system;
+
+typedef struct skr_options {
+    int32_t m;              /* maximum subspace size (Algorithm 2), 2 <= m <= SKR_MAX_M */
+    int32_t k;              /* recycle dimension, 0 <= k <= min(SKR_MAX_K, m-2); 0 = GMRES(m) */
+    int32_t maxit;          /* cap on Arnoldi steps per system (default 10000) */
+    int32_t max_refine;     /* cap on residual-refinement passes per system (default 10) */
+    double  tol;            /* target true relative residual ||b - A x|| / ||b|| (default 1e-8) */
+    double  inner_tol;      /* SKR_PREC_MIXED: relative reduction per inner solve (default 1e-5) */
+    int32_t precond;        /* SKR_PC_* (default SKR_PC_NONE) */
+    int32_t precision;      /* SKR_PREC_* (default SKR_PREC_FP64) */
+    int32_t cluster_size;   /* CTAs cooperating on one system, 1..16 (0 = chosen from n) */
+    int32_t max_slots;      /* chains in flight at once (0 = as many as fit on the GPU) */
+    int32_t mem;            /* SKR_MEM_DEVICE or SKR_MEM_HOST */
+    int32_t reserved;
+    void   *stream;         /* cudaStream_t */
+} skr_options;
+
+typedef struct skr_result {
+    int32_t steps;          /* Arnoldi steps (one A M^-1 product each) */
+    int32_t cycles;         /* GCRO-DR / GMRES cycles */
+    int32_t matvecs;        /* all A M^-1 products, including the k of the recycle refresh */
+    int32_t refinements;    /* inner solves (residual-refinement passes) */
+    int32_t flag;           /* SKR_CONVERGED, ... */
+    int32_t k_final;        /* recycle dimension carried out of this system */
+    double  relres;         /* true ||b - A x||_2 / ||b||_2, computed in FP64 on the device */
+    double  seconds;        /* device time spent on this system (globaltimer) */
+} skr_result;
+
+/* Fill *opt with the defaults named above. */
+skr_status skr_options_default(skr_options *opt);
+
+/*
+ * skr_sort -- Algorithm 1 (Sec. 4.1): greedy nearest-neighbour order.
+ *
+ * params    N x p doubles, row i = the flattened parameter matrix P(i)
+ * start     index of the first system (0 = the paper's system 1)
+ * perm_out  N int32: the solve order, perm_out[0] = start
+ * Distances are squared Frobenius norms summed in one fixed order (element
+ * t into lane t mod 256, lanes added left to right without fused
+ * multiply-add, then combined pairwise); ties go to the lowest index.
+ * Scratch: an N x N FP64 distance matrix in device memory, allocated and
+ * freed by the call.  Errors: N < 0, p < 1 (when N > 0), start outside
+ * [0, N), or a non-finite parameter -> SKR_ERR_INVALID_ARG.
+ */
+skr_status skr_sort(const double *params, int64_t N, int64_t p, int64_t start,
+                    int32_t mem, void *stream, int32_t *perm_out);
+
+/*
+ * skr_solve_sequence -- Algorithm 2 over a sorted sequence (Sec. 4.2,
+ * App. B), with the sorted list cut into independent chains (App. E.2.2).
+ *
+ * systems        N system descriptors (host array; their data pointers per opt->mem)
+ * order          N indices: the solve order (e.g. from skr_sort), or NULL = 0..N-1
+ * chain_offsets  nchains+1 offsets into order (chain c = order[off[c] .. off[c+1]) ),
+ *                or NULL = nchains contiguous near-equal pieces
+ * nchains        >= 1; every system of one chain must share fmt and grid
+ * opt            options (NULL = defaults)
+ * x_out          N pointers (host array); x_out[i] receives n doubles, the
+ *                solution of systems[i] (memory per opt->mem)
+ * results        N entries (host array), indexed like systems
+ * Each chain carries its own U_k, C_k; a chain's first system starts
+ * without a recycle space.  Per system: residual refinement in FP64
+ * around GCRO-DR inner solves (x = 0; repeat r = b - A x, stop when
+ * ||r|| <= tol ||b||, solve A M^-1 d = r, x += M^-1 d).
+ * Device memory for the Krylov basis and recycle vectors is allocated by
+ * the call (or reused from the previous call) and kept by the library until
+ * skr_release_workspace().
+ */
+skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_t *order,
+                              const int64_t *chain_offsets, int32_t nchains,
+                              const skr_options *opt, double *const *x_out,
+                              skr_result *results);
+
+/*
+ * skr_assemble -- the discretisation of one system (Sec. 3.1, App. A.2) as
+ * the solver builds it.
+ *
+ * coef_out    5 (2D) or 7 (3D) arrays of n doubles, the matrix A in the
+ *             layout of SKR_FMT_STENCIL5/7 (may be NULL)
+ * rhs_out     n doubles, b (may be NULL)
+ * Uses the same device code as the solver.  Memory per mem.
+ */
+skr_status skr_assemble(const skr_system *sys, int32_t mem, void *stream,
+                        double *coef_out, double *rhs_out);
+
+/*
+ * skr_apply -- y = A M^-1 v for one system, in the working precision of
+ * `precision` (SKR_PREC_MIXED: FP32 arithmetic, v rounded to FP32 on
+ * input and y widened to FP64 on output), using the solver's own operator
+ * code.  v, y: n doubles each, memory per mem.
+ */
+skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t precision,
+                     const double *v, double *y, int32_t mem, void *stream);
+
+/*
+ * skr_last_stats -- figures of the last skr_solve_sequence call on the
+ * calling thread: the algorithmic bytes its kernel streamed (the compulsory
+ * traffic of each pass, counted by the kernel from the pass sizes, not
+ * measured), the kernel's duration from CUDA events recorded around the
+ * launch on the call's stream, the cluster size, the number of chains in
+ * flight, and the number of kernel launches.  Any pointer may be NULL.
+ */
+skr_status skr_last_stats(uint64_t *bytes, double *kernel_ms, int32_t *cluster_size,
+                          int32_t *slots, int32_t *launches);
+
+/* Free the device workspace cached by skr_solve_sequence (all devices). */
+skr_status skr_release_workspace(void);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *skr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SKR_H */

@@ -1,0 +1,307 @@
+"""ctypes binding of libskr.so (the C ABI in include/skr.h).
+
+Argument marshalling only: every computation happens in the CUDA library.
+Functions keep the C names.  Arrays may be numpy arrays (host memory,
+SKR_MEM_HOST) or CUDA tensors (device memory, SKR_MEM_DEVICE); all arrays
+of one call must live in the same place.  If the library has not been
+built, importing this module raises: there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libskr.so")
+
+# constants (mirror include/skr.h)
+SKR_OK = 0
+SKR_NOT_READY = 1
+SKR_ERR_INVALID_ARG = -1
+SKR_ERR_OOM = -2
+SKR_ERR_CUDA = -3
+SKR_ERR_TIMEOUT = -4
+SKR_ERR_BUSY = -5
+SKR_CONVERGED = 0
+SKR_NOT_CONVERGED = 1
+SKR_BREAKDOWN = 2
+SKR_NUMERICAL = 3
+SKR_FMT_DARCY2D = 1
+SKR_FMT_DARCY3D = 2
+SKR_FMT_CONVDIFF2D = 3
+SKR_FMT_STENCIL5 = 4
+SKR_FMT_STENCIL7 = 5
+SKR_PC_NONE = 0
+SKR_PC_JACOBI = 1
+SKR_PC_ILU0 = 2
+SKR_PREC_FP64 = 0
+SKR_PREC_MIXED = 1
+SKR_MEM_DEVICE = 0
+SKR_MEM_HOST = 1
+SKR_MAX_M = 48
+SKR_MAX_K = 24
+
+PRECOND = {"none": SKR_PC_NONE, "jacobi": SKR_PC_JACOBI, "ilu0": SKR_PC_ILU0}
+PRECISION = {"fp64": SKR_PREC_FP64, "mixed": SKR_PREC_MIXED}
+
+
+class SkrSystem(ctypes.Structure):
+    _fields_ = [("fmt", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("coef", ctypes.c_void_p), ("rhs", ctypes.c_void_p),
+                ("params", ctypes.c_double * 4)]
+
+
+class SkrOptions(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("k", ctypes.c_int32), ("maxit", ctypes.c_int32),
+                ("max_refine", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("inner_tol", ctypes.c_double), ("precond", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
+                ("max_slots", ctypes.c_int32), ("mem", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class SkrResult(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("cycles", ctypes.c_int32), ("matvecs", ctypes.c_int32),
+                ("refinements", ctypes.c_int32), ("flag", ctypes.c_int32),
+                ("k_final", ctypes.c_int32), ("relres", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "libskr.so is not built (expected at %s); run __graft_entry__.build() "
+        "or python -m paper_2401_09516_gb300.build" % LIB_PATH)
+
+_lib = ctypes.CDLL(LIB_PATH)
+_i32, _i64, _vp, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double
+
+_lib.skr_options_default.argtypes = [ctypes.POINTER(SkrOptions)]
+_lib.skr_sort.argtypes = [_vp, _i64, _i64, _i64, _i32, _vp, _vp]
+_lib.skr_solve_sequence.argtypes = [ctypes.POINTER(SkrSystem), _i64, _vp, _vp, _i32,
+                                    ctypes.POINTER(SkrOptions), ctypes.POINTER(_vp),
+                                    ctypes.POINTER(SkrResult)]
+_lib.skr_assemble.argtypes = [ctypes.POINTER(SkrSystem), _i32, _vp, _vp, _vp]
+_lib.skr_apply.argtypes = [ctypes.POINTER(SkrSystem), _i32, _i32, _vp, _vp, _i32, _vp]
+_lib.skr_last_stats.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
+_lib.skr_release_workspace.argtypes = []
+_lib.skr_last_error.argtypes = []
+_lib.skr_last_error.restype = ctypes.c_char_p
+for _fn in ("skr_options_default", "skr_sort", "skr_solve_sequence", "skr_assemble", "skr_apply",
+            "skr_last_stats", "skr_release_workspace"):
+    getattr(_lib, _fn).restype = ctypes.c_int32
+
+
+class SkrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("skr status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _check(status):
+    if status != SKR_OK:
+        raise SkrError(status, _lib.skr_last_error().decode())
+    return status
+
+
+def _is_device(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_device(x):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("expected a numpy array or a CUDA tensor, got %r" % type(x))
+
+
+def _mem_of(*arrays):
+    kinds = {_is_device(a) for a in arrays if a is not None}
+    if len(kinds) > 1:
+        raise ValueError("all arrays of one call must be on the host or all on the device")
+    return SKR_MEM_DEVICE if kinds == {True} else SKR_MEM_HOST
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _f64(a):
+    if _is_device(a):
+        if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+            raise ValueError("device arrays must be contiguous float64")
+        return a
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def skr_last_error():
+    return _lib.skr_last_error().decode()
+
+
+def skr_options_default(**overrides):
+    """SkrOptions with the library defaults, then the given fields overridden.
+
+    precond / precision accept the names "none"/"jacobi"/"ilu0" and
+    "fp64"/"mixed"; stream accepts a torch stream or a raw handle.
+    """
+    opt = SkrOptions()
+    _check(_lib.skr_options_default(ctypes.byref(opt)))
+    for key, val in overrides.items():
+        if key == "precond" and isinstance(val, str):
+            val = PRECOND[val]
+        if key == "precision" and isinstance(val, str):
+            val = PRECISION[val]
+        if key == "stream":
+            val = _stream_handle(val)
+        setattr(opt, key, val)
+    return opt
+
+
+class System:
+    """One system of the sequence; keeps its arrays alive for the call."""
+
+    def __init__(self, fmt, nx, ny, nz=1, coef=None, rhs=None, params=(0.0, 0.0, 0.0, 0.0)):
+        self.coef = None if coef is None else _f64(coef)
+        self.rhs = None if rhs is None else _f64(rhs)
+        self.fmt, self.nx, self.ny, self.nz = int(fmt), int(nx), int(ny), int(nz)
+        self.params = tuple(float(p) for p in params) + (0.0,) * (4 - len(params))
+        self.n = self.nx * self.ny * (self.nz if fmt in (SKR_FMT_DARCY3D, SKR_FMT_STENCIL7) else 1)
+
+    def struct(self):
+        s = SkrSystem()
+        s.fmt, s.nx, s.ny, s.nz = self.fmt, self.nx, self.ny, self.nz
+        s.coef = _ptr(self.coef)
+        s.rhs = _ptr(self.rhs)
+        for i in range(4):
+            s.params[i] = self.params[i]
+        return s
+
+    def arrays(self):
+        return [self.coef, self.rhs]
+
+
+def darcy2d(loga, rhs=None):
+    """System from log a on the (nx+2) x (ny+2) node grid."""
+    return System(SKR_FMT_DARCY2D, loga.shape[0] - 2, loga.shape[1] - 2, 1, loga, rhs)
+
+
+def darcy3d(loga, rhs=None):
+    return System(SKR_FMT_DARCY3D, loga.shape[0] - 2, loga.shape[1] - 2, loga.shape[2] - 2, loga, rhs)
+
+
+def convdiff2d(nu, beta, nside, rhs=None):
+    return System(SKR_FMT_CONVDIFF2D, nside, nside, 1, None, rhs, (nu, beta[0], beta[1], 0.0))
+
+
+def skr_sort(params, start=0, stream=None):
+    """Algorithm 1 order of the rows of params (N x p float64)."""
+    P = _f64(params)
+    N = int(P.shape[0])
+    p = int(np.prod(P.shape[1:])) if N else 1
+    mem = _mem_of(P)
+    if mem == SKR_MEM_DEVICE:
+        import torch
+        perm = torch.empty(N, dtype=torch.int32, device=P.device)
+    else:
+        perm = np.empty(N, dtype=np.int32)
+    _check(_lib.skr_sort(_ptr(P) if N else None, N, p, int(start), mem, _stream_handle(stream),
+                         _ptr(perm) if N else None))
+    return perm
+
+
+def skr_solve_sequence(systems, order=None, chain_offsets=None, nchains=1, options=None, x_out=None):
+    """Solve the systems in `order` with recycling along each chain.
+
+    Returns (x_out, results): x_out is a list of n-vectors (numpy on the
+    host path, tensors on the device path), results a list of dicts.
+    """
+    N = len(systems)
+    arrays = [a for s in systems for a in s.arrays()]
+    if x_out is not None:
+        arrays += list(x_out)
+    mem = _mem_of(*arrays)
+    opt = options if options is not None else skr_options_default()
+    opt.mem = mem
+    if x_out is None:
+        if mem == SKR_MEM_DEVICE:
+            import torch
+            dev = next(a.device for a in arrays if a is not None)
+            x_out = [torch.empty(s.n, dtype=torch.float64, device=dev) for s in systems]
+        else:
+            x_out = [np.empty(s.n) for s in systems]
+    sysarr = (SkrSystem * max(N, 1))(*[s.struct() for s in systems])
+    xptr = (_vp * max(N, 1))(*[_ptr(x) for x in x_out])
+    res = (SkrResult * max(N, 1))()
+    ordv = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
+    offv = None if chain_offsets is None else np.ascontiguousarray(chain_offsets, dtype=np.int64)
+    _check(_lib.skr_solve_sequence(sysarr, N, None if ordv is None else ordv.ctypes.data,
+                                   None if offv is None else offv.ctypes.data, int(nchains),
+                                   ctypes.byref(opt), xptr, res))
+    return x_out, [res[i].as_dict() for i in range(N)]
+
+
+def skr_assemble(system, stream=None):
+    """(A as nst x n stencil arrays, b) built by the device assembly."""
+    mem = _mem_of(*system.arrays())
+    nst = 7 if system.fmt in (SKR_FMT_DARCY3D, SKR_FMT_STENCIL7) else 5
+    if mem == SKR_MEM_DEVICE:
+        import torch
+        dev = next(a.device for a in system.arrays() if a is not None)
+        coef = torch.empty((nst, system.n), dtype=torch.float64, device=dev)
+        rhs = torch.empty(system.n, dtype=torch.float64, device=dev)
+    else:
+        coef = np.empty((nst, system.n))
+        rhs = np.empty(system.n)
+    s = system.struct()
+    _check(_lib.skr_assemble(ctypes.byref(s), mem, _stream_handle(stream), _ptr(coef), _ptr(rhs)))
+    return coef, rhs
+
+
+def skr_apply(system, v, precond="none", precision="fp64", stream=None):
+    """y = A M^-1 v with the solver's operator code."""
+    v = _f64(v)
+    mem = _mem_of(v, *system.arrays())
+    if mem == SKR_MEM_DEVICE:
+        import torch
+        y = torch.empty_like(v)
+    else:
+        y = np.empty_like(v)
+    s = system.struct()
+    _check(_lib.skr_apply(ctypes.byref(s), PRECOND.get(precond, precond),
+                          PRECISION.get(precision, precision), _ptr(v), _ptr(y), mem,
+                          _stream_handle(stream)))
+    return y
+
+
+def skr_last_stats():
+    b = ctypes.c_uint64()
+    ms = ctypes.c_double()
+    cs, sl, ln = _i32(), _i32(), _i32()
+    _check(_lib.skr_last_stats(ctypes.byref(b), ctypes.byref(ms), ctypes.byref(cs), ctypes.byref(sl),
+                               ctypes.byref(ln)))
+    return {"bytes": b.value, "kernel_ms": ms.value, "cluster_size": cs.value, "slots": sl.value,
+            "launches": ln.value}
+
+
+def skr_release_workspace():
+    _check(_lib.skr_release_workspace())
+
+
+def exported_symbols():
+    """Names of the C functions this binding wraps."""
+    return ["skr_options_default", "skr_sort", "skr_solve_sequence", "skr_assemble", "skr_apply",
+            "skr_last_stats", "skr_release_workspace", "skr_last_error"]
+
+
+def library():
+    return _lib

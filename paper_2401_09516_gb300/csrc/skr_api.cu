@@ -1,0 +1,559 @@
+// C ABI of the SKR library (include/skr.h): validation, device workspace,
+// staging of host data, kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "skr_common.h"
+#include "skr_launch.h"
+#include "skr_ops.cuh"
+#include "skr_sort.cuh"
+
+using namespace skr;
+
+namespace {
+
+thread_local std::string g_err;
+
+skr_status fail(skr_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? SKR_ERR_OOM : SKR_ERR_CUDA,          \
+                        "%s failed: %s", #expr, cudaGetErrorString(e_));                      \
+        }                                                                                     \
+    } while (0)
+
+// RAII device buffer (per call).
+struct DBuf {
+    void *p = nullptr;
+    ~DBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 16); }
+    template <typename X> X *as() const { return reinterpret_cast<X *>(p); }
+};
+
+// Workspace cached across calls (per device), grown on demand.
+struct CachedWs {
+    int device = -1;
+    size_t bytes = 0;
+    void *base = nullptr;
+};
+std::mutex g_ws_mu;
+std::vector<CachedWs> g_ws;
+
+cudaError_t ws_get(size_t bytes, void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    for (auto &w : g_ws) {
+        if (w.device == dev) {
+            if (w.bytes >= bytes) {
+                *out = w.base;
+                return cudaSuccess;
+            }
+            cudaFree(w.base);
+            w.base = nullptr;
+            w.bytes = 0;
+            e = cudaMalloc(&w.base, bytes);
+            if (e != cudaSuccess) return e;
+            w.bytes = bytes;
+            *out = w.base;
+            return cudaSuccess;
+        }
+    }
+    CachedWs w;
+    w.device = dev;
+    e = cudaMalloc(&w.base, bytes);
+    if (e != cudaSuccess) return e;
+    w.bytes = bytes;
+    g_ws.push_back(w);
+    *out = w.base;
+    return cudaSuccess;
+}
+
+bool is_3d(int fmt) { return fmt == SKR_FMT_DARCY3D || fmt == SKR_FMT_STENCIL7; }
+
+long long sys_n(const skr_system &s) {
+    return (long long)s.nx * s.ny * (is_3d(s.fmt) ? s.nz : 1);
+}
+
+long long sys_coef_len(const skr_system &s) {
+    const long long n = sys_n(s);
+    switch (s.fmt) {
+        case SKR_FMT_DARCY2D: return (long long)(s.nx + 2) * (s.ny + 2);
+        case SKR_FMT_DARCY3D: return (long long)(s.nx + 2) * (s.ny + 2) * (s.nz + 2);
+        case SKR_FMT_STENCIL5: return 5 * n;
+        case SKR_FMT_STENCIL7: return 7 * n;
+        default: return 0;
+    }
+}
+
+skr_status check_system(const skr_system &s, long long idx) {
+    if (s.fmt < SKR_FMT_DARCY2D || s.fmt > SKR_FMT_STENCIL7)
+        return fail(SKR_ERR_INVALID_ARG, "system %lld: unknown format %d", idx, s.fmt);
+    if (s.nx < 1 || s.ny < 1 || (is_3d(s.fmt) && s.nz < 1))
+        return fail(SKR_ERR_INVALID_ARG, "system %lld: empty grid", idx);
+    if (s.fmt == SKR_FMT_CONVDIFF2D && s.nx != s.ny)
+        return fail(SKR_ERR_INVALID_ARG, "system %lld: convection-diffusion needs nx == ny", idx);
+    if (s.fmt == SKR_FMT_CONVDIFF2D && !(s.params[0] > 0.0))
+        return fail(SKR_ERR_INVALID_ARG, "system %lld: nu must be positive", idx);
+    if (s.fmt != SKR_FMT_CONVDIFF2D && s.coef == nullptr)
+        return fail(SKR_ERR_INVALID_ARG, "system %lld: coef is NULL", idx);
+    if (sys_n(s) > (1LL << 31) - 1024)
+        return fail(SKR_ERR_INVALID_ARG, "system %lld: too many unknowns", idx);
+    return SKR_OK;
+}
+
+bool same_shape(const skr_system &a, const skr_system &b) {
+    return a.fmt == b.fmt && a.nx == b.nx && a.ny == b.ny && (!is_3d(a.fmt) || a.nz == b.nz);
+}
+
+int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    return (int)std::max(1LL, std::min(b, 152LL * 16));
+}
+
+// Stage one system's data on the device when mem == HOST.
+struct Staged {
+    DBuf coef, rhs;
+    DevSystem dev;
+};
+
+skr_status stage_system(const skr_system &s, int mem, cudaStream_t st, Staged &out) {
+    out.dev.fmt = s.fmt;
+    out.dev.nx = s.nx;
+    out.dev.ny = s.ny;
+    out.dev.nz = is_3d(s.fmt) ? s.nz : 1;
+    for (int i = 0; i < 4; i++) out.dev.params[i] = s.params[i];
+    out.dev.x_out = nullptr;
+    const long long clen = sys_coef_len(s), n = sys_n(s);
+    if (mem == SKR_MEM_HOST) {
+        if (clen > 0) {
+            CUDA_TRY(out.coef.alloc(clen * 8));
+            CUDA_TRY(cudaMemcpyAsync(out.coef.p, s.coef, clen * 8, cudaMemcpyHostToDevice, st));
+        }
+        if (s.rhs) {
+            CUDA_TRY(out.rhs.alloc(n * 8));
+            CUDA_TRY(cudaMemcpyAsync(out.rhs.p, s.rhs, n * 8, cudaMemcpyHostToDevice, st));
+        }
+        out.dev.coef = out.coef.as<double>();
+        out.dev.rhs = s.rhs ? out.rhs.as<double>() : nullptr;
+    } else {
+        out.dev.coef = s.coef;
+        out.dev.rhs = s.rhs;
+    }
+    return SKR_OK;
+}
+
+struct LastStats {
+    unsigned long long bytes = 0;
+    float kernel_ms = 0.f;
+    int cluster_size = 0, slots = 0, launches = 0;
+};
+thread_local LastStats g_last;
+
+}  // namespace
+
+extern "C" {
+
+skr_status skr_options_default(skr_options *opt) {
+    if (!opt) return fail(SKR_ERR_INVALID_ARG, "opt is NULL");
+    memset(opt, 0, sizeof(*opt));
+    opt->m = 30;
+    opt->k = 10;
+    opt->maxit = 10000;
+    opt->max_refine = 10;
+    opt->tol = 1e-8;
+    opt->inner_tol = 1e-5;
+    opt->precond = SKR_PC_NONE;
+    opt->precision = SKR_PREC_FP64;
+    opt->cluster_size = 0;
+    opt->max_slots = 0;
+    opt->mem = SKR_MEM_DEVICE;
+    opt->stream = nullptr;
+    return SKR_OK;
+}
+
+const char *skr_last_error(void) { return g_err.c_str(); }
+
+skr_status skr_sort(const double *params, int64_t N, int64_t p, int64_t start, int32_t mem, void *stream,
+                    int32_t *perm_out) {
+    g_err.clear();
+    if (N < 0) return fail(SKR_ERR_INVALID_ARG, "N < 0");
+    if (N == 0) return SKR_OK;
+    if (!params || !perm_out) return fail(SKR_ERR_INVALID_ARG, "NULL pointer");
+    if (p < 1) return fail(SKR_ERR_INVALID_ARG, "p < 1");
+    if (start < 0 || start >= N) return fail(SKR_ERR_INVALID_ARG, "start out of range");
+    if (mem != SKR_MEM_DEVICE && mem != SKR_MEM_HOST) return fail(SKR_ERR_INVALID_ARG, "bad mem");
+    if (N > (1LL << 20)) return fail(SKR_ERR_INVALID_ARG, "N too large for the N x N distance matrix");
+    cudaStream_t st = (cudaStream_t)stream;
+    DBuf dparams, ddist, dperm, dtaken, derr;
+    const double *P = params;
+    if (mem == SKR_MEM_HOST) {
+        CUDA_TRY(dparams.alloc((size_t)N * p * 8));
+        CUDA_TRY(cudaMemcpyAsync(dparams.p, params, (size_t)N * p * 8, cudaMemcpyHostToDevice, st));
+        P = dparams.as<double>();
+    }
+    CUDA_TRY(ddist.alloc((size_t)N * N * 8));
+    CUDA_TRY(dtaken.alloc((size_t)N));
+    CUDA_TRY(derr.alloc(sizeof(int)));
+    CUDA_TRY(cudaMemsetAsync(derr.p, 0, sizeof(int), st));
+    int *perm = perm_out;
+    if (mem == SKR_MEM_HOST) {
+        CUDA_TRY(dperm.alloc((size_t)N * 4));
+        perm = dperm.as<int>();
+    }
+    const long long nt = (N + SORT_TILE - 1) / SORT_TILE;
+    const long long nblocks = nt * (nt + 1) / 2;
+    if (nblocks > 0x7fffffffLL) return fail(SKR_ERR_INVALID_ARG, "N too large");
+    sort_dist_kernel<<<(unsigned)nblocks, SORT_LANES, 0, st>>>(P, N, p, ddist.as<double>(), derr.as<int>());
+    CUDA_TRY(cudaGetLastError());
+    int herr = 0;
+    CUDA_TRY(cudaMemcpyAsync(&herr, derr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr) return fail(SKR_ERR_INVALID_ARG, "non-finite parameter distance");
+    sort_chain_kernel<<<1, 1024, 0, st>>>(ddist.as<double>(), N, start, perm, dtaken.as<unsigned char>());
+    CUDA_TRY(cudaGetLastError());
+    if (mem == SKR_MEM_HOST)
+        CUDA_TRY(cudaMemcpyAsync(perm_out, perm, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return SKR_OK;
+}
+
+skr_status skr_assemble(const skr_system *sys, int32_t mem, void *stream, double *coef_out, double *rhs_out) {
+    g_err.clear();
+    if (!sys) return fail(SKR_ERR_INVALID_ARG, "sys is NULL");
+    skr_status s0 = check_system(*sys, 0);
+    if (s0 != SKR_OK) return s0;
+    cudaStream_t st = (cudaStream_t)stream;
+    Staged sg;
+    s0 = stage_system(*sys, mem, st, sg);
+    if (s0 != SKR_OK) return s0;
+    const Geom g = make_geom(sys->fmt, sys->nx, sys->ny, sys->nz);
+    DBuf anode, A, b;
+    long long nn = (sys->fmt == SKR_FMT_DARCY2D || sys->fmt == SKR_FMT_DARCY3D) ? sys_coef_len(*sys) : 0;
+    if (nn > 0) {
+        CUDA_TRY(anode.alloc(nn * 8));
+        node_exp_kernel<<<grid_for(nn, 256), 256, 0, st>>>(sg.dev.coef, nn, anode.as<double>());
+        CUDA_TRY(cudaGetLastError());
+    }
+    CUDA_TRY(A.alloc((size_t)g.nst * g.n * 8));
+    CUDA_TRY(b.alloc((size_t)g.n * 8));
+    rows_kernel<<<grid_for(g.n, 256), 256, 0, st>>>(sg.dev, g, anode.as<double>(), A.as<double>(), g.n,
+                                                     b.as<double>(), nullptr, SKR_PC_NONE);
+    CUDA_TRY(cudaGetLastError());
+    const cudaMemcpyKind kind = (mem == SKR_MEM_HOST) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (coef_out) CUDA_TRY(cudaMemcpyAsync(coef_out, A.p, (size_t)g.nst * g.n * 8, kind, st));
+    if (rhs_out) CUDA_TRY(cudaMemcpyAsync(rhs_out, b.p, (size_t)g.n * 8, kind, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return SKR_OK;
+}
+
+skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t precision, const double *v, double *y,
+                     int32_t mem, void *stream) {
+    g_err.clear();
+    if (!sys || !v || !y) return fail(SKR_ERR_INVALID_ARG, "NULL pointer");
+    skr_status s0 = check_system(*sys, 0);
+    if (s0 != SKR_OK) return s0;
+    if (precond != SKR_PC_NONE && precond != SKR_PC_JACOBI)
+        return fail(SKR_ERR_INVALID_ARG, "preconditioner %d not available", precond);
+    if (precision != SKR_PREC_FP64 && precision != SKR_PREC_MIXED)
+        return fail(SKR_ERR_INVALID_ARG, "bad precision");
+    cudaStream_t st = (cudaStream_t)stream;
+    Staged sg;
+    s0 = stage_system(*sys, mem, st, sg);
+    if (s0 != SKR_OK) return s0;
+    const Geom g = make_geom(sys->fmt, sys->nx, sys->ny, sys->nz);
+    DBuf anode, A, dinv, Aw, vw, dv, dy;
+    long long nn = (sys->fmt == SKR_FMT_DARCY2D || sys->fmt == SKR_FMT_DARCY3D) ? sys_coef_len(*sys) : 0;
+    if (nn > 0) {
+        CUDA_TRY(anode.alloc(nn * 8));
+        node_exp_kernel<<<grid_for(nn, 256), 256, 0, st>>>(sg.dev.coef, nn, anode.as<double>());
+        CUDA_TRY(cudaGetLastError());
+    }
+    CUDA_TRY(A.alloc((size_t)g.nst * g.n * 8));
+    CUDA_TRY(dinv.alloc((size_t)g.n * 8));
+    rows_kernel<<<grid_for(g.n, 256), 256, 0, st>>>(sg.dev, g, anode.as<double>(), A.as<double>(), g.n, nullptr,
+                                                     dinv.as<double>(), precond);
+    CUDA_TRY(cudaGetLastError());
+    const double *vin = v;
+    double *yout = y;
+    if (mem == SKR_MEM_HOST) {
+        CUDA_TRY(dv.alloc((size_t)g.n * 8));
+        CUDA_TRY(dy.alloc((size_t)g.n * 8));
+        CUDA_TRY(cudaMemcpyAsync(dv.p, v, (size_t)g.n * 8, cudaMemcpyHostToDevice, st));
+        vin = dv.as<double>();
+        yout = dy.as<double>();
+    }
+    const int gb = grid_for(g.n, 256);
+    if (precision == SKR_PREC_MIXED) {
+        CUDA_TRY(Aw.alloc((size_t)g.nst * g.n * 4));
+        CUDA_TRY(vw.alloc((size_t)g.n * 4));
+        fold_kernel<float><<<gb, 256, 0, st>>>(g, A.as<double>(), g.n, dinv.as<double>(), Aw.as<float>());
+        to_working_kernel<float><<<gb, 256, 0, st>>>(vin, g.n, vw.as<float>());
+        apply_kernel<float><<<gb, 256, 0, st>>>(g, Aw.as<float>(), g.n, vw.as<float>(), yout);
+    } else {
+        CUDA_TRY(Aw.alloc((size_t)g.nst * g.n * 8));
+        fold_kernel<double><<<gb, 256, 0, st>>>(g, A.as<double>(), g.n, dinv.as<double>(), Aw.as<double>());
+        apply_kernel<double><<<gb, 256, 0, st>>>(g, Aw.as<double>(), g.n, vin, yout);
+    }
+    CUDA_TRY(cudaGetLastError());
+    if (mem == SKR_MEM_HOST) CUDA_TRY(cudaMemcpyAsync(y, yout, (size_t)g.n * 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return SKR_OK;
+}
+
+skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_t *order,
+                              const int64_t *chain_offsets, int32_t nchains, const skr_options *opt_in,
+                              double *const *x_out, skr_result *results) {
+    g_err.clear();
+    g_last = LastStats();
+    skr_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        skr_options_default(&opt);
+    if (N < 0) return fail(SKR_ERR_INVALID_ARG, "N < 0");
+    if (N == 0) return SKR_OK;
+    if (!systems || !x_out || !results) return fail(SKR_ERR_INVALID_ARG, "NULL pointer");
+    if (nchains < 1 || nchains > N) return fail(SKR_ERR_INVALID_ARG, "nchains must be in [1, N]");
+    if (opt.m < 2 || opt.m > SKR_MAX_M) return fail(SKR_ERR_INVALID_ARG, "m must be in [2, %d]", SKR_MAX_M);
+    if (opt.k < 0 || opt.k > SKR_MAX_K || (opt.k > 0 && opt.k > opt.m - 2))
+        return fail(SKR_ERR_INVALID_ARG, "k must be in [0, min(%d, m-2)]", SKR_MAX_K);
+    if (opt.maxit < 1) return fail(SKR_ERR_INVALID_ARG, "maxit < 1");
+    if (opt.max_refine < 1) return fail(SKR_ERR_INVALID_ARG, "max_refine < 1");
+    if (!(opt.tol > 0.0) || !(opt.tol < 1.0)) return fail(SKR_ERR_INVALID_ARG, "tol must be in (0, 1)");
+    if (opt.precision == SKR_PREC_MIXED && !(opt.inner_tol > 0.0 && opt.inner_tol < 1.0))
+        return fail(SKR_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
+    if (opt.precond != SKR_PC_NONE && opt.precond != SKR_PC_JACOBI)
+        return fail(SKR_ERR_INVALID_ARG, "preconditioner %d not available in the solver", opt.precond);
+    if (opt.precision != SKR_PREC_FP64 && opt.precision != SKR_PREC_MIXED)
+        return fail(SKR_ERR_INVALID_ARG, "bad precision");
+    if (opt.mem != SKR_MEM_DEVICE && opt.mem != SKR_MEM_HOST) return fail(SKR_ERR_INVALID_ARG, "bad mem");
+    if (opt.cluster_size < 0 || opt.cluster_size > 16) return fail(SKR_ERR_INVALID_ARG, "cluster_size in [0, 16]");
+    cudaStream_t st = (cudaStream_t)opt.stream;
+
+    // order and chains
+    std::vector<int> ord(N);
+    if (order) {
+        std::vector<char> seen(N, 0);
+        for (long long i = 0; i < N; i++) {
+            if (order[i] < 0 || order[i] >= N || seen[order[i]])
+                return fail(SKR_ERR_INVALID_ARG, "order is not a permutation of 0..N-1");
+            seen[order[i]] = 1;
+            ord[i] = order[i];
+        }
+    } else {
+        for (long long i = 0; i < N; i++) ord[i] = (int)i;
+    }
+    std::vector<long long> off(nchains + 1);
+    if (chain_offsets) {
+        for (int c = 0; c <= nchains; c++) off[c] = chain_offsets[c];
+        if (off[0] != 0 || off[nchains] != N) return fail(SKR_ERR_INVALID_ARG, "chain_offsets must span 0..N");
+        for (int c = 0; c < nchains; c++)
+            if (off[c + 1] <= off[c]) return fail(SKR_ERR_INVALID_ARG, "empty or decreasing chain");
+    } else {
+        for (int c = 0; c <= nchains; c++) off[c] = (long long)c * N / nchains;
+    }
+    long long nmax = 0, nodemax = 0;
+    for (long long i = 0; i < N; i++) {
+        skr_status s0 = check_system(systems[i], i);
+        if (s0 != SKR_OK) return s0;
+        if (!x_out[i]) return fail(SKR_ERR_INVALID_ARG, "x_out[%lld] is NULL", i);
+        nmax = std::max(nmax, sys_n(systems[i]));
+        if (systems[i].fmt == SKR_FMT_DARCY2D || systems[i].fmt == SKR_FMT_DARCY3D)
+            nodemax = std::max(nodemax, sys_coef_len(systems[i]));
+    }
+    for (int c = 0; c < nchains; c++)
+        for (long long q = off[c] + 1; q < off[c + 1]; q++)
+            if (!same_shape(systems[ord[q]], systems[ord[off[c]]]))
+                return fail(SKR_ERR_INVALID_ARG, "chain %d mixes grids or formats", c);
+
+    // launch geometry
+    const bool fp64 = opt.precision == SKR_PREC_FP64;
+    const int threads = 512;
+    int cs = opt.cluster_size;
+    if (cs == 0) {
+        cs = (int)std::min<long long>(8, std::max<long long>(1, (nmax + 8191) / 8192));
+    }
+    const size_t smem = chain_smem_bytes(opt.m, opt.k, threads);
+    if (smem > 227 * 1024) return fail(SKR_ERR_INVALID_ARG, "m, k too large for shared memory (%zu bytes)", smem);
+    int maxc = fp64 ? max_active_clusters_f64(cs, threads, smem) : max_active_clusters_f32(cs, threads, smem);
+    if (maxc < 1) return fail(SKR_ERR_CUDA, "cluster of %d CTAs with %zu bytes of shared memory cannot be scheduled", cs, smem);
+    int nslots = std::min(nchains, maxc);
+    if (opt.max_slots > 0) nslots = std::min(nslots, opt.max_slots);
+    const long long chunk = (((nmax + cs - 1) / cs) + 7) / 8 * 8;
+    const long long ld = ((chunk * cs) + 63) / 64 * 64;
+    const size_t esz = fp64 ? 8 : 4;
+    const long long nodecap = std::max<long long>(nodemax, 1);
+    // workspace layout
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o += (bytes + 255) / 256 * 256;
+        return r;
+    };
+    const size_t o_basis = take((size_t)nslots * NCOLS * ld * esz);
+    const size_t o_A64 = take((size_t)nslots * 7 * ld * 8);
+    const size_t o_Aw = take((size_t)nslots * 7 * ld * esz);
+    const size_t o_dinv = take((size_t)nslots * ld * 8);
+    const size_t o_x = take((size_t)nslots * ld * 8);
+    const size_t o_r = take((size_t)nslots * ld * 8);
+    const size_t o_b = take((size_t)nslots * ld * 8);
+    const size_t o_node = take((size_t)nslots * nodecap * 8);
+    void *wbase = nullptr;
+    CUDA_TRY(ws_get(o, &wbase));
+    char *wb = reinterpret_cast<char *>(wbase);
+    // the basis must start zeroed: padded rows are never written by the passes that read them
+    CUDA_TRY(cudaMemsetAsync(wb + o_basis, 0, (size_t)nslots * NCOLS * ld * esz, st));
+
+    // per-call device arrays
+    std::vector<Staged> staged(N);
+    std::vector<DevSystem> hsys(N);
+    for (long long i = 0; i < N; i++) {
+        skr_status s0 = stage_system(systems[i], opt.mem, st, staged[i]);
+        if (s0 != SKR_OK) return s0;
+        hsys[i] = staged[i].dev;
+    }
+    std::vector<DBuf> xstage;
+    if (opt.mem == SKR_MEM_HOST) {
+        xstage.resize(N);
+        for (long long i = 0; i < N; i++) {
+            CUDA_TRY(xstage[i].alloc((size_t)sys_n(systems[i]) * 8));
+            hsys[i].x_out = xstage[i].as<double>();
+        }
+    } else {
+        for (long long i = 0; i < N; i++) hsys[i].x_out = x_out[i];
+    }
+    DBuf dsys, dord, doff, dres, dctr;
+    CUDA_TRY(dsys.alloc(sizeof(DevSystem) * N));
+    CUDA_TRY(dord.alloc(sizeof(int) * N));
+    CUDA_TRY(doff.alloc(sizeof(long long) * (nchains + 1)));
+    CUDA_TRY(dres.alloc(sizeof(DevResult) * N));
+    CUDA_TRY(dctr.alloc(64));
+    CUDA_TRY(cudaMemcpyAsync(dsys.p, hsys.data(), sizeof(DevSystem) * N, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(dord.p, ord.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(doff.p, off.data(), sizeof(long long) * (nchains + 1), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(dctr.p, 0, 64, st));
+    CUDA_TRY(cudaMemsetAsync(dres.p, 0, sizeof(DevResult) * N, st));
+
+    ChainArgs a;
+    a.systems = dsys.as<DevSystem>();
+    a.order = dord.as<int>();
+    a.chain_off = doff.as<long long>();
+    a.nchains = nchains;
+    a.chain_counter = dctr.as<int>();
+    a.ws.basis = wb + o_basis;
+    a.ws.A64 = reinterpret_cast<double *>(wb + o_A64);
+    a.ws.Aw = wb + o_Aw;
+    a.ws.dinv = reinterpret_cast<double *>(wb + o_dinv);
+    a.ws.x = reinterpret_cast<double *>(wb + o_x);
+    a.ws.r = reinterpret_cast<double *>(wb + o_r);
+    a.ws.b = reinterpret_cast<double *>(wb + o_b);
+    a.ws.anode = reinterpret_cast<double *>(wb + o_node);
+    a.ws.ld = ld;
+    a.ws.nodecap = nodecap;
+    a.ws.nslots = nslots;
+    a.results = dres.as<DevResult>();
+    a.m = opt.m;
+    a.k = opt.k;
+    a.maxit = opt.maxit;
+    a.max_refine = opt.max_refine;
+    a.precond = opt.precond;
+    a.tol = opt.tol;
+    a.inner_tol = opt.inner_tol;
+    a.bytes = reinterpret_cast<unsigned long long *>(dctr.as<char>() + 32);
+
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    CUDA_TRY(cudaEventRecord(e0, st));
+    cudaError_t le = fp64 ? launch_chain_f64(a, nslots, cs, threads, smem, st)
+                          : launch_chain_f32(a, nslots, cs, threads, smem, st);
+    CUDA_TRY(cudaEventRecord(e1, st));
+    if (le != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(SKR_ERR_CUDA, "chain kernel launch failed: %s", cudaGetErrorString(le));
+    }
+    std::vector<DevResult> hres(N);
+    unsigned long long hbytes = 0;
+    CUDA_TRY(cudaMemcpyAsync(hres.data(), dres.p, sizeof(DevResult) * N, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&hbytes, a.bytes, sizeof(hbytes), cudaMemcpyDeviceToHost, st));
+    if (opt.mem == SKR_MEM_HOST) {
+        for (long long i = 0; i < N; i++)
+            CUDA_TRY(cudaMemcpyAsync(x_out[i], xstage[i].p, (size_t)sys_n(systems[i]) * 8,
+                                     cudaMemcpyDeviceToHost, st));
+    }
+    cudaError_t se = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (se != cudaSuccess) return fail(SKR_ERR_CUDA, "solve failed: %s", cudaGetErrorString(se));
+    for (long long i = 0; i < N; i++) {
+        skr_result &r = results[i];
+        const DevResult &d = hres[i];
+        r.steps = d.steps;
+        r.cycles = d.cycles;
+        r.matvecs = d.matvecs;
+        r.refinements = d.refinements;
+        r.flag = d.flag;
+        r.k_final = d.k_final;
+        r.relres = d.relres;
+        r.seconds = (d.t_end >= d.t_begin) ? (double)(d.t_end - d.t_begin) * 1e-9 : 0.0;
+    }
+    g_last.bytes = hbytes;
+    g_last.kernel_ms = ms;
+    g_last.cluster_size = cs;
+    g_last.slots = nslots;
+    g_last.launches = 1;
+    return SKR_OK;
+}
+
+skr_status skr_last_stats(uint64_t *bytes, double *kernel_ms, int32_t *cluster_size, int32_t *slots,
+                          int32_t *launches) {
+    if (bytes) *bytes = g_last.bytes;
+    if (kernel_ms) *kernel_ms = g_last.kernel_ms;
+    if (cluster_size) *cluster_size = g_last.cluster_size;
+    if (slots) *slots = g_last.slots;
+    if (launches) *launches = g_last.launches;
+    return SKR_OK;
+}
+
+skr_status skr_release_workspace(void) {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &w : g_ws) {
+        if (w.base) {
+            cudaSetDevice(w.device);
+            cudaFree(w.base);
+        }
+    }
+    g_ws.clear();
+    cudaSetDevice(cur);
+    return SKR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,900 @@
+// The chain kernel: one thread-block cluster solves one chain of systems,
+// in order, with GCRO-DR (Algorithm 2) and residual refinement, carrying
+// U_k, C_k from each system to the next (App. B).
+//
+// Work split.  Every vector of a system (x, r, b, the Krylov basis, U_k,
+// C_k) is cut into cs contiguous row ranges, one per CTA of the cluster;
+// every streaming pass touches only the CTA's own rows.  The only data that
+// crosses CTAs are (a) the stencil halo of the operator's input vector,
+// read through L2 (ld.global.cg) after a cluster barrier, and (b) partial
+// sums, combined through distributed shared memory.  Every CTA then holds
+// the same reduced values and runs the small dense step itself, so all
+// control decisions are taken identically by every CTA without a broadcast.
+//
+// Precision: T is the working precision of the Krylov vectors and of their
+// reductions (float for the mixed form, double for the FP64 form).  The
+// solution, the true residual, the right-hand side and the small dense step
+// are always FP64.
+#pragma once
+
+#include "skr_common.h"
+#include "skr_dense.cuh"
+#include "skr_device.cuh"
+#include "skr_stencil.cuh"
+
+namespace skr {
+
+template <typename T> struct Tiles;
+template <> struct Tiles<float> {
+    static constexpr int G = 32;   // columns per multi-dot group
+    static constexpr int TA = 8;   // Gram tile rows
+    static constexpr int TB = 8;   // Gram tile cols
+};
+template <> struct Tiles<double> {
+    static constexpr int G = 16;
+    static constexpr int TA = 4;
+    static constexpr int TB = 8;
+};
+
+// Shared-memory layout, computed identically on host and device.
+struct SmemPlan {
+    int m, k, nwarps;
+    int ldh, redcap;
+    // offsets in doubles
+    int o_red, o_vals, o_wsum, o_H, o_B, o_Rw, o_gvec, o_y2, o_gam, o_avec, o_gc, o_gs, o_dscr, o_F,
+        o_Z, o_wr, o_wi, o_xr, o_xi, o_vscr, o_P, o_GP, o_Qc, o_Rc, o_tau, o_D, o_sc, o_Tco, o_mon,
+        o_int, total;
+    // offsets inside the T coefficient region (in T elements)
+    int t_h, t_cC, t_cU, t_cr, t_cd, t_total;
+};
+
+__host__ __device__ inline int align2(int x) { return (x + 1) & ~1; }
+
+__host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads) {
+    SmemPlan P;
+    P.m = m;
+    P.k = k;
+    P.nwarps = nthreads / 32;
+    P.ldh = m + 1;
+    int rc = m + 8;
+    if ((m + 1) * k + 2 * k + 8 > rc) rc = (m + 1) * k + 2 * k + 8;
+    if (k * k + 8 > rc) rc = k * k + 8;
+    P.redcap = align2(rc);
+    const int kk = k + 1;
+    int o = 0;
+    P.o_red = o;   o += 2 * P.redcap;
+    P.o_vals = o;  o += P.redcap;
+    P.o_wsum = o;  o += align2(P.nwarps * 32);
+    P.o_H = o;     o += align2(P.ldh * m);
+    P.o_B = o;     o += align2(k * m);
+    P.o_Rw = o;    o += align2(P.ldh * m);
+    P.o_gvec = o;  o += align2(m + 2);
+    P.o_y2 = o;    o += align2(m + 2);
+    P.o_gam = o;   o += align2(m + 2);
+    P.o_avec = o;  o += align2(k + 2);
+    P.o_gc = o;    o += align2(m + 2);
+    P.o_gs = o;    o += align2(m + 2);
+    P.o_dscr = o;  o += align2(m + 2);
+    P.o_F = o;     o += align2(P.ldh * (m > k ? m : k));   // F / M; also the refresh Gram
+    P.o_Z = o;     o += align2(m * m > 2 * k * k ? m * m : 2 * k * k);  // Schur vectors; also R, R^-1
+    P.o_wr = o;    o += align2(m);
+    P.o_wi = o;    o += align2(m);
+    P.o_xr = o;    o += align2(kk * m > 64 ? kk * m : 64);   // also the Gram tile buffer
+    P.o_xi = o;    o += align2(kk * m);
+    P.o_vscr = o;  o += align2(m + 2);
+    P.o_P = o;     o += align2(m * kk);
+    P.o_GP = o;    o += align2(P.ldh * kk);
+    P.o_Qc = o;    o += align2(P.ldh * kk);
+    P.o_Rc = o;    o += align2(kk * kk);
+    P.o_tau = o;   o += align2(kk + 1);
+    P.o_D = o;     o += align2(k + 2);
+    P.o_sc = o;    o += 16;
+    // T coefficient region (sized in doubles: T is at most 8 bytes)
+    P.t_h = 0;
+    P.t_cC = P.t_h + align2(m + 4);
+    P.t_cU = P.t_cC + align2((m + 1) * (k > 0 ? k : 1));
+    P.t_cr = P.t_cU + align2(m * (k > 0 ? k : 1));
+    P.t_cd = P.t_cr + align2(m + 2);
+    P.t_total = P.t_cd + align2(m + k + 2);
+    P.o_Tco = o;   o += align2(P.t_total);
+    P.o_mon = o;   o += align2(3 * m + 4);             // FP32 Givens monitor (as floats, room to spare)
+    P.o_int = o;   o += align2(64 + 8 + 3 * MMAX);      // control ints
+    P.total = o;
+    return P;
+}
+
+__host__ __device__ inline size_t plan_bytes(const SmemPlan &P) { return (size_t)P.total * 8; }
+
+template <typename T>
+struct Ctx {
+    // cluster and rows
+    unsigned rank, cs;
+    long long lo, cnt;
+    Geom g;
+    long long ld;
+    // slot buffers
+    T *basis;
+    double *A64;
+    T *Aw;
+    double *dinv, *x, *r, *b, *anode;
+    // parameters
+    int m, k, maxit, precond;
+    // shared memory
+    SmemPlan P;
+    double *sm;
+    int parity;
+    // recycle dimension carried by this chain
+    int kc;
+    // per-system statistics
+    int steps, cycles, matvecs, refinements;
+    bool breakdown;
+    unsigned long long bytes;
+
+    __device__ T *col(int c) const { return basis + (long long)c * ld; }
+    __device__ double *D(int off) const { return sm + off; }
+    template <typename R>
+    __device__ R *red() const { return reinterpret_cast<R *>(sm + P.o_red + parity * P.redcap); }
+    template <typename R>
+    __device__ R *vals() const { return reinterpret_cast<R *>(sm + P.o_vals); }
+    __device__ T *tco(int off) const { return reinterpret_cast<T *>(sm + P.o_Tco) + off; }
+    __device__ int *ints() const { return reinterpret_cast<int *>(sm + P.o_int); }
+    __device__ float *mon() const { return reinterpret_cast<float *>(sm + P.o_mon); }
+};
+
+// Sum the CTA partials red<R>()[0..nv) over the cluster into vals<R>().
+// One cluster barrier; the reduction buffers alternate so that the next
+// call never overwrites a buffer that another CTA may still be reading.
+template <typename T, typename R>
+__device__ __forceinline__ void allreduce(Ctx<T> &c, int nv) {
+    cl_sync();
+    R *src = c.template red<R>();
+    R *dst = c.template vals<R>();
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        R s = R(0);
+        for (unsigned q = 0; q < c.cs; q++) s += *cl_map(src + i, q);
+        dst[i] = s;
+    }
+    c.parity ^= 1;
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ streaming passes
+
+// CTA partials of Q_j . y for the q columns starting at c0 (own rows), into out[0..q).
+template <typename T>
+__device__ void part_multidot(Ctx<T> &c, int c0, int q, const T *y, T *out) {
+    typedef typename Vec<T>::type VT;
+    constexpr int E = Vec<T>::N, G = Tiles<T>::G;
+    const int nvec = (int)(c.cnt / E);
+    const VT *yv = reinterpret_cast<const VT *>(y + c.lo);
+    T *wsum = reinterpret_cast<T *>(c.D(c.P.o_wsum));
+    for (int g0 = 0; g0 < q; g0 += G) {
+        const int gq = min(G, q - g0);
+        T acc[G];
+#pragma unroll
+        for (int j = 0; j < G; j++) acc[j] = T(0);
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+            const VT yy = yv[i];
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                if (j < gq) {
+                    const VT xv = reinterpret_cast<const VT *>(c.col(c0 + g0 + j) + c.lo)[i];
+                    acc[j] += vdot(xv, yy);
+                }
+            }
+        }
+        block_sum<G>(acc, gq, wsum, out + g0);
+    }
+    c.bytes += (unsigned long long)(q + 1) * c.g.n * sizeof(T);
+}
+
+// y -= sum_j h[j] Q_j over own rows (q columns from c0); optionally the CTA
+// partial of ||y||^2 into *nrm_out.
+template <typename T>
+__device__ void update_rows(Ctx<T> &c, int c0, int q, const T *h, T *y, T *nrm_out) {
+    typedef typename Vec<T>::type VT;
+    constexpr int E = Vec<T>::N;
+    const int nvec = (int)(c.cnt / E);
+    VT *yv = reinterpret_cast<VT *>(y + c.lo);
+    T acc[1] = {T(0)};
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+        VT yy = yv[i];
+#pragma unroll 8
+        for (int j = 0; j < q; j++) {
+            const VT xv = reinterpret_cast<const VT *>(c.col(c0 + j) + c.lo)[i];
+            yy = vaxmy(yy, h[j], xv);
+        }
+        yv[i] = yy;
+        acc[0] += vdot(yy, yy);
+    }
+    if (nrm_out) {
+        block_sum<1>(acc, 1, reinterpret_cast<T *>(c.D(c.P.o_wsum)), nrm_out);
+    } else {
+        __syncthreads();
+    }
+    c.bytes += (unsigned long long)(q + 2) * c.g.n * sizeof(T);
+}
+
+// Operator pass of an Arnoldi step: for own rows, vout = s * src (the new
+// basis vector, if vout) and y = A M^-1 (s * src); padded rows get zeros.
+template <typename T>
+__device__ void spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
+    const long long hi = c.lo + c.cnt;
+    for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
+        if (p < c.g.n) {
+            if (vout) vout[p] = s * __ldcg(src + p);
+            y[p] = stencil_apply_row(c.g, c.Aw, c.ld, src, s, p);
+        } else {
+            if (vout) vout[p] = T(0);
+            y[p] = T(0);
+        }
+    }
+    __syncthreads();
+    c.bytes += (unsigned long long)(3 + (vout ? 1 : 0) + c.g.nst) * c.g.n * sizeof(T) -
+               (unsigned long long)(vout ? 0 : 1) * c.g.n * sizeof(T);
+}
+
+// Tiled CTA partials of X_a . Y_b (a < na from column xa0, b < nb from
+// column yb0), into out[a * nb + b].
+template <typename T>
+__device__ void part_gram(Ctx<T> &c, int xa0, int na, int yb0, int nb, T *out) {
+    typedef typename Vec<T>::type VT;
+    constexpr int E = Vec<T>::N, TA = Tiles<T>::TA, TB = Tiles<T>::TB;
+    const int nvec = (int)(c.cnt / E);
+    T *wsum = reinterpret_cast<T *>(c.D(c.P.o_wsum));
+    T *tmp = reinterpret_cast<T *>(c.D(c.P.o_dscr));   // TA*TB <= 64 values needed
+    for (int a0 = 0; a0 < na; a0 += TA) {
+        const int ta = min(TA, na - a0);
+        for (int b0 = 0; b0 < nb; b0 += TB) {
+            const int tb = min(TB, nb - b0);
+            T acc[TA * TB];
+#pragma unroll
+            for (int e = 0; e < TA * TB; e++) acc[e] = T(0);
+            for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+                VT yv[TB];
+#pragma unroll
+                for (int bb = 0; bb < TB; bb++)
+                    yv[bb] = (bb < tb) ? reinterpret_cast<const VT *>(c.col(yb0 + b0 + bb) + c.lo)[i]
+                                       : vzero(T(0));
+#pragma unroll
+                for (int aa = 0; aa < TA; aa++) {
+                    if (aa < ta) {
+                        const VT xv = reinterpret_cast<const VT *>(c.col(xa0 + a0 + aa) + c.lo)[i];
+#pragma unroll
+                        for (int bb = 0; bb < TB; bb++) acc[aa * TB + bb] += vdot(xv, yv[bb]);
+                    }
+                }
+            }
+            (void)tmp;
+            // reduce the whole tile, then scatter the valid entries
+            T *tout = reinterpret_cast<T *>(c.D(c.P.o_vscr)) ;
+            (void)tout;
+            block_sum<TA * TB>(acc, TA * TB, wsum, reinterpret_cast<T *>(c.D(c.P.o_xr)));
+            const T *res = reinterpret_cast<const T *>(c.D(c.P.o_xr));
+            for (int e = threadIdx.x; e < ta * tb; e += blockDim.x) {
+                const int aa = e / tb, bb = e % tb;
+                out[(a0 + aa) * nb + (b0 + bb)] = res[aa * TB + bb];
+            }
+            __syncthreads();
+        }
+    }
+    c.bytes += (unsigned long long)(na + nb) * c.g.n * sizeof(T);
+}
+
+// ------------------------------------------------------------------ assembly
+
+// Build A (FP64), b, M^-1 diag and the working-precision operator A M^-1 for
+// system `sys` into the slot.  Three phases separated by cluster barriers:
+// node values, rows of A, folded operator (needs the neighbours' diagonal).
+template <typename T>
+__device__ void assemble_system(Ctx<T> &c, const DevSystem &sys) {
+    const long long nn = node_count(sys, c.g);
+    if (nn > 0) {
+        const long long per = (nn + c.cs - 1) / c.cs;
+        const long long a0 = (long long)c.rank * per, a1 = min(nn, a0 + per);
+        for (long long q = a0 + threadIdx.x; q < a1; q += blockDim.x) c.anode[q] = exp(sys.coef[q]);
+        cl_sync();
+    }
+    const long long hi = c.lo + c.cnt;
+    for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
+        if (p < c.g.n) {
+            double row[7];
+            system_row(sys, c.g, c.anode, p, row);
+            for (int s = 0; s < c.g.nst; s++) c.A64[(long long)s * c.ld + p] = row[s];
+            c.b[p] = sys.rhs ? sys.rhs[p] : 1.0;
+            c.dinv[p] = (c.precond == SKR_PC_JACOBI) ? 1.0 / row[0] : 1.0;
+        } else {
+            for (int s = 0; s < c.g.nst; s++) c.A64[(long long)s * c.ld + p] = 0.0;
+            c.b[p] = 0.0;
+            c.dinv[p] = 1.0;
+        }
+    }
+    cl_sync();
+    for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
+        if (p < c.g.n) {
+            for (int s = 0; s < c.g.nst; s++) {
+                const long long q = nb_index(c.g, p, s);
+                const double a = c.A64[(long long)s * c.ld + p];
+                c.Aw[(long long)s * c.ld + p] = (T)(a * __ldcg(c.dinv + q));
+            }
+        } else {
+            for (int s = 0; s < c.g.nst; s++) c.Aw[(long long)s * c.ld + p] = T(0);
+        }
+    }
+    __syncthreads();
+    c.bytes += (unsigned long long)c.g.n * (8 * (c.g.nst + 3) + sizeof(T) * c.g.nst) +
+               (unsigned long long)nn * 16;
+}
+
+// True residual r = b - A x (FP64) over own rows; returns ||r|| (cluster-wide).
+template <typename T>
+__device__ double true_residual(Ctx<T> &c) {
+    cl_sync();   // x of the neighbours must be complete
+    const long long hi = c.lo + c.cnt;
+    double acc[1] = {0.0};
+    for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
+        double rv = 0.0;
+        if (p < c.g.n) rv = residual_row(c.g, c.A64, c.ld, c.b, c.x, p);
+        c.r[p] = rv;
+        acc[0] += rv * rv;
+    }
+    block_sum<1>(acc, 1, c.D(c.P.o_wsum), c.template red<double>());
+    allreduce<T, double>(c, 1);
+    c.bytes += (unsigned long long)c.g.n * 8 * (c.g.nst + 3);
+    return sqrt(c.template vals<double>()[0]);
+}
+
+// ------------------------------------------------------------------ recycle refresh
+
+// App. B.1: [Q, R] = qr(A_new U), C = Q, U = U R^-1, by Cholesky QR applied
+// twice (the Gram matrices are reduced over the cluster, the k x k factors
+// are FP64).  On a failed Cholesky the recycle space is dropped (kc = 0).
+template <typename T>
+__device__ void refresh_recycle(Ctx<T> &c) {
+    const int kc = c.kc;
+    const int cC0 = COL_C_END - kc;
+    // W = A M^-1 U into the C columns
+    const long long hi = c.lo + c.cnt;
+    for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
+        T acc[KMAX];
+#pragma unroll
+        for (int b = 0; b < KMAX; b++) acc[b] = T(0);
+        if (p < c.g.n) {
+            for (int s = 0; s < c.g.nst; s++) {
+                const long long q = nb_index(c.g, p, s);
+                const T a = c.Aw[(long long)s * c.ld + p];
+#pragma unroll
+                for (int b = 0; b < KMAX; b++)
+                    if (b < kc) acc[b] += a * __ldcg(c.col(COL_U0 + b) + q);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < KMAX; b++)
+            if (b < kc) c.col(cC0 + b)[p] = acc[b];
+    }
+    __syncthreads();
+    c.matvecs += kc;
+    c.bytes += (unsigned long long)c.g.n * sizeof(T) * (c.g.nst + 2 * kc);
+    double *G = c.D(c.P.o_F);
+    double *R = c.D(c.P.o_Z);
+    double *Ri = c.D(c.P.o_Z) + kc * kc;
+    for (int pass = 0; pass < 2; pass++) {
+        part_gram(c, cC0, kc, cC0, kc, c.template red<T>());
+        allreduce<T, T>(c, kc * kc);
+        const T *gv = c.template vals<T>();
+        for (int e = threadIdx.x; e < kc * kc; e += blockDim.x) G[e] = (double)gv[e];  // symmetric
+        __syncthreads();
+        const int bad = cholesky_upper(G, kc, kc, R, kc, c.ints());
+        __syncthreads();
+        if (bad) {
+            c.kc = 0;
+            return;
+        }
+        upper_inverse(R, kc, kc, Ri, kc);
+        T *rt = c.tco(c.P.t_cC);
+        for (int e = threadIdx.x; e < kc * kc; e += blockDim.x) rt[e] = (T)Ri[e];  // column-major (i + j kc)
+        __syncthreads();
+        // W <- W R^-1, U <- U R^-1 (row-local, in place)
+        for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
+            for (int which = 0; which < 2; which++) {
+                T *base = (which == 0) ? c.col(cC0) : c.col(COL_U0);
+                T in[KMAX], out[KMAX];
+#pragma unroll
+                for (int b = 0; b < KMAX; b++) in[b] = (b < kc) ? base[(long long)b * c.ld + p] : T(0);
+#pragma unroll
+                for (int j = 0; j < KMAX; j++) {
+                    T s = T(0);
+#pragma unroll
+                    for (int i = 0; i < KMAX; i++)
+                        if (i <= j && j < kc) s += in[i] * rt[i + j * kc];
+                    out[j] = s;
+                }
+#pragma unroll
+                for (int b = 0; b < KMAX; b++)
+                    if (b < kc) base[(long long)b * c.ld + p] = out[b];
+            }
+        }
+        __syncthreads();
+        c.bytes += (unsigned long long)c.g.n * sizeof(T) * (2 * kc + 4 * kc);
+    }
+}
+
+// Projection at the start of a recycled cycle (the first step of
+// Algorithm 2): z = C^T r, d += U z, r -= C z.  Returns ||r||.
+template <typename T>
+__device__ double project_recycle(Ctx<T> &c) {
+    const int kc = c.kc;
+    const int cC0 = COL_C_END - kc;
+    T *rw = c.col(COL_RW), *dh = c.col(COL_DH);
+    part_multidot(c, cC0, kc, rw, c.template red<T>());
+    allreduce<T, T>(c, kc);
+    T *z = c.tco(c.P.t_h);
+    for (int i = threadIdx.x; i < kc; i += blockDim.x) z[i] = c.template vals<T>()[i];
+    __syncthreads();
+    typedef typename Vec<T>::type VT;
+    constexpr int E = Vec<T>::N;
+    const int nvec = (int)(c.cnt / E);
+    T acc[1] = {T(0)};
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+        VT rr = reinterpret_cast<VT *>(rw + c.lo)[i];
+        VT dd = reinterpret_cast<VT *>(dh + c.lo)[i];
+        for (int a = 0; a < kc; a++) {
+            rr = vaxmy(rr, z[a], reinterpret_cast<const VT *>(c.col(cC0 + a) + c.lo)[i]);
+            dd = vaxpy(dd, z[a], reinterpret_cast<const VT *>(c.col(COL_U0 + a) + c.lo)[i]);
+        }
+        reinterpret_cast<VT *>(rw + c.lo)[i] = rr;
+        reinterpret_cast<VT *>(dh + c.lo)[i] = dd;
+        acc[0] += vdot(rr, rr);
+    }
+    block_sum<1>(acc, 1, reinterpret_cast<T *>(c.D(c.P.o_wsum)), c.template red<T>());
+    allreduce<T, T>(c, 1);
+    c.bytes += (unsigned long long)c.g.n * sizeof(T) * (2 * kc + 4);
+    return sqrt((double)c.template vals<T>()[0]);
+}
+
+// ------------------------------------------------------------------ one cycle
+
+// FP32 Givens monitor on column j of H: returns the LSQ residual estimate.
+template <typename T>
+__device__ float monitor_step(Ctx<T> &c, int j, float beta) {
+    float *mc = c.mon(), *ms = mc + c.m, *mg = ms + c.m;
+    const double *H = c.D(c.P.o_H);
+    const int ldh = c.P.ldh;
+    if (threadIdx.x == 0) {
+        if (j == 0) mg[0] = beta;
+        float a = (float)M_(H, ldh, 0, j);
+        for (int i = 0; i < j; i++) {
+            const float b = (float)M_(H, ldh, i + 1, j);
+            const float na = mc[i] * a + ms[i] * b;
+            const float nb = -ms[i] * a + mc[i] * b;
+            a = nb;
+            (void)na;
+        }
+        // the rotated entry a now sits in row j; rotation j zeroes H(j+1, j)
+        const float b = (float)M_(H, ldh, j + 1, j);
+        const float r = hypotf(a, b);
+        const float cs = (r > 0.f) ? a / r : 1.f, sn = (r > 0.f) ? b / r : 0.f;
+        mc[j] = cs;
+        ms[j] = sn;
+        mg[j + 1] = -sn * mg[j];
+        mg[j] = cs * mg[j];
+        c.ints()[4] = __float_as_int(fabsf(mg[j + 1]));
+    }
+    __syncthreads();
+    const float est = __int_as_float(c.ints()[4]);
+    __syncthreads();
+    return est;
+}
+
+// One GCRO-DR cycle (kc > 0) or GMRES cycle (kc == 0) on the inner system
+// A M^-1 d = r, following Algorithm 2.  rnw = ||rw|| on entry; returns the
+// new ||rw||.
+template <typename T>
+__device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
+    const int kc = c.kc;
+    const int Lmax = (kc == 0) ? c.m : c.m - kc;
+    const int L = min(Lmax, c.maxit - c.steps);
+    const int ldh = c.P.ldh;
+    double *H = c.D(c.P.o_H), *Bm = c.D(c.P.o_B);
+    const int cQ0 = COL_C_END - kc;   // [C, V_1, ...] start
+    T *h = c.tco(c.P.t_h);
+    const T tiny = (sizeof(T) == 4) ? T(1e-6) : T(1e-13);
+
+    const T *src = c.col(COL_RW);
+    T s = (T)(1.0 / rnw);
+    int ycur = COL_Y0;
+    int jdone = 0;
+    bool early = false;
+    for (int j = 0; j < L; j++) {
+        T *y = c.col(ycur);
+        // S: V_j = s * src; y = A M^-1 V_j; dots [C, V_0..V_j] . y and y . y
+        spmv_pass(c, src, s, c.col(COL_V0 + j), y);
+        const int q = kc + j + 1;
+        part_multidot(c, cQ0, q, y, c.template red<T>());
+        {
+            T acc[1] = {T(0)};
+            typedef typename Vec<T>::type VT;
+            const int nvec = (int)(c.cnt / Vec<T>::N);
+            for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+                const VT yy = reinterpret_cast<const VT *>(y + c.lo)[i];
+                acc[0] += vdot(yy, yy);
+            }
+            block_sum<1>(acc, 1, reinterpret_cast<T *>(c.D(c.P.o_wsum)), c.template red<T>() + q);
+        }
+        allreduce<T, T>(c, q + 1);
+        const T ynorm = sqrt(c.template vals<T>()[q]);
+        for (int i = threadIdx.x; i < q; i += blockDim.x) {
+            const T v = c.template vals<T>()[i];
+            h[i] = v;
+            if (i < kc)
+                M_(Bm, kc, i, j) = (double)v;
+            else
+                M_(H, ldh, i - kc, j) = (double)v;
+        }
+        __syncthreads();
+        update_rows(c, cQ0, q, h, y, (T *)nullptr);
+        // second Gram-Schmidt pass
+        part_multidot(c, cQ0, q, y, c.template red<T>());
+        allreduce<T, T>(c, q);
+        for (int i = threadIdx.x; i < q; i += blockDim.x) {
+            const T v = c.template vals<T>()[i];
+            h[i] = v;
+            if (i < kc)
+                M_(Bm, kc, i, j) += (double)v;
+            else
+                M_(H, ldh, i - kc, j) += (double)v;
+        }
+        __syncthreads();
+        update_rows(c, cQ0, q, h, y, c.template red<T>());
+        allreduce<T, T>(c, 1);
+        const T hn = sqrt(c.template vals<T>()[0]);
+        if (threadIdx.x == 0) M_(H, ldh, j + 1, j) = (double)hn;
+        for (int i = j + 2 + threadIdx.x; i <= c.m; i += blockDim.x) M_(H, ldh, i, j) = 0.0;
+        __syncthreads();
+        c.steps += 1;
+        c.matvecs += 1;
+        const float est = monitor_step(c, j, (float)rnw);
+        const bool brk = !(hn > tiny * ynorm);
+        src = y;
+        s = brk ? T(0) : T(1) / hn;
+        ycur = (ycur == COL_Y0) ? COL_Y1 : COL_Y0;
+        jdone = j + 1;
+        if (brk) c.breakdown = true;
+        if (est <= (float)target || brk) {
+            early = true;
+            break;
+        }
+    }
+    if (jdone == 0) return rnw;
+    // materialise V_{jdone} = s * src (own rows only)
+    {
+        T *v = c.col(COL_V0 + jdone);
+        for (long long p = c.lo + threadIdx.x; p < c.lo + c.cnt; p += blockDim.x) v[p] = s * src[p];
+        __syncthreads();
+    }
+    const int Ld = jdone;
+    const bool full = (!early) && (Ld == Lmax) && (c.k > 0);
+    const int mt = kc + Ld;
+    // Gram pass for the harmonic-Ritz problem: [C, V_0..V_Ld]^T U and ||u_b||^2
+    T *gram = c.template red<T>();
+    if (full && kc > 0) {
+        part_gram(c, cQ0, kc + Ld + 1, COL_U0, kc, gram);
+        // ||u_b||^2
+        typedef typename Vec<T>::type VT;
+        const int nvec = (int)(c.cnt / Vec<T>::N);
+        T acc[KMAX];
+#pragma unroll
+        for (int b = 0; b < KMAX; b++) acc[b] = T(0);
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+#pragma unroll
+            for (int b = 0; b < KMAX; b++)
+                if (b < kc) {
+                    const VT u = reinterpret_cast<const VT *>(c.col(COL_U0 + b) + c.lo)[i];
+                    acc[b] += vdot(u, u);
+                }
+        }
+        block_sum<KMAX>(acc, kc, reinterpret_cast<T *>(c.D(c.P.o_wsum)), gram + (kc + Ld + 1) * kc);
+        allreduce<T, T>(c, (kc + Ld + 1) * kc + kc);
+    }
+    // ---- small dense step (FP64, every CTA)
+    double *Rw = c.D(c.P.o_Rw), *gv = c.D(c.P.o_gvec), *y2 = c.D(c.P.o_y2), *gam = c.D(c.P.o_gam);
+    double *av = c.D(c.P.o_avec), *gc = c.D(c.P.o_gc), *gs = c.D(c.P.o_gs), *ds = c.D(c.P.o_dscr);
+    givens_lsq(H, ldh, Ld, rnw, Rw, ldh, gc, gs, gv, y2, ds);
+    for (int i = threadIdx.x; i <= Ld; i += blockDim.x) {
+        double sacc = 0.0;
+        for (int j = 0; j < Ld; j++) sacc += M_(H, ldh, i, j) * y2[j];
+        gam[i] = sacc;
+    }
+    for (int a = threadIdx.x; a < kc; a += blockDim.x) {
+        double sacc = 0.0;
+        for (int j = 0; j < Ld; j++) sacc += M_(Bm, kc, a, j) * y2[j];
+        av[a] = -sacc;
+    }
+    __syncthreads();
+    int knew = -1;
+    double *Dk = c.D(c.P.o_D);
+    double *Pm = c.D(c.P.o_P), *GP = c.D(c.P.o_GP), *Qc = c.D(c.P.o_Qc), *Rc = c.D(c.P.o_Rc);
+    if (full) {
+        double *F = c.D(c.P.o_F);
+        const T *gr = c.template vals<T>();
+        for (int b = threadIdx.x; b < kc; b += blockDim.x)
+            Dk[b] = 1.0 / sqrt((double)gr[(kc + Ld + 1) * kc + b]);
+        __syncthreads();
+        // F = W^T V_hat = [[C^T U D, 0], [V^T U D, I']]  ((mt+1) x mt)
+        for (int e = threadIdx.x; e < (mt + 1) * mt; e += blockDim.x) {
+            const int i = e % (mt + 1), j = e / (mt + 1);
+            double v;
+            if (j < kc)
+                v = (double)gr[i * kc + j] * Dk[j];
+            else
+                v = (i >= kc && i - kc == j - kc) ? 1.0 : 0.0;
+            M_(F, ldh, i, j) = v;
+        }
+        __syncthreads();
+        // Q_G^T F: the Givens rotations act on rows kc+i, kc+i+1
+        for (int j = threadIdx.x; j < mt; j += blockDim.x) {
+            for (int i = 0; i < Ld; i++) {
+                const double a = M_(F, ldh, kc + i, j), b = M_(F, ldh, kc + i + 1, j);
+                M_(F, ldh, kc + i, j) = gc[i] * a + gs[i] * b;
+                M_(F, ldh, kc + i + 1, j) = -gs[i] * a + gc[i] * b;
+            }
+        }
+        __syncthreads();
+        // M = R_G^-1 (Q_G^T F)[0:mt], R_G = [[D, B], [0, R_H]], in place in F
+        for (int i = mt - 1; i >= 0; i--) {
+            const double rii = (i < kc) ? Dk[i] : M_(Rw, ldh, i - kc, i - kc);
+            for (int j = threadIdx.x; j < mt; j += blockDim.x) M_(F, ldh, i, j) /= rii;
+            __syncthreads();
+            for (int e = threadIdx.x; e < i * mt; e += blockDim.x) {
+                const int r = e % i, j = e / i;
+                double rri;
+                if (r < kc)
+                    rri = (i < kc) ? 0.0 : M_(Bm, kc, r, i - kc);
+                else
+                    rri = M_(Rw, ldh, r - kc, i - kc);
+                M_(F, ldh, r, j) -= rri * M_(F, ldh, i, j);
+            }
+            __syncthreads();
+        }
+        knew = harmonic_select(F, ldh, mt, c.k, Pm, mt, c.D(c.P.o_Z), mt, c.D(c.P.o_wr),
+                               c.D(c.P.o_wi), c.D(c.P.o_xr), c.D(c.P.o_xi), c.D(c.P.o_vscr),
+                               c.D(c.P.o_sc), c.ints() + 8);
+        __syncthreads();
+        if (knew > 0) {
+            // G P_k, G = [[D, B], [0, Hbar]]
+            for (int e = threadIdx.x; e < (mt + 1) * knew; e += blockDim.x) {
+                const int i = e % (mt + 1), cc = e / (mt + 1);
+                double sacc = 0.0;
+                if (i < kc) {
+                    sacc = Dk[i] * M_(Pm, mt, i, cc);
+                    for (int j = 0; j < Ld; j++) sacc += M_(Bm, kc, i, j) * M_(Pm, mt, kc + j, cc);
+                } else {
+                    for (int j = 0; j < Ld; j++) sacc += M_(H, ldh, i - kc, j) * M_(Pm, mt, kc + j, cc);
+                }
+                M_(GP, ldh, i, cc) = sacc;
+            }
+            __syncthreads();
+            const int bad = householder_qr(GP, ldh, mt + 1, knew, Qc, ldh, Rc, knew,
+                                           c.D(c.P.o_tau), c.D(c.P.o_sc));
+            __syncthreads();
+            if (bad) {
+                knew = -1;
+            } else {
+                // P R^-1 (in place in P), using R^-1 in Z
+                double *Ri = c.D(c.P.o_Z);
+                upper_inverse(Rc, knew, knew, Ri, knew);
+                for (int i = threadIdx.x; i < mt; i += blockDim.x) {
+                    double rowv[KMAX + 1];
+                    for (int cc = 0; cc < knew; cc++) rowv[cc] = M_(Pm, mt, i, cc);
+                    for (int cc = 0; cc < knew; cc++) {
+                        double sacc = 0.0;
+                        for (int q2 = 0; q2 <= cc; q2++) sacc += rowv[q2] * M_(Ri, knew, q2, cc);
+                        M_(Pm, mt, i, cc) = sacc;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (knew > KMAX) knew = -1;
+    }
+    // ---- coefficients in working precision
+    T *cC = c.tco(c.P.t_cC), *cU = c.tco(c.P.t_cU), *cr = c.tco(c.P.t_cr), *cd = c.tco(c.P.t_cd);
+    const int kn = (knew > 0) ? knew : 0;
+    for (int i = threadIdx.x; i <= Ld; i += blockDim.x) cr[i] = (T)gam[i];
+    for (int a = threadIdx.x; a < kc; a += blockDim.x) cd[a] = (T)av[a];
+    for (int j = threadIdx.x; j < Ld; j += blockDim.x) cd[kc + j] = (T)y2[j];
+    for (int e = threadIdx.x; e < (mt + 1) * kn; e += blockDim.x) {
+        const int i = e / kn, o = e % kn;
+        cC[i * kn + o] = (T)M_(Qc, ldh, i, o);
+    }
+    for (int e = threadIdx.x; e < mt * kn; e += blockDim.x) {
+        const int i = e / kn, o = e % kn;
+        const double sc = (i < kc) ? Dk[i] : 1.0;
+        cU[i * kn + o] = (T)(sc * M_(Pm, mt, i, o));
+    }
+    __syncthreads();
+    // ---- update pass (own rows): r, C_new, then d, U_new
+    T *rw = c.col(COL_RW), *dh = c.col(COL_DH);
+    const int knc = kn;   // new recycle dimension (0: keep the old C, U)
+    double nacc[1] = {0.0};
+    T tacc[1] = {T(0)};
+    for (long long p = c.lo + threadIdx.x; p < c.lo + c.cnt; p += blockDim.x) {
+        // sub-pass A: inputs C (kc) then V_0..V_Ld
+        T o[KMAX];
+#pragma unroll
+        for (int b = 0; b < KMAX; b++) o[b] = T(0);
+        T racc = rw[p];
+        for (int i = 0; i < kc + Ld + 1; i++) {
+            const T xv = c.col(cQ0 + i)[p];
+            if (i >= kc) racc -= cr[i - kc] * xv;
+            if (knc > 0) {
+#pragma unroll
+                for (int b = 0; b < KMAX; b++)
+                    if (b < knc) o[b] += xv * cC[i * knc + b];
+            }
+        }
+        rw[p] = racc;
+        tacc[0] += racc * racc;
+        if (knc > 0) {
+#pragma unroll
+            for (int b = 0; b < KMAX; b++)
+                if (b < knc) c.col(COL_C_END - knc + b)[p] = o[b];
+        }
+        // sub-pass B: inputs U (kc) then V_0..V_{Ld-1}
+#pragma unroll
+        for (int b = 0; b < KMAX; b++) o[b] = T(0);
+        T dacc = dh[p];
+        for (int i = 0; i < kc + Ld; i++) {
+            const T xv = (i < kc) ? c.col(COL_U0 + i)[p] : c.col(COL_V0 + (i - kc))[p];
+            dacc += cd[i] * xv;
+            if (knc > 0) {
+#pragma unroll
+                for (int b = 0; b < KMAX; b++)
+                    if (b < knc) o[b] += xv * cU[i * knc + b];
+            }
+        }
+        dh[p] = dacc;
+        if (knc > 0) {
+#pragma unroll
+            for (int b = 0; b < KMAX; b++)
+                if (b < knc) c.col(COL_U0 + b)[p] = o[b];
+        }
+    }
+    (void)nacc;
+    block_sum<1>(tacc, 1, reinterpret_cast<T *>(c.D(c.P.o_wsum)), c.template red<T>());
+    allreduce<T, T>(c, 1);
+    c.bytes += (unsigned long long)c.g.n * sizeof(T) *
+               ((kc + Ld + 1) + (kc + Ld) + 4 + 2 * knc);
+    if (knc > 0) c.kc = knc;
+    c.cycles += 1;
+    return sqrt((double)c.template vals<T>()[0]);
+}
+
+// ------------------------------------------------------------------ one system
+
+template <typename T>
+__device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx) {
+    const DevSystem sys = a.systems[sysidx];
+    const unsigned long long t0 = global_ns();
+    c.g = make_geom(sys.fmt, sys.nx, sys.ny, sys.nz);
+    const long long chunk = (((c.g.n + c.cs - 1) / c.cs) + 7) / 8 * 8;
+    c.lo = (long long)c.rank * chunk;
+    c.cnt = chunk;
+    c.steps = c.cycles = c.matvecs = c.refinements = 0;
+    c.breakdown = false;
+    assemble_system(c, sys);
+    // refresh the carried recycle space against the new operator (App. B.1)
+    if (c.kc > 0) {
+        cl_sync();   // U halo from the previous system
+        refresh_recycle(c);
+    }
+    const long long hi = c.lo + c.cnt;
+    // ||b||
+    double bacc[1] = {0.0};
+    for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
+        c.x[p] = 0.0;
+        const double bv = c.b[p];
+        c.r[p] = bv;
+        bacc[0] += bv * bv;
+    }
+    block_sum<1>(bacc, 1, c.D(c.P.o_wsum), c.template red<double>());
+    allreduce<T, double>(c, 1);
+    const double bnorm = sqrt(c.template vals<double>()[0]);
+    const bool fp64 = sizeof(T) == 8;
+    double rnorm = bnorm;
+    int flag = SKR_NOT_CONVERGED;
+    for (int it = 0;; it++) {
+        if (it > 0) rnorm = true_residual(c);
+        if (isnan(rnorm) || isinf(rnorm)) {
+            flag = SKR_NUMERICAL;
+            break;
+        }
+        if (rnorm <= a.tol * bnorm) {
+            flag = SKR_CONVERGED;
+            break;
+        }
+        if (it >= a.max_refine || c.steps >= c.maxit) {
+            flag = c.breakdown ? SKR_BREAKDOWN : SKR_NOT_CONVERGED;
+            break;
+        }
+        const double target = fp64 ? a.tol * bnorm : fmax(a.inner_tol * rnorm, a.tol * bnorm);
+        // inner system A M^-1 d = r in working precision
+        T *rw = c.col(COL_RW), *dh = c.col(COL_DH);
+        for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
+            rw[p] = (T)c.r[p];
+            dh[p] = T(0);
+        }
+        __syncthreads();
+        double rnw = rnorm;
+        for (;;) {
+            if (c.kc > 0) rnw = project_recycle(c);
+            if (!(rnw > target) || c.steps >= c.maxit) break;
+            rnw = run_cycle(c, rnw, target);
+            if (isnan(rnw)) break;
+        }
+        // x += M^-1 d
+        for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x)
+            c.x[p] += c.dinv[p] * (double)dh[p];
+        __syncthreads();
+        c.refinements += 1;
+        c.bytes += (unsigned long long)c.g.n * (8 * 3 + sizeof(T));
+    }
+    // write the solution
+    for (long long p = c.lo + threadIdx.x; p < min(hi, c.g.n); p += blockDim.x) sys.x_out[p] = c.x[p];
+    c.bytes += (unsigned long long)c.g.n * 16;
+    cl_sync();
+    if (c.rank == 0 && threadIdx.x == 0) {
+        DevResult res;
+        res.steps = c.steps;
+        res.cycles = c.cycles;
+        res.matvecs = c.matvecs;
+        res.refinements = c.refinements;
+        res.flag = flag;
+        res.k_final = c.kc;
+        res.relres = (bnorm > 0.0) ? rnorm / bnorm : 0.0;
+        res.t_begin = t0;
+        res.t_end = global_ns();
+        a.results[sysidx] = res;
+        if (a.bytes) atomicAdd(a.bytes, c.bytes);
+    }
+    c.bytes = 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) chain_kernel(const ChainArgs a) {
+    extern __shared__ __align__(16) double smem_dyn[];
+    Ctx<T> c;
+    c.rank = cl_rank();
+    c.cs = cl_size();
+    const int slot = blockIdx.x / c.cs;
+    c.P = make_plan(a.m, a.k, blockDim.x);
+    c.sm = smem_dyn;
+    c.parity = 0;
+    c.m = a.m;
+    c.k = a.k;
+    c.maxit = a.maxit;
+    c.precond = a.precond;
+    c.ld = a.ws.ld;
+    c.basis = reinterpret_cast<T *>(a.ws.basis) + (long long)slot * NCOLS * c.ld;
+    c.A64 = a.ws.A64 + (long long)slot * 7 * c.ld;
+    c.Aw = reinterpret_cast<T *>(a.ws.Aw) + (long long)slot * 7 * c.ld;
+    c.dinv = a.ws.dinv + (long long)slot * c.ld;
+    c.x = a.ws.x + (long long)slot * c.ld;
+    c.r = a.ws.r + (long long)slot * c.ld;
+    c.b = a.ws.b + (long long)slot * c.ld;
+    c.anode = a.ws.anode + (long long)slot * a.ws.nodecap;
+    c.bytes = 0;
+    int *ictl = c.ints();
+    for (;;) {
+        if (c.rank == 0 && threadIdx.x == 0) ictl[0] = atomicAdd(a.chain_counter, 1);
+        cl_sync();
+        const int chain = *cl_map(&ictl[0], 0);
+        cl_sync();
+        if (chain >= a.nchains) break;
+        c.kc = 0;
+        for (long long pos = a.chain_off[chain]; pos < a.chain_off[chain + 1]; pos++)
+            solve_system(c, a, a.order[pos]);
+    }
+}
+
+}  // namespace skr

@@ -1,0 +1,74 @@
+// Internal descriptors shared by the host side of the library and its
+// kernels.  Nothing here is part of the public ABI (include/skr.h).
+#pragma once
+
+#include <stdint.h>
+
+#include "../../include/skr.h"
+
+namespace skr {
+
+constexpr int MMAX = SKR_MAX_M;   // restart length capacity
+constexpr int KMAX = SKR_MAX_K;   // recycle dimension capacity
+constexpr int LDH = MMAX + 1;     // leading dimension of the small FP64 matrices
+
+// Column layout of a slot's basis slab (working precision, column stride ld):
+//   [0, KMAX)                 C_k, right-aligned: columns KMAX-kc .. KMAX-1
+//   [KMAX, KMAX+MMAX+1)       V_1 .. V_{MMAX+1}
+//   [UB, UB+KMAX)             U_k
+//   Y0, Y1                    ping-pong scratch for the Arnoldi vector w
+//   RW                        inner residual (working precision)
+//   DH                        inner correction d (working precision)
+// C directly precedes V, so [C_k, V_1..V_j] is one contiguous column range.
+constexpr int COL_C_END = KMAX;
+constexpr int COL_V0 = KMAX;
+constexpr int COL_U0 = KMAX + MMAX + 1;
+constexpr int COL_Y0 = COL_U0 + KMAX;
+constexpr int COL_Y1 = COL_Y0 + 1;
+constexpr int COL_RW = COL_Y0 + 2;
+constexpr int COL_DH = COL_Y0 + 3;
+constexpr int NCOLS = COL_Y0 + 4;
+
+// One system as the kernels see it (device pointers).
+struct DevSystem {
+    int fmt, nx, ny, nz;
+    const double *coef;
+    const double *rhs;
+    double params[4];
+    double *x_out;
+};
+
+// Per-system outcome written by the kernel (mirrors skr_result).
+struct DevResult {
+    int steps, cycles, matvecs, refinements, flag, k_final;
+    double relres;
+    unsigned long long t_begin, t_end;
+};
+
+// Device workspace: one region per slot (cluster in flight).
+struct Workspace {
+    void *basis;              // NCOLS * ld elements of T per slot
+    double *A64;              // 7 * ld doubles per slot (unfolded matrix)
+    void *Aw;                 // 7 * ld elements of T per slot (right-preconditioned operator)
+    double *dinv;             // ld per slot (Jacobi: 1/diag, else 1)
+    double *x, *r, *b;        // ld per slot each (FP64 solution, residual, rhs)
+    double *anode;            // node scratch per slot (exp(log a)), nodecap doubles
+    long long ld;             // column stride (elements), multiple of 64
+    long long nodecap;        // node scratch capacity per slot
+    int nslots;
+};
+
+struct ChainArgs {
+    const DevSystem *systems;
+    const int *order;
+    const long long *chain_off;   // nchains + 1
+    int nchains;
+    int *chain_counter;           // dynamic chain assignment (zeroed by the host)
+    Workspace ws;
+    DevResult *results;
+    int m, k, maxit, max_refine, precond;
+    double tol, inner_tol;
+    unsigned long long *bytes;    // algorithmic bytes counter (optional)
+};
+
+}  // namespace skr

@@ -1,0 +1,55 @@
+// Stand-alone kernels for the operator entry points (skr_assemble,
+// skr_apply).  They call the same row functions as the chain kernel, on a
+// plain grid without clusters.
+#pragma once
+
+#include "skr_common.h"
+#include "skr_stencil.cuh"
+
+namespace skr {
+
+__global__ void node_exp_kernel(const double *__restrict__ loga, long long nn, double *__restrict__ anode) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nn;
+         q += (long long)gridDim.x * blockDim.x)
+        anode[q] = exp(loga[q]);
+}
+
+// A (nst arrays, stride ld), b, dinv (Jacobi or 1).
+__global__ void rows_kernel(DevSystem sys, Geom g, const double *anode, double *A, long long ld,
+                            double *b, double *dinv, int precond) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n;
+         p += (long long)gridDim.x * blockDim.x) {
+        double row[7];
+        system_row(sys, g, anode, p, row);
+        for (int s = 0; s < g.nst; s++) A[(long long)s * ld + p] = row[s];
+        if (b) b[p] = sys.rhs ? sys.rhs[p] : 1.0;
+        if (dinv) dinv[p] = (precond == SKR_PC_JACOBI) ? 1.0 / row[0] : 1.0;
+    }
+}
+
+template <typename T>
+__global__ void fold_kernel(Geom g, const double *A, long long ld, const double *dinv, T *Aw) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n;
+         p += (long long)gridDim.x * blockDim.x) {
+        for (int s = 0; s < g.nst; s++) {
+            const long long q = nb_index(g, p, s);
+            Aw[(long long)s * ld + p] = (T)(A[(long long)s * ld + p] * dinv[q]);
+        }
+    }
+}
+
+template <typename T>
+__global__ void to_working_kernel(const double *v, long long n, T *out) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x)
+        out[p] = (T)v[p];
+}
+
+template <typename T>
+__global__ void apply_kernel(Geom g, const T *Aw, long long ld, const T *v, double *y) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n;
+         p += (long long)gridDim.x * blockDim.x)
+        y[p] = (double)stencil_apply_row(g, Aw, ld, v, T(1), p);
+}
+
+}  // namespace skr

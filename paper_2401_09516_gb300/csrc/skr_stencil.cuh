@@ -1,0 +1,179 @@
+// Finite-difference assembly and the stencil operator (Sec. 3.1, App. A.2).
+//
+// A matrix row p holds NST = 5 (2D) or 7 (3D) coefficients, stored as NST
+// arrays of length ld ("structure of arrays"): slot 0 is the diagonal, then
+// the minus/plus neighbours along x, y (and z).  Unknowns are row-major with
+// the last grid index fastest (p = i*ny + j in 2D, as in the paper's 2x2
+// example), so the x neighbours are +-ny apart and the y neighbours +-1.
+// Couplings to boundary nodes (Dirichlet u = 0) are stored as zeros, which
+// lets the operator read a clamped, always-valid index without branches.
+#pragma once
+
+#include "skr_common.h"
+#include "skr_device.cuh"
+
+namespace skr {
+
+struct Geom {
+    int nx, ny, nz;      // interior grid (nz = 1 in 2D)
+    int nst;             // 5 or 7
+    long long n;         // unknowns
+    long long off[7];    // neighbour offsets by slot (off[0] = 0)
+};
+
+__host__ __device__ inline Geom make_geom(int fmt, int nx, int ny, int nz) {
+    Geom g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = (fmt == SKR_FMT_DARCY3D || fmt == SKR_FMT_STENCIL7) ? nz : 1;
+    g.nst = (fmt == SKR_FMT_DARCY3D || fmt == SKR_FMT_STENCIL7) ? 7 : 5;
+    g.n = (long long)nx * ny * g.nz;
+    const long long sx = (long long)ny * g.nz, sy = g.nz;
+    g.off[0] = 0;
+    g.off[1] = -sx;
+    g.off[2] = sx;
+    g.off[3] = -sy;
+    g.off[4] = sy;
+    g.off[5] = -1;
+    g.off[6] = 1;
+    return g;
+}
+
+// Neighbour index for slot s, clamped to p when outside [0, n).  The
+// coefficient of an outside (boundary) neighbour is zero.
+__device__ __forceinline__ long long nb_index(const Geom &g, long long p, int s) {
+    long long q = p + g.off[s];
+    return (q < 0 || q >= g.n) ? p : q;
+}
+
+// ---------------------------------------------------------------- assembly
+
+// Darcy -div(a grad u) = f, flux form, face value = mean of the two nodes
+// (2D or 3D).  anode: exp(log a) at all (nx+2)(ny+2)[(nz+2)] nodes, read
+// through L2 because other CTAs of the cluster wrote it.
+__device__ __forceinline__ void darcy_row(const Geom &g, const double *anode, long long p,
+                                          double *c /* [7] */) {
+    if (g.nst == 5) {
+        const long long i = p / g.ny, j = p - i * g.ny;
+        const long long W = g.ny + 2;
+        const long long q = (i + 1) * W + (j + 1);
+        const double ac = __ldcg(anode + q);
+        const double hx = 1.0 / (double)(g.nx + 1), hy = 1.0 / (double)(g.ny + 1);
+        const double hx2 = hx * hx, hy2 = hy * hy;
+        const double fxm = 0.5 * (ac + __ldcg(anode + q - W)) / hx2;
+        const double fxp = 0.5 * (ac + __ldcg(anode + q + W)) / hx2;
+        const double fym = 0.5 * (ac + __ldcg(anode + q - 1)) / hy2;
+        const double fyp = 0.5 * (ac + __ldcg(anode + q + 1)) / hy2;
+        c[0] = fxm + fxp + fym + fyp;
+        c[1] = (i > 0) ? -fxm : 0.0;
+        c[2] = (i < g.nx - 1) ? -fxp : 0.0;
+        c[3] = (j > 0) ? -fym : 0.0;
+        c[4] = (j < g.ny - 1) ? -fyp : 0.0;
+    } else {
+        const long long nyz = (long long)g.ny * g.nz;
+        const long long i = p / nyz, rem = p - i * nyz, j = rem / g.nz, l = rem - j * g.nz;
+        const long long Wz = g.nz + 2, Wy = (long long)(g.ny + 2) * Wz;
+        const long long q = (i + 1) * Wy + (j + 1) * Wz + (l + 1);
+        const double ac = __ldcg(anode + q);
+        const double hx = 1.0 / (double)(g.nx + 1), hy = 1.0 / (double)(g.ny + 1),
+                     hz = 1.0 / (double)(g.nz + 1);
+        const double hx2 = hx * hx, hy2 = hy * hy, hz2 = hz * hz;
+        const double fxm = 0.5 * (ac + __ldcg(anode + q - Wy)) / hx2;
+        const double fxp = 0.5 * (ac + __ldcg(anode + q + Wy)) / hx2;
+        const double fym = 0.5 * (ac + __ldcg(anode + q - Wz)) / hy2;
+        const double fyp = 0.5 * (ac + __ldcg(anode + q + Wz)) / hy2;
+        const double fzm = 0.5 * (ac + __ldcg(anode + q - 1)) / hz2;
+        const double fzp = 0.5 * (ac + __ldcg(anode + q + 1)) / hz2;
+        c[0] = fxm + fxp + fym + fyp + fzm + fzp;
+        c[1] = (i > 0) ? -fxm : 0.0;
+        c[2] = (i < g.nx - 1) ? -fxp : 0.0;
+        c[3] = (j > 0) ? -fym : 0.0;
+        c[4] = (j < g.ny - 1) ? -fyp : 0.0;
+        c[5] = (l > 0) ? -fzm : 0.0;
+        c[6] = (l < g.nz - 1) ? -fzp : 0.0;
+    }
+}
+
+// -nu lap u + beta . grad u = f with first-order upwinding (2D).
+__device__ __forceinline__ void convdiff_row(const Geom &g, const double *prm, long long p,
+                                             double *c) {
+    const long long i = p / g.ny, j = p - i * g.ny;
+    const double hh = 1.0 / (double)(g.nx + 1);
+    const double nu = prm[0], bx = prm[1], by = prm[2];
+    const double d = nu / (hh * hh);
+    const double cxm = -d - fmax(bx, 0.0) / hh;
+    const double cxp = -d + fmin(bx, 0.0) / hh;
+    const double cym = -d - fmax(by, 0.0) / hh;
+    const double cyp = -d + fmin(by, 0.0) / hh;
+    c[0] = 4.0 * d + fabs(bx) / hh + fabs(by) / hh;
+    c[1] = (i > 0) ? cxm : 0.0;
+    c[2] = (i < g.nx - 1) ? cxp : 0.0;
+    c[3] = (j > 0) ? cym : 0.0;
+    c[4] = (j < g.ny - 1) ? cyp : 0.0;
+}
+
+// Assembled-input formats: copy the row, zeroing couplings that leave the grid.
+__device__ __forceinline__ void stencil_input_row(const Geom &g, const double *coef, long long p,
+                                                  double *c) {
+    for (int s = 0; s < g.nst; s++) c[s] = coef[(long long)s * g.n + p];
+    if (g.nst == 5) {
+        const long long i = p / g.ny, j = p - i * g.ny;
+        if (i == 0) c[1] = 0.0;
+        if (i == g.nx - 1) c[2] = 0.0;
+        if (j == 0) c[3] = 0.0;
+        if (j == g.ny - 1) c[4] = 0.0;
+    } else {
+        const long long nyz = (long long)g.ny * g.nz;
+        const long long i = p / nyz, rem = p - i * nyz, j = rem / g.nz, l = rem - j * g.nz;
+        if (i == 0) c[1] = 0.0;
+        if (i == g.nx - 1) c[2] = 0.0;
+        if (j == 0) c[3] = 0.0;
+        if (j == g.ny - 1) c[4] = 0.0;
+        if (l == 0) c[5] = 0.0;
+        if (l == g.nz - 1) c[6] = 0.0;
+    }
+}
+
+__device__ __forceinline__ void system_row(const DevSystem &sys, const Geom &g,
+                                           const double *anode, long long p, double *c) {
+    if (sys.fmt == SKR_FMT_DARCY2D || sys.fmt == SKR_FMT_DARCY3D)
+        darcy_row(g, anode, p, c);
+    else if (sys.fmt == SKR_FMT_CONVDIFF2D)
+        convdiff_row(g, sys.params, p, c);
+    else
+        stencil_input_row(g, sys.coef, p, c);
+}
+
+__device__ __forceinline__ long long node_count(const DevSystem &sys, const Geom &g) {
+    if (sys.fmt == SKR_FMT_DARCY2D) return (long long)(g.nx + 2) * (g.ny + 2);
+    if (sys.fmt == SKR_FMT_DARCY3D) return (long long)(g.nx + 2) * (g.ny + 2) * (g.nz + 2);
+    return 0;
+}
+
+// ---------------------------------------------------------------- operator
+
+// y_p = sum_s Aw[s][p] * scale * src[nb_s(p)]  (working precision T).
+// src may have been written by other CTAs: read through L2.
+template <typename T>
+__device__ __forceinline__ T stencil_apply_row(const Geom &g, const T *Aw, long long ld,
+                                               const T *src, T scale, long long p) {
+    T acc = T(0);
+    for (int s = 0; s < g.nst; s++) {
+        const long long q = nb_index(g, p, s);
+        acc += Aw[(long long)s * ld + p] * (scale * __ldcg(src + q));
+    }
+    return acc;
+}
+
+// r_p = b_p - sum_s A[s][p] * x[nb_s(p)]  (FP64 true residual).
+__device__ __forceinline__ double residual_row(const Geom &g, const double *A, long long ld,
+                                               const double *b, const double *x, long long p) {
+    double acc = 0.0;
+    for (int s = 0; s < g.nst; s++) {
+        const long long q = nb_index(g, p, s);
+        acc += A[(long long)s * ld + p] * __ldcg(x + q);
+    }
+    return b[p] - acc;
+}
+
+}  // namespace skr

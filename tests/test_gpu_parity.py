@@ -1,0 +1,308 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import assembly, krylov, precond as oprecond, skr as oskr, sort as osort  # noqa: E402
+from workloads import convdiff2d_sequence, darcy2d_sequence, darcy3d_sequence  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def skr():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2401_09516_gb300 as m
+    return m
+
+
+DEV = "cuda:0"
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _stencil_from_csr(A, g_nx, g_ny, g_nz=1):
+    """Oracle CSR -> stencil arrays in the library layout (diag, x-, x+, y-, y+, z-, z+)."""
+    n = A.shape[0]
+    if g_nz == 1:
+        offs = [0, -g_ny, g_ny, -1, 1]
+    else:
+        offs = [0, -g_ny * g_nz, g_ny * g_nz, -g_nz, g_nz, -1, 1]
+    out = np.zeros((len(offs), n))
+    A = A.tocsr()
+    for p in range(n):
+        for q in range(A.indptr[p], A.indptr[p + 1]):
+            c = A.indices[q]
+            s = offs.index(c - p)
+            out[s, p] += A.data[q]
+    return out
+
+
+# ------------------------------------------------------------------ sort
+
+@pytest.mark.parametrize("N,p,seed", [(20, 34 * 34, 1), (57, 1000, 2), (1, 10, 3), (2, 3, 4)])
+def test_sort_bit_exact(skr, N, p, seed):
+    rng = np.random.default_rng(seed)
+    P = rng.standard_normal((N, p))
+    for start in sorted({0, N // 2, N - 1}):
+        got = skr.skr_sort(_dev(P), start=start).cpu().numpy().tolist()
+        assert got == osort.greedy_sort(P, start)
+        got_h = skr.skr_sort(P, start=start).tolist()
+        assert got_h == got
+
+
+def test_sort_ties_and_duplicates(skr):
+    rng = np.random.default_rng(8)
+    P = rng.integers(-2, 3, size=(40, 7)).astype(np.float64)   # many exact ties
+    P[13] = P[5]
+    P[29] = P[5]
+    for start in (0, 5, 39):
+        assert skr.skr_sort(_dev(P), start=start).cpu().numpy().tolist() == osort.greedy_sort(P, start)
+
+
+def test_sort_full_size_darcy256(skr):
+    L = darcy2d_sequence(256, 200, 0.1, seed=2)
+    P = L.reshape(200, -1)
+    got = skr.skr_sort(_dev(P)).cpu().numpy().tolist()
+    assert got == osort.greedy_sort(P, 0)
+
+
+def test_sort_rejects_non_finite(skr):
+    P = np.ones((4, 3))
+    P[2, 1] = np.nan
+    with pytest.raises(skr.SkrError):
+        skr.skr_sort(_dev(P))
+
+
+# ------------------------------------------------------------------ assembly and operator
+
+@pytest.mark.parametrize("nx,ny", [(2, 2), (13, 11), (64, 64)])
+def test_assemble_darcy2d(skr, nx, ny):
+    rng = np.random.default_rng(nx)
+    loga = rng.standard_normal((nx + 2, ny + 2))
+    A, b = assembly.darcy2d(loga)
+    want = _stencil_from_csr(A, nx, ny)
+    coef, rhs = skr.skr_assemble(skr.darcy2d(_dev(loga)))
+    np.testing.assert_allclose(coef.cpu().numpy(), want, rtol=1e-13, atol=1e-13 * np.abs(want).max())
+    np.testing.assert_array_equal(rhs.cpu().numpy(), b)
+
+
+def test_assemble_darcy2d_unit_coefficient_is_minus_paper_matrix(skr):
+    # a = 1 on a 2x2 grid: the paper's Sec. 3.1 matrix times -1/h^2, h = 1/3
+    coef, _ = skr.skr_assemble(skr.darcy2d(_dev(np.zeros((4, 4)))))
+    A = np.zeros((4, 4))
+    offs = [0, -2, 2, -1, 1]
+    c = coef.cpu().numpy()
+    for s, o in enumerate(offs):
+        for p in range(4):
+            if 0 <= p + o < 4 and c[s, p] != 0:
+                A[p, p + o] = c[s, p]
+    paper = np.array([[-4, 1, 1, 0], [1, -4, 0, 1], [1, 0, -4, 1], [0, 1, 1, -4]], dtype=float)
+    np.testing.assert_allclose(A, -paper * 9.0, rtol=1e-15)
+
+
+def test_assemble_darcy3d(skr):
+    loga = darcy3d_sequence(6, 1, 0.2, seed=3, pad_factor=2)[0]
+    A, b = assembly.darcy3d(loga)
+    want = _stencil_from_csr(A, 6, 6, 6)
+    coef, rhs = skr.skr_assemble(skr.darcy3d(_dev(loga)))
+    np.testing.assert_allclose(coef.cpu().numpy(), want, rtol=1e-13, atol=1e-13 * np.abs(want).max())
+
+
+def test_assemble_convdiff_and_stencil_input(skr):
+    nu, beta, f = convdiff2d_sequence(12, 1, seed=4)
+    A, b = assembly.convdiff2d(nu[0], beta[0], 12, rhs=f[0])
+    want = _stencil_from_csr(A, 12, 12)
+    coef, rhs = skr.skr_assemble(skr.convdiff2d(nu[0], beta[0], 12, rhs=_dev(f[0])))
+    np.testing.assert_allclose(coef.cpu().numpy(), want, rtol=1e-14, atol=1e-14 * np.abs(want).max())
+    np.testing.assert_array_equal(rhs.cpu().numpy(), b)
+    sysS = skr.System(skr._native.SKR_FMT_STENCIL5, 12, 12, 1, _dev(want))
+    coef2, _ = skr.skr_assemble(sysS)
+    np.testing.assert_array_equal(coef2.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("pc", ["none", "jacobi"])
+def test_apply_operator(skr, pc):
+    rng = np.random.default_rng(5)
+    nx, ny = 37, 29
+    loga = rng.standard_normal((nx + 2, ny + 2))
+    A, _ = assembly.darcy2d(loga)
+    M = oprecond.RightPreconditioner(A, pc)
+    v = rng.standard_normal(nx * ny)
+    want = A @ M.apply(v)
+    sysd = skr.darcy2d(_dev(loga))
+    y64 = skr.skr_apply(sysd, _dev(v), precond=pc, precision="fp64").cpu().numpy()
+    np.testing.assert_allclose(y64, want, rtol=1e-12, atol=1e-13 * np.abs(want).max())
+    y32 = skr.skr_apply(sysd, _dev(v), precond=pc, precision="mixed").cpu().numpy()
+    assert np.abs(y32 - want).max() <= 5e-6 * np.abs(want).max()
+
+
+# ------------------------------------------------------------------ solves
+
+def _check_solution(x_gpu, A, b, tol_res, x_ref=None, tol_err=None):
+    x = x_gpu.cpu().numpy() if hasattr(x_gpu, "cpu") else x_gpu
+    rr = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+    assert rr <= tol_res * 1.01, rr
+    if x_ref is not None:
+        err = np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref)
+        assert err <= tol_err, err
+
+
+@pytest.mark.parametrize("k", [0, 6])
+def test_solve_fp64_small_matches_oracle(skr, k):
+    L = darcy2d_sequence(16, 6, 0.2, seed=11)
+    order = osort.greedy_sort(L.reshape(6, -1))
+    systems = [skr.darcy2d(_dev(l)) for l in L]
+    opt = skr.skr_options_default(m=20, k=k, tol=1e-8, precond="none", precision="fp64")
+    xs, res = skr.skr_solve_sequence(systems, order=order, options=opt)
+    sysd = [dict(kind="darcy2d", loga=l) for l in L]
+    xo, info = oskr.solve_sequence(sysd, order, "none", 20, k, 1e-8)
+    for i in range(6):
+        A, b = assembly.darcy2d(L[i])
+        assert res[i]["flag"] == 0, res[i]
+        assert res[i]["relres"] <= 1e-8
+        xd = np.linalg.solve(A.toarray(), b)
+        _check_solution(xs[i], A, b, 1e-8, xd, 1e-6)
+        # same algorithm, different rounding: step counts agree closely
+        assert abs(res[i]["steps"] - info[i]["steps"]) <= max(3, 0.15 * info[i]["steps"]), \
+            (i, res[i]["steps"], info[i]["steps"])
+    if k > 0:
+        assert all(r["k_final"] > 0 for r in res)
+
+
+def test_solve_config_darcy32_fp64(skr):
+    """20 Darcy systems on a 32x32 grid, FP64, GCRO-DR(30, 10), no preconditioner."""
+    L = darcy2d_sequence(32, 20, 0.2, seed=1)
+    P = L.reshape(20, -1)
+    order = skr.skr_sort(_dev(P)).cpu().numpy().tolist()
+    assert order == osort.greedy_sort(P)
+    systems = [skr.darcy2d(_dev(l)) for l in L]
+    opt = skr.skr_options_default(m=30, k=10, tol=1e-8, precond="none", precision="fp64")
+    xs, res = skr.skr_solve_sequence(systems, order=order, options=opt)
+    sysd = [dict(kind="darcy2d", loga=l) for l in L]
+    xo, info = oskr.solve_sequence(sysd, order, "none", 30, 10, 1e-8)
+    tot_g = sum(r["steps"] for r in res)
+    tot_o = sum(i["steps"] for i in info)
+    assert abs(tot_g - tot_o) <= 0.1 * tot_o, (tot_g, tot_o)
+    for i in range(20):
+        A, b = assembly.darcy2d(L[i])
+        assert res[i]["flag"] == 0
+        _check_solution(xs[i], A, b, 1e-8, xo[i], 1e-6)
+
+
+def test_solve_mixed_jacobi_matches_oracle(skr):
+    L = darcy2d_sequence(48, 8, 0.1, seed=21)
+    order = osort.greedy_sort(L.reshape(8, -1))
+    systems = [skr.darcy2d(_dev(l)) for l in L]
+    opt = skr.skr_options_default(m=40, k=20, tol=1e-8, precond="jacobi", precision="mixed")
+    xs, res = skr.skr_solve_sequence(systems, order=order, options=opt)
+    sysd = [dict(kind="darcy2d", loga=l) for l in L]
+    xo, info = oskr.solve_sequence(sysd, order, "jacobi", 40, 20, 1e-12, precision="fp64")
+    for i in range(8):
+        A, b = assembly.darcy2d(L[i])
+        assert res[i]["flag"] == 0, res[i]
+        _check_solution(xs[i], A, b, 1e-8, xo[i], 1e-6)
+
+
+@pytest.mark.parametrize("cs", [1, 2, 3, 4, 8, 16])
+def test_cluster_sizes_agree(skr, cs):
+    # ragged grid: n = 13 * 11 = 143 is not a multiple of any tile
+    rng = np.random.default_rng(31)
+    L = [rng.standard_normal((15, 13)) * 0.5 for _ in range(3)]
+    systems = [skr.darcy2d(_dev(l)) for l in L]
+    opt = skr.skr_options_default(m=16, k=4, tol=1e-10, precond="jacobi", precision="fp64",
+                                  cluster_size=cs)
+    xs, res = skr.skr_solve_sequence(systems, options=opt)
+    for i in range(3):
+        A, b = assembly.darcy2d(L[i])
+        xd = np.linalg.solve(A.toarray(), b)
+        assert res[i]["flag"] == 0
+        _check_solution(xs[i], A, b, 1e-10, xd, 1e-8)
+
+
+def test_chains_slots_and_host_memory(skr):
+    L = darcy2d_sequence(20, 9, 0.2, seed=41)
+    order = osort.greedy_sort(L.reshape(9, -1))
+    opt = dict(m=20, k=6, tol=1e-9, precond="jacobi", precision="fp64")
+    sysd = [skr.darcy2d(_dev(l)) for l in L]
+    xa, ra = skr.skr_solve_sequence(sysd, order=order, nchains=3,
+                                    options=skr.skr_options_default(**opt))
+    xb, rb = skr.skr_solve_sequence(sysd, order=order, nchains=3,
+                                    options=skr.skr_options_default(max_slots=1, **opt))
+    sysh = [skr.darcy2d(l) for l in L]
+    xc, rc = skr.skr_solve_sequence(sysh, order=order, nchains=3,
+                                    options=skr.skr_options_default(**opt))
+    sysdd = [dict(kind="darcy2d", loga=l) for l in L]
+    xo, info = oskr.solve_sequence(sysdd, order, "jacobi", 20, 6, 1e-9, nchains=3)
+    for i in range(9):
+        A, b = assembly.darcy2d(L[i])
+        for x in (xa[i], xb[i], xc[i]):
+            _check_solution(x, A, b, 1e-9, xo[i], 1e-6)
+        # a chain's state does not depend on how many chains run at once
+        assert ra[i]["steps"] == rb[i]["steps"] == rc[i]["steps"]
+        np.testing.assert_array_equal(xa[i].cpu().numpy(), xb[i].cpu().numpy())
+        np.testing.assert_array_equal(xa[i].cpu().numpy(), xc[i])
+
+
+def test_convdiff_and_darcy3d_solves(skr):
+    nu, beta, f = convdiff2d_sequence(24, 3, seed=5)
+    systems = [skr.convdiff2d(nu[i], beta[i], 24, rhs=_dev(f[i])) for i in range(3)]
+    opt = skr.skr_options_default(m=30, k=8, tol=1e-8, precond="jacobi", precision="mixed")
+    xs, res = skr.skr_solve_sequence(systems, options=opt)
+    for i in range(3):
+        A, b = assembly.convdiff2d(nu[i], beta[i], 24, rhs=f[i])
+        xd = np.linalg.solve(A.toarray(), b)
+        assert res[i]["flag"] == 0
+        _check_solution(xs[i], A, b, 1e-8, xd, 1e-6)
+    L3 = darcy3d_sequence(10, 3, 0.2, seed=6)
+    systems = [skr.darcy3d(_dev(l)) for l in L3]
+    xs, res = skr.skr_solve_sequence(systems, options=opt)
+    for i in range(3):
+        A, b = assembly.darcy3d(L3[i])
+        import scipy.sparse.linalg as spla
+        xd = spla.spsolve(A.tocsc(), b)
+        assert res[i]["flag"] == 0
+        _check_solution(xs[i], A, b, 1e-8, xd, 1e-6)
+
+
+def test_single_system_and_identical_repeat(skr):
+    loga = darcy2d_sequence(24, 1, 0.2, seed=51)[0]
+    systems = [skr.darcy2d(_dev(loga))] * 3
+    opt = skr.skr_options_default(m=20, k=8, tol=1e-8, precond="none", precision="fp64")
+    xs, res = skr.skr_solve_sequence(systems, options=opt)
+    # recycling an exact invariant subspace of the same matrix (Sec. 5.1)
+    assert res[1]["steps"] < 0.75 * res[0]["steps"], [r["steps"] for r in res]
+    xs1, res1 = skr.skr_solve_sequence(systems[:1], options=opt)
+    assert res1[0]["steps"] == res[0]["steps"]
+
+
+def test_invalid_arguments(skr):
+    loga = np.zeros((6, 6))
+    s = [skr.darcy2d(_dev(loga))]
+    with pytest.raises(skr.SkrError):
+        skr.skr_solve_sequence(s, options=skr.skr_options_default(m=60))
+    with pytest.raises(skr.SkrError):
+        skr.skr_solve_sequence(s, options=skr.skr_options_default(m=10, k=9))
+    with pytest.raises(skr.SkrError):
+        skr.skr_solve_sequence(s, order=[1], options=skr.skr_options_default())
+    mixed = [skr.darcy2d(_dev(np.zeros((6, 6)))), skr.darcy2d(_dev(np.zeros((7, 7))))]
+    with pytest.raises(skr.SkrError):
+        skr.skr_solve_sequence(mixed, nchains=1, options=skr.skr_options_default())
+
+
+def test_zero_rhs_and_nan_input(skr):
+    loga = np.zeros((10, 10))
+    zero = np.zeros(64)
+    xs, res = skr.skr_solve_sequence([skr.darcy2d(_dev(loga), rhs=_dev(zero))],
+                                     options=skr.skr_options_default(m=10, k=2))
+    assert res[0]["flag"] == 0 and np.all(xs[0].cpu().numpy() == 0)
+    bad = np.zeros((10, 10))
+    bad[3, 4] = np.nan
+    xs, res = skr.skr_solve_sequence([skr.darcy2d(_dev(bad))], options=skr.skr_options_default(m=10, k=2))
+    assert res[0]["flag"] == 3

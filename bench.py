@@ -120,8 +120,10 @@ def run_gpu(args):
 
     W = WORKLOAD
     # weak scaling: every rank solves its own 200-system batch (independent chains)
-    L = darcy2d_sequence(W["nside"], W["nsys"], W["ell"], W["sigma"], seed=W["seed"] + 1000 * rank)
-    N = W["nsys"]
+    L = darcy2d_sequence(W["nside"], max(W["nsys"], args.nsys), W["ell"], W["sigma"],
+                         seed=W["seed"] + 1000 * rank)
+    N = args.nsys
+    L = L[:N]
     n = W["nside"] ** 2
     P_dev = torch.tensor(L.reshape(N, -1), device=dev)
     fields = [P_dev[i].view(W["nside"] + 2, W["nside"] + 2) for i in range(N)]
@@ -133,7 +135,7 @@ def run_gpu(args):
     def opts(k):
         return skr.skr_options_default(m=W["m"], k=k, tol=W["tol"], inner_tol=W["inner_tol"],
                                        precond=W["precond"], precision=W["precision"],
-                                       stream=stream)
+                                       cluster_size=args.cluster_size, stream=stream)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -169,7 +171,8 @@ def run_gpu(args):
     sampler.start()
     t_skr, st_skr, res_skr = timed(W["k"], args.steps, args.warmup)
     clocks = sampler.stop()
-    t_gm, st_gm, res_gm = timed(0, args.gmres_steps, 1)
+    if args.gmres_steps > 0:
+        t_gm, st_gm, res_gm = timed(0, args.gmres_steps, 1)
 
     def agg(ms_list):
         ms = max(ms_list) if ws == 1 else ms_list
@@ -180,9 +183,15 @@ def run_gpu(args):
         return sum(ms_list) / len(ms_list)
 
     ms_step = agg(t_skr)
-    ms_gm = agg(t_gm)
     value = N * ws / (ms_step / 1e3)
-    gm_value = N * ws / (ms_gm / 1e3)
+    if args.gmres_steps > 0:
+        ms_gm = agg(t_gm)
+        gm_value = N * ws / (ms_gm / 1e3)
+        steps_gm = sum(r["steps"] for r in res_gm[-1]) / N
+        gm_flags = sorted({r["flag"] for r in res_gm[-1]})
+    else:
+        ms_gm = gm_value = steps_gm = None
+        gm_flags = []
     # roofline of the dominant kernel (the chain kernel), measured per launch
     peak, peak_kind = _peaks()
     kbytes = sum(s["bytes"] for s in st_skr) / len(st_skr)
@@ -193,34 +202,38 @@ def run_gpu(args):
     flags = sorted({r["flag"] for r in res_skr[-1]})
     lat = sorted(r["seconds"] * 1e3 for r in res_skr[-1])
     steps_skr = sum(r["steps"] for r in res_skr[-1]) / N
-    steps_gm = sum(r["steps"] for r in res_gm[-1]) / N
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    Lh = [torch.from_numpy(np.ascontiguousarray(L[i])).pin_memory() for i in range(N)]
-    Ph = torch.from_numpy(np.ascontiguousarray(L.reshape(N, -1))).pin_memory()
-    xh = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(N)]
-    sys_h = [skr.darcy2d(Lh[i].numpy()) for i in range(N)]
-    xh_np = [x.numpy() for x in xh]
+    e2e = None
+    if args.e2e:
+        Lh = [torch.from_numpy(np.ascontiguousarray(L[i])).pin_memory() for i in range(N)]
+        Ph = torch.from_numpy(np.ascontiguousarray(L.reshape(N, -1))).pin_memory()
+        xh = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(N)]
+        sys_h = [skr.darcy2d(Lh[i].numpy()) for i in range(N)]
+        xh_np = [x.numpy() for x in xh]
 
-    def e2e_step():
-        perm = skr.skr_sort(Ph.numpy(), stream=stream)
-        skr.skr_solve_sequence(sys_h, order=perm, nchains=nchains, options=opts(W["k"]), x_out=xh_np)
+        def e2e_step():
+            perm = skr.skr_sort(Ph.numpy(), stream=stream)
+            skr.skr_solve_sequence(sys_h, order=perm, nchains=nchains, options=opts(W["k"]),
+                                   x_out=xh_np)
 
-    e2e_step()
-    torch.cuda.synchronize()
-    e2e_ms = []
-    for _ in range(max(1, args.steps)):
-        flush.zero_()
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
         e2e_step()
         torch.cuda.synchronize()
-        barrier()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_val = N * ws / (agg(e2e_ms) / 1e3)
-    h2d = Ph.numel() * 8 + sum(t.numel() for t in Lh) * 8
-    d2h = N * n * 8 + N * 4
+        e2e_ms = []
+        for _ in range(max(1, args.steps)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            barrier()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e_val = N * ws / (agg(e2e_ms) / 1e3)
+        h2d = Ph.numel() * 8 + sum(t.numel() for t in Lh) * 8
+        d2h = N * n * 8 + N * 4
+        e2e = {"value": round(e2e_val, 3), "unit": "systems/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
 
     line = {
         "metric": METRIC,
@@ -236,17 +249,18 @@ def run_gpu(args):
         "dtype": "f32+f64",
         "data": "synthetic",
         "config": {
-            "workload": "darcy2d 256x256 (n=65536), 200 systems, a=exp(GRF ell=0.1 sigma=1), f=1, "
-                        "Jacobi, GCRO-DR m=40 k=20, mixed precision, tol 1e-8",
+            "workload": "darcy2d 256x256 (n=65536), %d systems, a=exp(GRF ell=0.1 sigma=1), f=1, "
+                        "Jacobi, GCRO-DR m=40 k=20, mixed precision, tol 1e-8" % N,
             "chains": nchains, "cluster_size": st_skr[-1]["cluster_size"],
             "slots": st_skr[-1]["slots"], "l2": "flushed between steps (256 MB write)",
             "parallelism": "replicas" if ws > 1 else "single GPU",
         },
-        "gmres_value": round(gm_value, 3),
-        "gmres_ms_per_step": round(ms_gm, 3),
-        "speedup_vs_gmres": round(value / gm_value, 3),
+        "gmres_value": None if gm_value is None else round(gm_value, 3),
+        "gmres_ms_per_step": None if ms_gm is None else round(ms_gm, 3),
+        "speedup_vs_gmres": None if gm_value is None else round(value / gm_value, 3),
         "avg_steps_skr": round(steps_skr, 1),
-        "avg_steps_gmres": round(steps_gm, 1),
+        "avg_steps_gmres": None if steps_gm is None else round(steps_gm, 1),
+        "gmres_flags": gm_flags,
         "max_relres": relmax,
         "flags": flags,
         "latency_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3)},
@@ -254,8 +268,7 @@ def run_gpu(args):
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                      "kernel": "chain_kernel<float>", "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": int(kbytes), "kernel_ms": round(kms, 3)},
-        "e2e": {"value": round(e2e_val, 3), "unit": "systems/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+        "e2e": e2e,
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }
@@ -322,8 +335,11 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="skr", choices=["skr", "reference"])
-    ap.add_argument("--chains", type=int, default=20, help="independent chains the sorted order is cut into")
+    ap.add_argument("--chains", type=int, default=76, help="independent chains the sorted order is cut into")
+    ap.add_argument("--cluster-size", type=int, default=2, help="CTAs per chain (thread-block cluster)")
+    ap.add_argument("--nsys", type=int, default=200, help="systems per batch (200 = the full workload)")
     ap.add_argument("--gmres-steps", type=int, default=1)
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=20.0)

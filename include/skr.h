@@ -104,7 +104,7 @@ typedef struct skr_options {
     int32_t cluster_size;   /* CTAs cooperating on one system, 1..16 (0 = chosen from n) */
     int32_t max_slots;      /* chains in flight at once (0 = as many as fit on the GPU) */
     int32_t mem;            /* SKR_MEM_DEVICE or SKR_MEM_HOST */
-    int32_t reserved;
+    int32_t profile;        /* nonzero: accumulate device time per phase (skr_last_profile) */
     void   *stream;         /* cudaStream_t */
 } skr_options;
 
@@ -195,6 +195,16 @@ skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t precision,
  */
 skr_status skr_last_stats(uint64_t *bytes, double *kernel_ms, int32_t *cluster_size,
                           int32_t *slots, int32_t *launches);
+
+/*
+ * skr_last_profile -- device time per phase of the last skr_solve_sequence
+ * call made with opt->profile != 0, summed over all clusters (rank-0 CTA
+ * clocks, globaltimer): ns_out[i] for phase i < min(nphase, SKR_NPHASE),
+ * in the order assembly, refresh, projection, operator, multi-dot, update,
+ * gram, dense, cycle-update, true-residual, other.
+ */
+#define SKR_NPHASE 11
+skr_status skr_last_profile(double *ns_out, int32_t nphase);
 
 /* Free the device workspace cached by skr_solve_sequence (all devices). */
 skr_status skr_release_workspace(void);

@@ -57,7 +57,7 @@ class SkrOptions(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("precond", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
                 ("max_slots", ctypes.c_int32), ("mem", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class SkrResult(ctypes.Structure):
@@ -87,11 +87,12 @@ _lib.skr_assemble.argtypes = [ctypes.POINTER(SkrSystem), _i32, _vp, _vp, _vp]
 _lib.skr_apply.argtypes = [ctypes.POINTER(SkrSystem), _i32, _i32, _vp, _vp, _i32, _vp]
 _lib.skr_last_stats.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
+_lib.skr_last_profile.argtypes = [ctypes.POINTER(ctypes.c_double), _i32]
 _lib.skr_release_workspace.argtypes = []
 _lib.skr_last_error.argtypes = []
 _lib.skr_last_error.restype = ctypes.c_char_p
 for _fn in ("skr_options_default", "skr_sort", "skr_solve_sequence", "skr_assemble", "skr_apply",
-            "skr_last_stats", "skr_release_workspace"):
+            "skr_last_stats", "skr_last_profile", "skr_release_workspace"):
     getattr(_lib, _fn).restype = ctypes.c_int32
 
 
@@ -293,6 +294,17 @@ def skr_last_stats():
             "launches": ln.value}
 
 
+PHASES = ["assembly", "refresh", "projection", "operator", "multidot", "update", "gram", "dense",
+          "cycle_update", "true_residual", "other"]
+
+
+def skr_last_profile():
+    """Per-phase device time (ms) of the last profiled skr_solve_sequence call."""
+    arr = (ctypes.c_double * len(PHASES))()
+    _check(_lib.skr_last_profile(arr, len(PHASES)))
+    return {name: arr[i] * 1e-6 for i, name in enumerate(PHASES)}
+
+
 def skr_release_workspace():
     _check(_lib.skr_release_workspace())
 
@@ -300,7 +312,7 @@ def skr_release_workspace():
 def exported_symbols():
     """Names of the C functions this binding wraps."""
     return ["skr_options_default", "skr_sort", "skr_solve_sequence", "skr_assemble", "skr_apply",
-            "skr_last_stats", "skr_release_workspace", "skr_last_error"]
+            "skr_last_stats", "skr_last_profile", "skr_release_workspace", "skr_last_error"]
 
 
 def library():

@@ -166,6 +166,7 @@ skr_status stage_system(const skr_system &s, int mem, cudaStream_t st, Staged &o
 }
 
 struct LastStats {
+    unsigned long long prof[SKR_NPHASE] = {0};
     unsigned long long bytes = 0;
     float kernel_ms = 0.f;
     int cluster_size = 0, slots = 0, launches = 0;
@@ -391,12 +392,12 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
 
     // launch geometry
     const bool fp64 = opt.precision == SKR_PREC_FP64;
-    const int threads = 512;
+    const int threads = chain_threads();
     int cs = opt.cluster_size;
     if (cs == 0) {
         cs = (int)std::min<long long>(8, std::max<long long>(1, (nmax + 8191) / 8192));
     }
-    const size_t smem = chain_smem_bytes(opt.m, opt.k, threads);
+    const size_t smem = chain_smem_bytes(opt.m, opt.k, threads, fp64 ? 8 : 4);
     if (smem > 227 * 1024) return fail(SKR_ERR_INVALID_ARG, "m, k too large for shared memory (%zu bytes)", smem);
     int maxc = fp64 ? max_active_clusters_f64(cs, threads, smem) : max_active_clusters_f32(cs, threads, smem);
     if (maxc < 1) return fail(SKR_ERR_CUDA, "cluster of %d CTAs with %zu bytes of shared memory cannot be scheduled", cs, smem);
@@ -450,11 +451,11 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     CUDA_TRY(dord.alloc(sizeof(int) * N));
     CUDA_TRY(doff.alloc(sizeof(long long) * (nchains + 1)));
     CUDA_TRY(dres.alloc(sizeof(DevResult) * N));
-    CUDA_TRY(dctr.alloc(64));
+    CUDA_TRY(dctr.alloc(64 + 8 * SKR_NPHASE));
     CUDA_TRY(cudaMemcpyAsync(dsys.p, hsys.data(), sizeof(DevSystem) * N, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(dord.p, ord.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(doff.p, off.data(), sizeof(long long) * (nchains + 1), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemsetAsync(dctr.p, 0, 64, st));
+    CUDA_TRY(cudaMemsetAsync(dctr.p, 0, 64 + 8 * SKR_NPHASE, st));
     CUDA_TRY(cudaMemsetAsync(dres.p, 0, sizeof(DevResult) * N, st));
 
     ChainArgs a;
@@ -483,6 +484,7 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     a.tol = opt.tol;
     a.inner_tol = opt.inner_tol;
     a.bytes = reinterpret_cast<unsigned long long *>(dctr.as<char>() + 32);
+    a.prof = opt.profile ? reinterpret_cast<unsigned long long *>(dctr.as<char>() + 64) : nullptr;
 
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
@@ -500,6 +502,8 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     unsigned long long hbytes = 0;
     CUDA_TRY(cudaMemcpyAsync(hres.data(), dres.p, sizeof(DevResult) * N, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(&hbytes, a.bytes, sizeof(hbytes), cudaMemcpyDeviceToHost, st));
+    unsigned long long hprof[SKR_NPHASE] = {0};
+    if (a.prof) CUDA_TRY(cudaMemcpyAsync(hprof, a.prof, sizeof(hprof), cudaMemcpyDeviceToHost, st));
     if (opt.mem == SKR_MEM_HOST) {
         for (long long i = 0; i < N; i++)
             CUDA_TRY(cudaMemcpyAsync(x_out[i], xstage[i].p, (size_t)sys_n(systems[i]) * 8,
@@ -524,6 +528,7 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
         r.seconds = (d.t_end >= d.t_begin) ? (double)(d.t_end - d.t_begin) * 1e-9 : 0.0;
     }
     g_last.bytes = hbytes;
+    for (int i = 0; i < SKR_NPHASE; i++) g_last.prof[i] = hprof[i];
     g_last.kernel_ms = ms;
     g_last.cluster_size = cs;
     g_last.slots = nslots;
@@ -538,6 +543,12 @@ skr_status skr_last_stats(uint64_t *bytes, double *kernel_ms, int32_t *cluster_s
     if (cluster_size) *cluster_size = g_last.cluster_size;
     if (slots) *slots = g_last.slots;
     if (launches) *launches = g_last.launches;
+    return SKR_OK;
+}
+
+skr_status skr_last_profile(double *ns_out, int32_t nphase) {
+    if (!ns_out || nphase < 0) return fail(SKR_ERR_INVALID_ARG, "bad arguments");
+    for (int i = 0; i < nphase && i < SKR_NPHASE; i++) ns_out[i] = (double)g_last.prof[i];
     return SKR_OK;
 }
 

@@ -25,6 +25,13 @@
 namespace skr {
 
 template <typename T> struct Tiles;
+// Threads per CTA of the chain kernel: 16 warps, one CTA per SM.  The
+// streaming passes issue 16-byte loads of up to 32 basis columns per row
+// group; measured on GB300 this keeps more bytes in flight than 8 warps
+// with more registers, or than register-resident one-element passes.
+constexpr int CHAIN_THREADS = 512;
+constexpr int CHAIN_MIN_BLOCKS = 1;
+
 template <> struct Tiles<float> {
     static constexpr int G = 32;   // columns per multi-dot group
     static constexpr int TA = 8;   // Gram tile rows
@@ -36,10 +43,32 @@ template <> struct Tiles<double> {
     static constexpr int TB = 8;
 };
 
+// Precision of the harmonic-Ritz eigen-solve: FP32 in the mixed form (the
+// eigenvectors only select the recycled subspace; M, G P_k, its QR and R^-1
+// stay FP64, so A U = C and C^T C = I hold to FP64 accuracy of the small
+// step), FP64 in the FP64 form.
+template <typename T> struct EigT { typedef double type; };
+template <> struct EigT<float> { typedef float type; };
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { typedef float2 type; };
+template <> struct Vec2<double> { typedef double2 type; };
+
+// four consecutive coefficients from shared memory (16-byte aligned)
+__device__ __forceinline__ void ld4(const float *p, float &a, float &b, float &c, float &d) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double &a, double &b, double &c, double &d) {
+    const double2 v0 = *reinterpret_cast<const double2 *>(p);
+    const double2 v1 = *reinterpret_cast<const double2 *>(p + 2);
+    a = v0.x; b = v0.y; c = v1.x; d = v1.y;
+}
+
 // Shared-memory layout, computed identically on host and device.
 struct SmemPlan {
     int m, k, nwarps;
-    int ldh, redcap;
+    int ldh, redcap, redsz;   // redsz: one reduction buffer, in doubles
     // offsets in doubles
     int o_red, o_vals, o_wsum, o_H, o_B, o_Rw, o_gvec, o_y2, o_gam, o_avec, o_gc, o_gs, o_dscr, o_F,
         o_Z, o_wr, o_wi, o_xr, o_xi, o_vscr, o_P, o_GP, o_Qc, o_Rc, o_tau, o_D, o_sc, o_Tco, o_mon,
@@ -50,7 +79,7 @@ struct SmemPlan {
 
 __host__ __device__ inline int align2(int x) { return (x + 1) & ~1; }
 
-__host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads) {
+__host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads, int esz) {
     SmemPlan P;
     P.m = m;
     P.k = k;
@@ -60,10 +89,11 @@ __host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads) {
     if ((m + 1) * k + 2 * k + 8 > rc) rc = (m + 1) * k + 2 * k + 8;
     if (k * k + 8 > rc) rc = k * k + 8;
     P.redcap = align2(rc);
+    P.redsz = align2((P.redcap * esz + 7) / 8);   // reductions are in the working precision
     const int kk = k + 1;
     int o = 0;
-    P.o_red = o;   o += 2 * P.redcap;
-    P.o_vals = o;  o += P.redcap;
+    P.o_red = o;   o += 2 * P.redsz;
+    P.o_vals = o;  o += P.redsz;
     P.o_wsum = o;  o += align2(P.nwarps * 32);
     P.o_H = o;     o += align2(P.ldh * m);
     P.o_B = o;     o += align2(k * m);
@@ -74,29 +104,39 @@ __host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads) {
     P.o_avec = o;  o += align2(k + 2);
     P.o_gc = o;    o += align2(m + 2);
     P.o_gs = o;    o += align2(m + 2);
-    P.o_dscr = o;  o += align2(m + 2);
+    P.o_dscr = o;  o += align2(2 * m + 4);
     P.o_F = o;     o += align2(P.ldh * (m > k ? m : k));   // F / M; also the refresh Gram
     P.o_Z = o;     o += align2(m * m > 2 * k * k ? m * m : 2 * k * k);  // Schur vectors; also R, R^-1
     P.o_wr = o;    o += align2(m);
     P.o_wi = o;    o += align2(m);
-    P.o_xr = o;    o += align2(kk * m > 64 ? kk * m : 64);   // also the Gram tile buffer
-    P.o_xi = o;    o += align2(kk * m);
     P.o_vscr = o;  o += align2(m + 2);
     P.o_P = o;     o += align2(m * kk);
-    P.o_GP = o;    o += align2(P.ldh * kk);
-    P.o_Qc = o;    o += align2(P.ldh * kk);
+    // G P_k and its Q factor are formed after the eigen-solve, when the F/M
+    // and R_H regions are free again
+    P.o_GP = P.o_F;
+    P.o_Qc = P.o_Rw;
     P.o_Rc = o;    o += align2(kk * kk);
     P.o_tau = o;   o += align2(kk + 1);
     P.o_D = o;     o += align2(k + 2);
     P.o_sc = o;    o += 16;
     // T coefficient region (sized in doubles: T is at most 8 bytes)
     P.t_h = 0;
-    P.t_cC = P.t_h + align2(m + 4);
-    P.t_cU = P.t_cC + align2((m + 1) * (k > 0 ? k : 1));
-    P.t_cr = P.t_cU + align2(m * (k > 0 ? k : 1));
+    P.t_cC = P.t_h + ((m + 4 + 3) & ~3);   // multiple of 4 elements: float4 loads
+    const int ks = ((k > 0 ? k : 1) + 3) & ~3;   // padded coefficient row stride
+    P.t_cU = P.t_cC + align2((m + 1) * ks);
+    P.t_cr = P.t_cU + align2(m * ks);
     P.t_cd = P.t_cr + align2(m + 2);
     P.t_total = P.t_cd + align2(m + k + 2);
-    P.o_Tco = o;   o += align2(P.t_total);
+    // the eigenvector workspace (xr, xi, in the eigen-solve precision, which
+    // has the working element size) and the Gram tile buffer live in the
+    // coefficient region: it is written only after the eigen-solve
+    const int xsz = align2((kk * m * esz + 7) / 8);
+    int tco = align2(P.t_total);
+    if (2 * xsz > tco) tco = 2 * xsz;
+    if (tco < 32) tco = 32;
+    P.o_Tco = o;   o += tco;
+    P.o_xr = P.o_Tco;
+    P.o_xi = P.o_Tco + xsz;
     P.o_mon = o;   o += align2(3 * m + 4);             // FP32 Givens monitor (as floats, room to spare)
     P.o_int = o;   o += align2(64 + 8 + 3 * MMAX);      // control ints
     P.total = o;
@@ -127,13 +167,25 @@ struct Ctx {
     int kc;
     // per-system statistics
     int steps, cycles, matvecs, refinements;
+    int updates_since_refresh;   // recycle updates since C = A U was last recomputed
     bool breakdown;
     unsigned long long bytes;
+    // optional per-phase device time (rank 0, thread 0)
+    unsigned long long *prof;
+    unsigned long long tmark;
+
+    __device__ __forceinline__ void tick(int ph) {
+        if (prof != nullptr && rank == 0 && threadIdx.x == 0) {
+            const unsigned long long t = global_ns();
+            atomicAdd(prof + ph, t - tmark);
+            tmark = t;
+        }
+    }
 
     __device__ T *col(int c) const { return basis + (long long)c * ld; }
     __device__ double *D(int off) const { return sm + off; }
     template <typename R>
-    __device__ R *red() const { return reinterpret_cast<R *>(sm + P.o_red + parity * P.redcap); }
+    __device__ R *red() const { return reinterpret_cast<R *>(sm + P.o_red + parity * P.redsz); }
     template <typename R>
     __device__ R *vals() const { return reinterpret_cast<R *>(sm + P.o_vals); }
     __device__ T *tco(int off) const { return reinterpret_cast<T *>(sm + P.o_Tco) + off; }
@@ -219,14 +271,81 @@ __device__ void update_rows(Ctx<T> &c, int c0, int q, const T *h, T *y, T *nrm_o
 // basis vector, if vout) and y = A M^-1 (s * src); padded rows get zeros.
 template <typename T>
 __device__ void spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
+    typedef typename Vec<T>::type VT;
+    constexpr int E = Vec<T>::N;
     const long long hi = c.lo + c.cnt;
-    for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
-        if (p < c.g.n) {
-            if (vout) vout[p] = s * __ldcg(src + p);
-            y[p] = stencil_apply_row(c.g, c.Aw, c.ld, src, s, p);
-        } else {
-            if (vout) vout[p] = T(0);
-            y[p] = T(0);
+    // the fastest grid index runs along the vector when its extent is a
+    // multiple of E: then the two neighbours along it come from the vector
+    // itself (plus one value at each end) and every other neighbour offset
+    // is a multiple of E, so all loads are 16-byte vectors
+    const int last = (c.g.nst == 5) ? c.g.ny : c.g.nz;
+    const int sL = (c.g.nst == 5) ? 3 : 5;   // slots of the -1 / +1 neighbours
+    if (last % E == 0) {
+        const long long n = c.g.n;
+        for (long long p = c.lo + (long long)E * threadIdx.x; p < hi; p += (long long)E * blockDim.x) {
+            if (p >= n) {
+                if (vout) *reinterpret_cast<VT *>(vout + p) = vzero(T(0));
+                *reinterpret_cast<VT *>(y + p) = vzero(T(0));
+                continue;
+            }
+            const VT xc = __ldcg(reinterpret_cast<const VT *>(src + p));
+            const T left = (p > 0) ? __ldcg(src + p - 1) : T(0);
+            const T right = (p + E < n) ? __ldcg(src + p + E) : T(0);
+            T xl[E], xr[E], xm[E];
+            {
+                const T *xa = reinterpret_cast<const T *>(&xc);
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    xm[e] = xa[e];
+                    xl[e] = (e == 0) ? left : xa[e - 1];
+                    xr[e] = (e == E - 1) ? right : xa[e + 1];
+                }
+            }
+            T acc[E];
+            {
+                const VT a0 = *reinterpret_cast<const VT *>(c.Aw + p);
+                const T *aa = reinterpret_cast<const T *>(&a0);
+#pragma unroll
+                for (int e = 0; e < E; e++) acc[e] = aa[e] * xm[e];
+            }
+            {
+                const VT am = *reinterpret_cast<const VT *>(c.Aw + (long long)sL * c.ld + p);
+                const VT ap = *reinterpret_cast<const VT *>(c.Aw + (long long)(sL + 1) * c.ld + p);
+                const T *a1 = reinterpret_cast<const T *>(&am);
+                const T *a2 = reinterpret_cast<const T *>(&ap);
+#pragma unroll
+                for (int e = 0; e < E; e++) acc[e] += a1[e] * xl[e] + a2[e] * xr[e];
+            }
+            for (int sl = 1; sl < c.g.nst; sl++) {
+                if (sl == sL || sl == sL + 1) continue;
+                const long long q = p + c.g.off[sl];
+                const VT xv = (q >= 0 && q < n) ? __ldcg(reinterpret_cast<const VT *>(src + q)) : xc;
+                const VT av = *reinterpret_cast<const VT *>(c.Aw + (long long)sl * c.ld + p);
+                const T *xa = reinterpret_cast<const T *>(&xv);
+                const T *aa = reinterpret_cast<const T *>(&av);
+#pragma unroll
+                for (int e = 0; e < E; e++) acc[e] += aa[e] * xa[e];
+            }
+            VT out, vv;
+            T *oa = reinterpret_cast<T *>(&out);
+            T *va = reinterpret_cast<T *>(&vv);
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                oa[e] = s * acc[e];
+                va[e] = s * xm[e];
+            }
+            if (vout) *reinterpret_cast<VT *>(vout + p) = vv;
+            *reinterpret_cast<VT *>(y + p) = out;
+        }
+    } else {
+        for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
+            if (p < c.g.n) {
+                if (vout) vout[p] = s * __ldcg(src + p);
+                y[p] = stencil_apply_row(c.g, c.Aw, c.ld, src, s, p);
+            } else {
+                if (vout) vout[p] = T(0);
+                y[p] = T(0);
+            }
         }
     }
     __syncthreads();
@@ -351,6 +470,8 @@ __device__ double true_residual(Ctx<T> &c) {
 // are FP64).  On a failed Cholesky the recycle space is dropped (kc = 0).
 template <typename T>
 __device__ void refresh_recycle(Ctx<T> &c) {
+    cl_sync();   // U of the neighbours (halo of the operator) must be complete
+    c.updates_since_refresh = 0;
     const int kc = c.kc;
     const int cC0 = COL_C_END - kc;
     // W = A M^-1 U into the C columns
@@ -509,6 +630,7 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
         T *y = c.col(ycur);
         // S: V_j = s * src; y = A M^-1 V_j; dots [C, V_0..V_j] . y and y . y
         spmv_pass(c, src, s, c.col(COL_V0 + j), y);
+        c.tick(PH_SPMV);
         const int q = kc + j + 1;
         part_multidot(c, cQ0, q, y, c.template red<T>());
         {
@@ -522,6 +644,7 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
             block_sum<1>(acc, 1, reinterpret_cast<T *>(c.D(c.P.o_wsum)), c.template red<T>() + q);
         }
         allreduce<T, T>(c, q + 1);
+        c.tick(PH_DOT);
         const T ynorm = sqrt(c.template vals<T>()[q]);
         for (int i = threadIdx.x; i < q; i += blockDim.x) {
             const T v = c.template vals<T>()[i];
@@ -533,9 +656,11 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
         }
         __syncthreads();
         update_rows(c, cQ0, q, h, y, (T *)nullptr);
+        c.tick(PH_UPD);
         // second Gram-Schmidt pass
         part_multidot(c, cQ0, q, y, c.template red<T>());
         allreduce<T, T>(c, q);
+        c.tick(PH_DOT);
         for (int i = threadIdx.x; i < q; i += blockDim.x) {
             const T v = c.template vals<T>()[i];
             h[i] = v;
@@ -547,6 +672,7 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
         __syncthreads();
         update_rows(c, cQ0, q, h, y, c.template red<T>());
         allreduce<T, T>(c, 1);
+        c.tick(PH_UPD);
         const T hn = sqrt(c.template vals<T>()[0]);
         if (threadIdx.x == 0) M_(H, ldh, j + 1, j) = (double)hn;
         for (int i = j + 2 + threadIdx.x; i <= c.m; i += blockDim.x) M_(H, ldh, i, j) = 0.0;
@@ -554,6 +680,7 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
         c.steps += 1;
         c.matvecs += 1;
         const float est = monitor_step(c, j, (float)rnw);
+        c.tick(PH_OTHER);
         const bool brk = !(hn > tiny * ynorm);
         src = y;
         s = brk ? T(0) : T(1) / hn;
@@ -596,6 +723,7 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
         block_sum<KMAX>(acc, kc, reinterpret_cast<T *>(c.D(c.P.o_wsum)), gram + (kc + Ld + 1) * kc);
         allreduce<T, T>(c, (kc + Ld + 1) * kc + kc);
     }
+    c.tick(PH_GRAM);
     // ---- small dense step (FP64, every CTA)
     double *Rw = c.D(c.P.o_Rw), *gv = c.D(c.P.o_gvec), *y2 = c.D(c.P.o_y2), *gam = c.D(c.P.o_gam);
     double *av = c.D(c.P.o_avec), *gc = c.D(c.P.o_gc), *gs = c.D(c.P.o_gs), *ds = c.D(c.P.o_dscr);
@@ -656,9 +784,25 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
             }
             __syncthreads();
         }
-        knew = harmonic_select(F, ldh, mt, c.k, Pm, mt, c.D(c.P.o_Z), mt, c.D(c.P.o_wr),
-                               c.D(c.P.o_wi), c.D(c.P.o_xr), c.D(c.P.o_xi), c.D(c.P.o_vscr),
-                               c.D(c.P.o_sc), c.ints() + 8);
+        {
+            typedef typename EigT<T>::type R;
+            R *Mr, *Zr;
+            int ldm;
+            if (sizeof(R) == 4) {
+                Mr = reinterpret_cast<R *>(c.D(c.P.o_Z));
+                Zr = Mr + mt * mt;
+                ldm = mt;
+            } else {
+                Mr = reinterpret_cast<R *>(F);
+                Zr = reinterpret_cast<R *>(c.D(c.P.o_Z));
+                ldm = ldh;
+            }
+            knew = harmonic_select<R>(F, ldh, mt, c.k, Pm, mt, Mr, ldm, Zr,
+                                      reinterpret_cast<R *>(c.D(c.P.o_wr)), reinterpret_cast<R *>(c.D(c.P.o_wi)),
+                                      reinterpret_cast<R *>(c.D(c.P.o_xr)), reinterpret_cast<R *>(c.D(c.P.o_xi)),
+                                      reinterpret_cast<R *>(c.D(c.P.o_vscr)), reinterpret_cast<R *>(c.D(c.P.o_sc)),
+                                      c.ints() + 8, Rw);
+        }
         __syncthreads();
         if (knew > 0) {
             // G P_k, G = [[D, B], [0, Hbar]]
@@ -700,77 +844,123 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
     // ---- coefficients in working precision
     T *cC = c.tco(c.P.t_cC), *cU = c.tco(c.P.t_cU), *cr = c.tco(c.P.t_cr), *cd = c.tco(c.P.t_cd);
     const int kn = (knew > 0) ? knew : 0;
+    const int KS = (kn + 3) & ~3;
     for (int i = threadIdx.x; i <= Ld; i += blockDim.x) cr[i] = (T)gam[i];
     for (int a = threadIdx.x; a < kc; a += blockDim.x) cd[a] = (T)av[a];
     for (int j = threadIdx.x; j < Ld; j += blockDim.x) cd[kc + j] = (T)y2[j];
-    for (int e = threadIdx.x; e < (mt + 1) * kn; e += blockDim.x) {
-        const int i = e / kn, o = e % kn;
-        cC[i * kn + o] = (T)M_(Qc, ldh, i, o);
+    for (int e = threadIdx.x; e < (mt + 1) * KS; e += blockDim.x) {
+        const int i = e / KS, o = e % KS;
+        cC[i * KS + o] = (o < kn) ? (T)M_(Qc, ldh, i, o) : T(0);
     }
-    for (int e = threadIdx.x; e < mt * kn; e += blockDim.x) {
-        const int i = e / kn, o = e % kn;
+    for (int e = threadIdx.x; e < mt * KS; e += blockDim.x) {
+        const int i = e / KS, o = e % KS;
         const double sc = (i < kc) ? Dk[i] : 1.0;
-        cU[i * kn + o] = (T)(sc * M_(Pm, mt, i, o));
+        cU[i * KS + o] = (o < kn) ? (T)(sc * M_(Pm, mt, i, o)) : T(0);
     }
     __syncthreads();
-    // ---- update pass (own rows): r, C_new, then d, U_new
+    c.tick(PH_DENSE);
+    // ---- update pass (own rows, two rows per thread): r and C_new from
+    // [C, V_0..V_Ld], then d and U_new from [U, V_0..V_{Ld-1}]
+    typedef typename Vec2<T>::type T2;
     T *rw = c.col(COL_RW), *dh = c.col(COL_DH);
     const int knc = kn;   // new recycle dimension (0: keep the old C, U)
-    double nacc[1] = {0.0};
+    const int nin_a = kc + Ld + 1, nin_b = kc + Ld;
     T tacc[1] = {T(0)};
-    for (long long p = c.lo + threadIdx.x; p < c.lo + c.cnt; p += blockDim.x) {
-        // sub-pass A: inputs C (kc) then V_0..V_Ld
-        T o[KMAX];
+    constexpr int UB = 8;
+    for (long long p = c.lo + 2 * threadIdx.x; p < c.lo + c.cnt; p += 2 * blockDim.x) {
+        T o0[KMAX], o1[KMAX];
 #pragma unroll
-        for (int b = 0; b < KMAX; b++) o[b] = T(0);
-        T racc = rw[p];
-        for (int i = 0; i < kc + Ld + 1; i++) {
-            const T xv = c.col(cQ0 + i)[p];
-            if (i >= kc) racc -= cr[i - kc] * xv;
-            if (knc > 0) {
+        for (int b2 = 0; b2 < KMAX; b2++) o0[b2] = o1[b2] = T(0);
+        T2 racc = *reinterpret_cast<const T2 *>(rw + p);
+        for (int i0 = 0; i0 < nin_a; i0 += UB) {
+            T2 xv[UB];
 #pragma unroll
-                for (int b = 0; b < KMAX; b++)
-                    if (b < knc) o[b] += xv * cC[i * knc + b];
+            for (int u = 0; u < UB; u++)
+                xv[u] = (i0 + u < nin_a) ? *reinterpret_cast<const T2 *>(c.col(cQ0 + i0 + u) + p) : T2{T(0), T(0)};
+#pragma unroll
+            for (int u = 0; u < UB; u++) {
+                const int i = i0 + u;
+                if (i < nin_a) {
+                    if (i >= kc) {
+                        const T gmm = cr[i - kc];
+                        racc.x -= gmm * xv[u].x;
+                        racc.y -= gmm * xv[u].y;
+                    }
+                    const T *cc = cC + i * KS;
+#pragma unroll
+                    for (int b4 = 0; b4 < KMAX; b4 += 4) {
+                        if (b4 < knc) {
+                            T q0, q1, q2, q3;
+                            ld4(cc + b4, q0, q1, q2, q3);
+                            o0[b4] += xv[u].x * q0; o1[b4] += xv[u].y * q0;
+                            o0[b4 + 1] += xv[u].x * q1; o1[b4 + 1] += xv[u].y * q1;
+                            o0[b4 + 2] += xv[u].x * q2; o1[b4 + 2] += xv[u].y * q2;
+                            o0[b4 + 3] += xv[u].x * q3; o1[b4 + 3] += xv[u].y * q3;
+                        }
+                    }
+                }
             }
         }
-        rw[p] = racc;
-        tacc[0] += racc * racc;
-        if (knc > 0) {
+        *reinterpret_cast<T2 *>(rw + p) = racc;
+        tacc[0] += racc.x * racc.x + racc.y * racc.y;
 #pragma unroll
-            for (int b = 0; b < KMAX; b++)
-                if (b < knc) c.col(COL_C_END - knc + b)[p] = o[b];
-        }
-        // sub-pass B: inputs U (kc) then V_0..V_{Ld-1}
+        for (int b2 = 0; b2 < KMAX; b2++)
+            if (b2 < knc) *reinterpret_cast<T2 *>(c.col(COL_C_END - knc + b2) + p) = T2{o0[b2], o1[b2]};
 #pragma unroll
-        for (int b = 0; b < KMAX; b++) o[b] = T(0);
-        T dacc = dh[p];
-        for (int i = 0; i < kc + Ld; i++) {
-            const T xv = (i < kc) ? c.col(COL_U0 + i)[p] : c.col(COL_V0 + (i - kc))[p];
-            dacc += cd[i] * xv;
-            if (knc > 0) {
+        for (int b2 = 0; b2 < KMAX; b2++) o0[b2] = o1[b2] = T(0);
+        T2 dacc = *reinterpret_cast<const T2 *>(dh + p);
+        for (int i0 = 0; i0 < nin_b; i0 += UB) {
+            T2 xv[UB];
 #pragma unroll
-                for (int b = 0; b < KMAX; b++)
-                    if (b < knc) o[b] += xv * cU[i * knc + b];
+            for (int u = 0; u < UB; u++) {
+                const int i = i0 + u;
+                const T *src = (i < kc) ? c.col(COL_U0 + i) : c.col(COL_V0 + (i - kc));
+                xv[u] = (i < nin_b) ? *reinterpret_cast<const T2 *>(src + p) : T2{T(0), T(0)};
+            }
+#pragma unroll
+            for (int u = 0; u < UB; u++) {
+                const int i = i0 + u;
+                if (i < nin_b) {
+                    const T dv = cd[i];
+                    dacc.x += dv * xv[u].x;
+                    dacc.y += dv * xv[u].y;
+                    const T *cc = cU + i * KS;
+#pragma unroll
+                    for (int b4 = 0; b4 < KMAX; b4 += 4) {
+                        if (b4 < knc) {
+                            T q0, q1, q2, q3;
+                            ld4(cc + b4, q0, q1, q2, q3);
+                            o0[b4] += xv[u].x * q0; o1[b4] += xv[u].y * q0;
+                            o0[b4 + 1] += xv[u].x * q1; o1[b4 + 1] += xv[u].y * q1;
+                            o0[b4 + 2] += xv[u].x * q2; o1[b4 + 2] += xv[u].y * q2;
+                            o0[b4 + 3] += xv[u].x * q3; o1[b4 + 3] += xv[u].y * q3;
+                        }
+                    }
+                }
             }
         }
-        dh[p] = dacc;
-        if (knc > 0) {
+        *reinterpret_cast<T2 *>(dh + p) = dacc;
 #pragma unroll
-            for (int b = 0; b < KMAX; b++)
-                if (b < knc) c.col(COL_U0 + b)[p] = o[b];
-        }
+        for (int b2 = 0; b2 < KMAX; b2++)
+            if (b2 < knc) *reinterpret_cast<T2 *>(c.col(COL_U0 + b2) + p) = T2{o0[b2], o1[b2]};
     }
-    (void)nacc;
     block_sum<1>(tacc, 1, reinterpret_cast<T *>(c.D(c.P.o_wsum)), c.template red<T>());
     allreduce<T, T>(c, 1);
     c.bytes += (unsigned long long)c.g.n * sizeof(T) *
                ((kc + Ld + 1) + (kc + Ld) + 4 + 2 * knc);
-    if (knc > 0) c.kc = knc;
+    c.tick(PH_CUPD);
+    if (knc > 0) {
+        c.kc = knc;
+        c.updates_since_refresh += 1;
+    }
     c.cycles += 1;
     return sqrt((double)c.template vals<T>()[0]);
 }
 
 // ------------------------------------------------------------------ one system
+
+// Mixed form: recycle updates between two recomputations of C = A M^-1 U.
+constexpr int RECYCLE_REFRESH = 8;
 
 template <typename T>
 __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx) {
@@ -782,12 +972,12 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx) {
     c.cnt = chunk;
     c.steps = c.cycles = c.matvecs = c.refinements = 0;
     c.breakdown = false;
+    if (c.rank == 0 && threadIdx.x == 0) c.tmark = global_ns();
     assemble_system(c, sys);
+    c.tick(PH_ASM);
     // refresh the carried recycle space against the new operator (App. B.1)
-    if (c.kc > 0) {
-        cl_sync();   // U halo from the previous system
-        refresh_recycle(c);
-    }
+    if (c.kc > 0) refresh_recycle(c);
+    c.tick(PH_REFRESH);
     const long long hi = c.lo + c.cnt;
     // ||b||
     double bacc[1] = {0.0};
@@ -805,6 +995,7 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx) {
     int flag = SKR_NOT_CONVERGED;
     for (int it = 0;; it++) {
         if (it > 0) rnorm = true_residual(c);
+        c.tick(PH_RESID);
         if (isnan(rnorm) || isinf(rnorm)) {
             flag = SKR_NUMERICAL;
             break;
@@ -818,6 +1009,13 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx) {
             break;
         }
         const double target = fp64 ? a.tol * bnorm : fmax(a.inner_tol * rnorm, a.tol * bnorm);
+        // mixed form: FP32 rounding makes A U = C drift with every recycle
+        // update (by ~eps32 kappa each); recompute C from U (App. B.1) at
+        // every refinement pass and every RECYCLE_REFRESH updates
+        if (!fp64 && it > 0 && c.kc > 0 && c.updates_since_refresh > 0) {
+            refresh_recycle(c);
+            c.tick(PH_REFRESH);
+        }
         // inner system A M^-1 d = r in working precision
         T *rw = c.col(COL_RW), *dh = c.col(COL_DH);
         for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
@@ -827,10 +1025,16 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx) {
         __syncthreads();
         double rnw = rnorm;
         for (;;) {
+            c.tick(PH_OTHER);
             if (c.kc > 0) rnw = project_recycle(c);
+            c.tick(PH_PROJ);
             if (!(rnw > target) || c.steps >= c.maxit) break;
             rnw = run_cycle(c, rnw, target);
             if (isnan(rnw)) break;
+            if (!fp64 && c.kc > 0 && c.updates_since_refresh >= RECYCLE_REFRESH) {
+                refresh_recycle(c);
+                c.tick(PH_REFRESH);
+            }
         }
         // x += M^-1 d
         for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x)
@@ -861,13 +1065,13 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512, 1) chain_kernel(const ChainArgs a) {
+__global__ void __launch_bounds__(CHAIN_THREADS, CHAIN_MIN_BLOCKS) chain_kernel(const ChainArgs a) {
     extern __shared__ __align__(16) double smem_dyn[];
     Ctx<T> c;
     c.rank = cl_rank();
     c.cs = cl_size();
     const int slot = blockIdx.x / c.cs;
-    c.P = make_plan(a.m, a.k, blockDim.x);
+    c.P = make_plan(a.m, a.k, blockDim.x, (int)sizeof(T));
     c.sm = smem_dyn;
     c.parity = 0;
     c.m = a.m;
@@ -884,6 +1088,8 @@ __global__ void __launch_bounds__(512, 1) chain_kernel(const ChainArgs a) {
     c.b = a.ws.b + (long long)slot * c.ld;
     c.anode = a.ws.anode + (long long)slot * a.ws.nodecap;
     c.bytes = 0;
+    c.prof = a.prof;
+    c.tmark = 0;
     int *ictl = c.ints();
     for (;;) {
         if (c.rank == 0 && threadIdx.x == 0) ictl[0] = atomicAdd(a.chain_counter, 1);
@@ -892,6 +1098,7 @@ __global__ void __launch_bounds__(512, 1) chain_kernel(const ChainArgs a) {
         cl_sync();
         if (chain >= a.nchains) break;
         c.kc = 0;
+        c.updates_since_refresh = 0;
         for (long long pos = a.chain_off[chain]; pos < a.chain_off[chain + 1]; pos++)
             solve_system(c, a, a.order[pos]);
     }

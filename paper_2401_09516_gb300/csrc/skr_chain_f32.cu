@@ -14,6 +14,8 @@ int max_active_clusters_f32(int cs, int threads, size_t smem) {
     return chain_max_clusters<float>(cs, threads, smem);
 }
 
-size_t chain_smem_bytes(int m, int k, int threads) { return plan_bytes(make_plan(m, k, threads)); }
+size_t chain_smem_bytes(int m, int k, int threads, int esz) { return plan_bytes(make_plan(m, k, threads, esz)); }
+
+int chain_threads() { return CHAIN_THREADS; }
 
 }  // namespace skr

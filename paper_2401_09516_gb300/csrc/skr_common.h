@@ -69,6 +69,9 @@ struct ChainArgs {
     int m, k, maxit, max_refine, precond;
     double tol, inner_tol;
     unsigned long long *bytes;    // algorithmic bytes counter (optional)
+    unsigned long long *prof;     // SKR_NPHASE per-phase ns accumulators (optional)
 };
+
+enum Phase { PH_ASM, PH_REFRESH, PH_PROJ, PH_SPMV, PH_DOT, PH_UPD, PH_GRAM, PH_DENSE, PH_CUPD, PH_RESID, PH_OTHER };
 
 }  // namespace skr

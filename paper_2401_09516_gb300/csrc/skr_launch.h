@@ -17,7 +17,9 @@ cudaError_t launch_chain_f64(const ChainArgs &a, int nclusters, int cs, int thre
 // Clusters of cs CTAs that can be resident at once (0 on error).
 int max_active_clusters_f32(int cs, int threads, size_t smem);
 int max_active_clusters_f64(int cs, int threads, size_t smem);
-// Dynamic shared memory of the chain kernel for (m, k, threads).
-size_t chain_smem_bytes(int m, int k, int threads);
+// Threads per CTA the chain kernel is compiled for.
+int chain_threads();
+// Dynamic shared memory of the chain kernel for (m, k, threads, element size).
+size_t chain_smem_bytes(int m, int k, int threads, int esz);
 
 }  // namespace skr

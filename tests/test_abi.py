@@ -58,6 +58,7 @@ int main(void) {
     S, O, R = native.SkrSystem, native.SkrOptions, native.SkrResult
     assert vals[:3] == [ctypes.sizeof(S), ctypes.sizeof(O), ctypes.sizeof(R)]
     assert vals[3:7] == [S.coef.offset, S.params.offset, O.tol.offset, O.stream.offset]
+    assert O.profile.offset == 52
     assert vals[7:9] == [R.relres.offset, R.seconds.offset]
 
 

@@ -139,6 +139,37 @@ skr_status skr_sort(const double *params, int64_t N, int64_t p, int64_t start,
                     int32_t mem, void *stream, int32_t *perm_out);
 
 /*
+ * skr_sort_noalloc -- the order of skr_sort, for callers that cannot
+ * allocate device memory.  The paper has no counterpart: this entry point
+ * exists for deployment, not for the method.
+ *
+ * Some callers cannot let a library call cudaMalloc: applications that hand
+ * all device memory to their own pool allocator and forbid hidden
+ * allocations, and loops with a latency budget in which a cudaMalloc /
+ * cudaFree pair (each may synchronise the device) is not acceptable.  This
+ * call computes the same permutation as skr_sort, bit for bit, and allocates
+ * nothing: its scratch (the N x N distance matrix, the per-system "placed"
+ * flags and an error word, about 2 MiB in all) lives in one fixed array of
+ * device memory that every GPU loading this library holds until the process
+ * exits.
+ *
+ * params    N x p doubles in DEVICE memory, row i = P(i) flattened
+ * perm_out  N int32 in DEVICE memory
+ * N         at most SKR_SORT_NOALLOC_MAX_N; a larger N is rejected with
+ *           SKR_ERR_INVALID_ARG before any device work
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call on a device uses the same array and leaves its
+ * contents behind: each call resets what must start at zero (the error word;
+ * the kernel resets the flags), but two calls whose work overlaps on the GPU
+ * (different streams or host threads) race on the array, so serialise them.
+ * Host-memory pointers are rejected; other errors as skr_sort.
+ */
+#define SKR_SORT_NOALLOC_MAX_N 512
+skr_status skr_sort_noalloc(const double *params, int64_t N, int64_t p, int64_t start,
+                            void *stream, int32_t *perm_out);
+
+/*
  * skr_solve_sequence -- Algorithm 2 over a sorted sequence (Sec. 4.2,
  * App. B), with the sorted list cut into independent chains (App. E.2.2).
  *

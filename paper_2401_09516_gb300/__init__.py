@@ -19,4 +19,5 @@ from ._native import (  # noqa: F401
     skr_release_workspace,
     skr_solve_sequence,
     skr_sort,
+    skr_sort_noalloc,
 )

@@ -80,6 +80,7 @@ _i32, _i64, _vp, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.
 
 _lib.skr_options_default.argtypes = [ctypes.POINTER(SkrOptions)]
 _lib.skr_sort.argtypes = [_vp, _i64, _i64, _i64, _i32, _vp, _vp]
+_lib.skr_sort_noalloc.argtypes = [_vp, _i64, _i64, _i64, _vp, _vp]
 _lib.skr_solve_sequence.argtypes = [ctypes.POINTER(SkrSystem), _i64, _vp, _vp, _i32,
                                     ctypes.POINTER(SkrOptions), ctypes.POINTER(_vp),
                                     ctypes.POINTER(SkrResult)]
@@ -91,7 +92,7 @@ _lib.skr_last_profile.argtypes = [ctypes.POINTER(ctypes.c_double), _i32]
 _lib.skr_release_workspace.argtypes = []
 _lib.skr_last_error.argtypes = []
 _lib.skr_last_error.restype = ctypes.c_char_p
-for _fn in ("skr_options_default", "skr_sort", "skr_solve_sequence", "skr_assemble", "skr_apply",
+for _fn in ("skr_options_default", "skr_sort", "skr_sort_noalloc", "skr_solve_sequence", "skr_assemble", "skr_apply",
             "skr_last_stats", "skr_last_profile", "skr_release_workspace"):
     getattr(_lib, _fn).restype = ctypes.c_int32
 
@@ -220,6 +221,29 @@ def skr_sort(params, start=0, stream=None):
     return perm
 
 
+SKR_SORT_NOALLOC_MAX_N = 512
+
+
+def skr_sort_noalloc(params, start=0, stream=None):
+    """skr_sort without device allocation, for callers that cannot allocate.
+
+    params must be a CUDA tensor (N x p float64, N <= SKR_SORT_NOALLOC_MAX_N);
+    returns the order as an int32 CUDA tensor.  The scratch is a fixed array
+    the library keeps on every device; calls that overlap on the GPU race on
+    it, so callers serialise them.
+    """
+    P = _f64(params)
+    if not _is_device(P):
+        raise ValueError("skr_sort_noalloc takes device arrays only")
+    import torch
+    N = int(P.shape[0])
+    p = int(np.prod(P.shape[1:])) if N else 1
+    perm = torch.empty(N, dtype=torch.int32, device=P.device)
+    _check(_lib.skr_sort_noalloc(_ptr(P) if N else None, N, p, int(start), _stream_handle(stream),
+                                 _ptr(perm) if N else None))
+    return perm
+
+
 def skr_solve_sequence(systems, order=None, chain_offsets=None, nchains=1, options=None, x_out=None):
     """Solve the systems in `order` with recycling along each chain.
 
@@ -311,7 +335,7 @@ def skr_release_workspace():
 
 def exported_symbols():
     """Names of the C functions this binding wraps."""
-    return ["skr_options_default", "skr_sort", "skr_solve_sequence", "skr_assemble", "skr_apply",
+    return ["skr_options_default", "skr_sort", "skr_sort_noalloc", "skr_solve_sequence", "skr_assemble", "skr_apply",
             "skr_last_stats", "skr_last_profile", "skr_release_workspace", "skr_last_error"]
 
 

@@ -568,3 +568,88 @@ skr_status skr_release_workspace(void) {
 }
 
 }  // extern "C"
+// ---------------------------------------------------------------- sort without allocation
+//
+// skr_sort_noalloc keeps its scratch (the N x N distance matrix, the
+// per-system "placed" flags and an error word) in one fixed array in
+// device memory that every GPU loading this library holds until the process
+// exits, so the call itself never allocates.  Host code must not pass the
+// array's name to a kernel: in host code that name denotes a host-side
+// stand-in, not the device address.  The device address is looked up once
+// per device with cudaGetSymbolAddress and cached.
+namespace {
+constexpr long long NOALLOC_MAX_N = SKR_SORT_NOALLOC_MAX_N;
+constexpr size_t NOALLOC_DIST_BYTES = (size_t)NOALLOC_MAX_N * NOALLOC_MAX_N * sizeof(double);
+constexpr size_t NOALLOC_FLAGS_OFF = NOALLOC_DIST_BYTES;                  // N bytes
+constexpr size_t NOALLOC_ERR_OFF = NOALLOC_DIST_BYTES + NOALLOC_MAX_N;    // one int
+constexpr size_t NOALLOC_BYTES = NOALLOC_ERR_OFF + 256;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_sort_scratch[NOALLOC_BYTES];
+
+namespace {
+// Device address of g_sort_scratch on the current device (set-up on first use).
+skr_status noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(SKR_ERR_INVALID_ARG, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+        if (e != cudaSuccess || p == nullptr)
+            return fail(SKR_ERR_CUDA, "cudaGetSymbolAddress of the sort scratch failed: %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = reinterpret_cast<unsigned char *>(g_noalloc_addr[dev]);
+    return SKR_OK;
+}
+
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+extern "C" skr_status skr_sort_noalloc(const double *params, int64_t N, int64_t p, int64_t start,
+                                       void *stream, int32_t *perm_out) {
+    g_err.clear();
+    if (N < 0) return fail(SKR_ERR_INVALID_ARG, "N < 0");
+    if (N == 0) return SKR_OK;
+    if (N > NOALLOC_MAX_N)
+        return fail(SKR_ERR_INVALID_ARG, "N = %lld exceeds SKR_SORT_NOALLOC_MAX_N = %lld", (long long)N,
+                    NOALLOC_MAX_N);
+    if (!params || !perm_out) return fail(SKR_ERR_INVALID_ARG, "NULL pointer");
+    if (p < 1) return fail(SKR_ERR_INVALID_ARG, "p < 1");
+    if (start < 0 || start >= N) return fail(SKR_ERR_INVALID_ARG, "start out of range");
+    if (!is_device_pointer(params) || !is_device_pointer(perm_out))
+        return fail(SKR_ERR_INVALID_ARG, "params and perm_out must be device memory");
+    unsigned char *base = nullptr;
+    skr_status s0 = noalloc_scratch(&base);
+    if (s0 != SKR_OK) return s0;
+    double *dist = reinterpret_cast<double *>(base);
+    unsigned char *taken = base + NOALLOC_FLAGS_OFF;
+    int *err = reinterpret_cast<int *>(base + NOALLOC_ERR_OFF);
+    cudaStream_t st = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: reset the error word
+    // (the chain kernel clears the placed flags itself)
+    CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+    const long long nt = (N + SORT_TILE - 1) / SORT_TILE;
+    sort_dist_kernel<<<(unsigned)(nt * (nt + 1) / 2), SORT_LANES, 0, st>>>(params, N, p, dist, err);
+    CUDA_TRY(cudaGetLastError());
+    int herr = 0;
+    CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr) return fail(SKR_ERR_INVALID_ARG, "non-finite parameter distance");
+    sort_chain_kernel<<<1, 1024, 0, st>>>(dist, N, start, perm_out, taken);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return SKR_OK;
+}

@@ -216,6 +216,75 @@ skr_status skr_assemble(const skr_system *sys, int32_t mem, void *stream,
 skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t precision,
                      const double *v, double *y, int32_t mem, void *stream);
 
+/* ------------------------------------------------------------------ serving
+ *
+ * A request loop over the same solver: systems arrive one at a time (as in
+ * data generation for a neural operator, Sec. 1 and Fig. 1, where a stream
+ * of PDE instances is solved), are admitted as device memory and slots free
+ * up, are routed to the resident recycle chain nearest to them in parameter
+ * space (the sort's distance, Algorithm 1, applied online), and run
+ * concurrently with the requests of other chains (continuous batching: a new
+ * request starts as soon as it is admitted, while others are on the GPU).
+ * Each chain keeps its U_k, C_k in device memory between requests and
+ * refreshes them against every new matrix (App. B.1).
+ */
+typedef struct skr_server skr_server;
+
+typedef struct skr_server_info {
+    int64_t submitted, completed, queued, running;
+    int32_t chains;           /* recycle chains created so far */
+    int32_t pad;
+    double  p50_ms, p99_ms, mean_ms;   /* submit-to-completion latency of completed requests */
+    double  hbm_bytes;        /* device memory held by the server's chains */
+} skr_server_info;
+
+/*
+ * skr_server_create -- start a server on the current CUDA device.
+ *
+ * opt          solver options (m, k, tol, precond, precision, cluster_size, ...);
+ *              opt->mem and opt->stream are ignored (requests are host memory,
+ *              every chain has its own stream)
+ * hbm_budget   bytes of device memory the server may hold for chains (each
+ *              chain holds one workspace slot sized for its grid plus its
+ *              request buffers); 0 = no limit
+ * max_chains   upper bound on resident chains (0 = 64)
+ * A host thread owned by the server admits, routes, launches and collects
+ * requests.  Errors: bad options -> SKR_ERR_INVALID_ARG.
+ */
+skr_status skr_server_create(const skr_options *opt, size_t hbm_budget, int32_t max_chains,
+                             skr_server **srv);
+
+/*
+ * skr_submit -- enqueue one system; returns at once with a ticket.
+ *
+ * sys    the system, its data in HOST memory; the server copies it before
+ *        returning, so the caller may reuse or free the buffers
+ * key    p doubles, the routing parameter vector (e.g. log a flattened, or
+ *        (nu, beta)); only chains of the same format, grid and p are
+ *        candidates.  key may be NULL (p = 0): the system's own coefficient
+ *        data is then the key
+ * A request is admitted when a chain of its shape is idle (the nearest idle
+ * one is taken) or when a new chain fits in the budget; otherwise it waits.
+ * A request larger than the whole budget is rejected (SKR_ERR_OOM).
+ */
+skr_status skr_submit(skr_server *srv, const skr_system *sys, const double *key, int64_t p,
+                      uint64_t *ticket);
+
+/*
+ * skr_poll -- SKR_NOT_READY while the request is queued or running; once it
+ * is done, copies the n-vector solution to x_out (host memory) and the
+ * outcome to *res, forgets the ticket and returns SKR_OK.  An unknown ticket
+ * -> SKR_ERR_INVALID_ARG.
+ */
+skr_status skr_poll(skr_server *srv, uint64_t ticket, double *x_out, skr_result *res);
+
+/* Counters and latency percentiles of the server so far. */
+skr_status skr_server_stats(skr_server *srv, skr_server_info *info);
+
+/* Wait for the running requests, stop the loop and free every resource;
+ * queued requests are dropped. */
+skr_status skr_server_destroy(skr_server *srv);
+
 /*
  * skr_last_stats -- figures of the last skr_solve_sequence call on the
  * calling thread: the algorithmic bytes its kernel streamed (the compulsory

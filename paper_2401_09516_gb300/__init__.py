@@ -5,6 +5,7 @@ include/skr.h); `paper_2401_09516_gb300._native` is its ctypes binding.
 Build with `python -m paper_2401_09516_gb300.build`.
 """
 from ._native import (  # noqa: F401
+    Server,
     System,
     SkrError,
     convdiff2d,
@@ -16,7 +17,12 @@ from ._native import (  # noqa: F401
     skr_last_profile,
     skr_last_stats,
     skr_options_default,
+    skr_poll,
     skr_release_workspace,
+    skr_server_create,
+    skr_server_destroy,
+    skr_server_stats,
+    skr_submit,
     skr_solve_sequence,
     skr_sort,
     skr_sort_noalloc,

@@ -70,6 +70,16 @@ class SkrResult(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class SkrServerInfo(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("chains", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("hbm_bytes", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(
         "libskr.so is not built (expected at %s); run __graft_entry__.build() "
@@ -90,10 +100,16 @@ _lib.skr_last_stats.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(
                                 ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
 _lib.skr_last_profile.argtypes = [ctypes.POINTER(ctypes.c_double), _i32]
 _lib.skr_release_workspace.argtypes = []
+_lib.skr_server_create.argtypes = [ctypes.POINTER(SkrOptions), ctypes.c_size_t, _i32, ctypes.POINTER(_vp)]
+_lib.skr_submit.argtypes = [_vp, ctypes.POINTER(SkrSystem), _vp, _i64, ctypes.POINTER(ctypes.c_uint64)]
+_lib.skr_poll.argtypes = [_vp, ctypes.c_uint64, _vp, ctypes.POINTER(SkrResult)]
+_lib.skr_server_stats.argtypes = [_vp, ctypes.POINTER(SkrServerInfo)]
+_lib.skr_server_destroy.argtypes = [_vp]
 _lib.skr_last_error.argtypes = []
 _lib.skr_last_error.restype = ctypes.c_char_p
 for _fn in ("skr_options_default", "skr_sort", "skr_sort_noalloc", "skr_solve_sequence", "skr_assemble", "skr_apply",
-            "skr_last_stats", "skr_last_profile", "skr_release_workspace"):
+            "skr_last_stats", "skr_last_profile", "skr_release_workspace", "skr_server_create",
+            "skr_submit", "skr_poll", "skr_server_stats", "skr_server_destroy"):
     getattr(_lib, _fn).restype = ctypes.c_int32
 
 
@@ -333,10 +349,97 @@ def skr_release_workspace():
     _check(_lib.skr_release_workspace())
 
 
+def skr_server_create(options=None, hbm_budget=0, max_chains=0):
+    """Start a serving loop; returns an opaque handle (see Server)."""
+    opt = options if options is not None else skr_options_default()
+    h = _vp()
+    _check(_lib.skr_server_create(ctypes.byref(opt), int(hbm_budget), int(max_chains), ctypes.byref(h)))
+    return h
+
+
+def skr_submit(server, system, key=None):
+    """Enqueue one system (host arrays); returns its ticket."""
+    for a in system.arrays():
+        if a is not None and _is_device(a):
+            raise ValueError("skr_submit takes host arrays")
+    k = None if key is None else np.ascontiguousarray(key, dtype=np.float64).reshape(-1)
+    s = system.struct()
+    t = ctypes.c_uint64()
+    _check(_lib.skr_submit(server, ctypes.byref(s), None if k is None else k.ctypes.data,
+                           0 if k is None else k.size, ctypes.byref(t)))
+    return t.value
+
+
+def skr_poll(server, ticket, n):
+    """(x, result) once the request is done, else None."""
+    x = np.empty(n)
+    r = SkrResult()
+    st = _lib.skr_poll(server, ctypes.c_uint64(ticket), x.ctypes.data, ctypes.byref(r))
+    if st == SKR_NOT_READY:
+        return None
+    _check(st)
+    return x, r.as_dict()
+
+
+def skr_server_stats(server):
+    info = SkrServerInfo()
+    _check(_lib.skr_server_stats(server, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def skr_server_destroy(server):
+    _check(_lib.skr_server_destroy(server))
+
+
+class Server:
+    """Context-managed serving loop over skr_server_* (marshalling only)."""
+
+    def __init__(self, options=None, hbm_budget=0, max_chains=0):
+        self.handle = skr_server_create(options, hbm_budget, max_chains)
+        self._n = {}
+
+    def submit(self, system, key=None):
+        t = skr_submit(self.handle, system, key)
+        self._n[t] = system.n
+        return t
+
+    def poll(self, ticket):
+        out = skr_poll(self.handle, ticket, self._n[ticket])
+        if out is not None:
+            del self._n[ticket]
+        return out
+
+    def wait(self, ticket, timeout=120.0):
+        import time
+        t0 = time.time()
+        while True:
+            out = self.poll(ticket)
+            if out is not None:
+                return out
+            if time.time() - t0 > timeout:
+                raise TimeoutError("request %d not done after %.0f s" % (ticket, timeout))
+            time.sleep(0.0005)
+
+    def stats(self):
+        return skr_server_stats(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            skr_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def exported_symbols():
     """Names of the C functions this binding wraps."""
     return ["skr_options_default", "skr_sort", "skr_sort_noalloc", "skr_solve_sequence", "skr_assemble", "skr_apply",
-            "skr_last_stats", "skr_last_profile", "skr_release_workspace", "skr_last_error"]
+            "skr_last_stats", "skr_last_profile", "skr_release_workspace", "skr_last_error",
+            "skr_server_create", "skr_submit", "skr_poll", "skr_server_stats", "skr_server_destroy"]
 
 
 def library():

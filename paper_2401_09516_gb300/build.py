@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libskr.so")
-UNITS = ["skr_api.cu", "skr_chain_f32.cu", "skr_chain_f64.cu"]
+UNITS = ["skr_api.cu", "skr_chain_f32.cu", "skr_chain_f64.cu", "skr_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

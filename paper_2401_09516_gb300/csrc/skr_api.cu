@@ -13,6 +13,7 @@
 
 #include "skr_common.h"
 #include "skr_launch.h"
+#include "skr_workspace.h"
 #include "skr_ops.cuh"
 #include "skr_sort.cuh"
 
@@ -164,6 +165,18 @@ skr_status stage_system(const skr_system &s, int mem, cudaStream_t st, Staged &o
     }
     return SKR_OK;
 }
+
+}  // namespace
+
+namespace skr {
+// Record an error message for the calling thread (used by the server unit).
+skr_status set_last_error(skr_status code, const char *msg) {
+    g_err = msg;
+    return code;
+}
+}  // namespace skr
+
+namespace {
 
 struct LastStats {
     unsigned long long prof[SKR_NPHASE] = {0};
@@ -403,30 +416,15 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     if (maxc < 1) return fail(SKR_ERR_CUDA, "cluster of %d CTAs with %zu bytes of shared memory cannot be scheduled", cs, smem);
     int nslots = std::min(nchains, maxc);
     if (opt.max_slots > 0) nslots = std::min(nslots, opt.max_slots);
-    const long long chunk = (((nmax + cs - 1) / cs) + 7) / 8 * 8;
-    const long long ld = ((chunk * cs) + 63) / 64 * 64;
+    const long long ld = chain_ld(nmax, cs);
     const size_t esz = fp64 ? 8 : 4;
     const long long nodecap = std::max<long long>(nodemax, 1);
-    // workspace layout
-    size_t o = 0;
-    auto take = [&](size_t bytes) {
-        size_t r = o;
-        o += (bytes + 255) / 256 * 256;
-        return r;
-    };
-    const size_t o_basis = take((size_t)nslots * NCOLS * ld * esz);
-    const size_t o_A64 = take((size_t)nslots * 7 * ld * 8);
-    const size_t o_Aw = take((size_t)nslots * 7 * ld * esz);
-    const size_t o_dinv = take((size_t)nslots * ld * 8);
-    const size_t o_x = take((size_t)nslots * ld * 8);
-    const size_t o_r = take((size_t)nslots * ld * 8);
-    const size_t o_b = take((size_t)nslots * ld * 8);
-    const size_t o_node = take((size_t)nslots * nodecap * 8);
+    const SlabLayout L = slab_layout(nslots, ld, nodecap, esz);
     void *wbase = nullptr;
-    CUDA_TRY(ws_get(o, &wbase));
+    CUDA_TRY(ws_get(L.total, &wbase));
     char *wb = reinterpret_cast<char *>(wbase);
     // the basis must start zeroed: padded rows are never written by the passes that read them
-    CUDA_TRY(cudaMemsetAsync(wb + o_basis, 0, (size_t)nslots * NCOLS * ld * esz, st));
+    CUDA_TRY(cudaMemsetAsync(wb + L.o_basis, 0, (size_t)nslots * NCOLS * ld * esz, st));
 
     // per-call device arrays
     std::vector<Staged> staged(N);
@@ -464,17 +462,7 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     a.chain_off = doff.as<long long>();
     a.nchains = nchains;
     a.chain_counter = dctr.as<int>();
-    a.ws.basis = wb + o_basis;
-    a.ws.A64 = reinterpret_cast<double *>(wb + o_A64);
-    a.ws.Aw = wb + o_Aw;
-    a.ws.dinv = reinterpret_cast<double *>(wb + o_dinv);
-    a.ws.x = reinterpret_cast<double *>(wb + o_x);
-    a.ws.r = reinterpret_cast<double *>(wb + o_r);
-    a.ws.b = reinterpret_cast<double *>(wb + o_b);
-    a.ws.anode = reinterpret_cast<double *>(wb + o_node);
-    a.ws.ld = ld;
-    a.ws.nodecap = nodecap;
-    a.ws.nslots = nslots;
+    a.ws = slab_bind(wb, L, nslots, ld, nodecap);
     a.results = dres.as<DevResult>();
     a.m = opt.m;
     a.k = opt.k;
@@ -485,6 +473,7 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     a.inner_tol = opt.inner_tol;
     a.bytes = reinterpret_cast<unsigned long long *>(dctr.as<char>() + 32);
     a.prof = opt.profile ? reinterpret_cast<unsigned long long *>(dctr.as<char>() + 64) : nullptr;
+    a.chain_kc = nullptr;
 
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));

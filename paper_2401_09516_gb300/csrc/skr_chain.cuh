@@ -1098,9 +1098,14 @@ __global__ void __launch_bounds__(CHAIN_THREADS, CHAIN_MIN_BLOCKS) chain_kernel(
         cl_sync();
         if (chain >= a.nchains) break;
         c.kc = 0;
+        if (a.chain_kc) {
+            const int k0 = a.chain_kc[chain];
+            c.kc = (k0 > 0 && k0 <= a.k) ? k0 : 0;
+        }
         c.updates_since_refresh = 0;
         for (long long pos = a.chain_off[chain]; pos < a.chain_off[chain + 1]; pos++)
             solve_system(c, a, a.order[pos]);
+        if (a.chain_kc && c.rank == 0 && threadIdx.x == 0) a.chain_kc[chain] = c.kc;
     }
 }
 

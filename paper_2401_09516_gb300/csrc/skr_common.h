@@ -70,6 +70,9 @@ struct ChainArgs {
     double tol, inner_tol;
     unsigned long long *bytes;    // algorithmic bytes counter (optional)
     unsigned long long *prof;     // SKR_NPHASE per-phase ns accumulators (optional)
+    int *chain_kc;                // per-chain recycle dimension carried between launches
+                                  // (optional: read at chain start, written at chain end;
+                                  // the chain's U_k, C_k stay in its workspace slot)
 };
 
 enum Phase { PH_ASM, PH_REFRESH, PH_PROJ, PH_SPMV, PH_DOT, PH_UPD, PH_GRAM, PH_DENSE, PH_CUPD, PH_RESID, PH_OTHER };

@@ -1,0 +1,507 @@
+// Serving loop over the chain kernel (include/skr.h, skr_server_*).
+//
+// One host thread per server owns every CUDA call: it collects finished
+// requests (event queries), admits queued ones (nearest idle chain of the
+// same shape, or a new chain if the device-memory budget allows), and
+// launches each admitted request as a one-cluster chain-kernel launch on the
+// chain's own stream.  Requests of different chains therefore run
+// concurrently on the GPU; a request that arrives while others run starts as
+// soon as a chain of its shape is free.  skr_submit and skr_poll only touch
+// host data under the server's mutex.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "skr_common.h"
+#include "skr_launch.h"
+#include "skr_workspace.h"
+
+namespace skr {
+skr_status set_last_error(skr_status code, const char *msg);
+}
+
+using namespace skr;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+skr_status err(skr_status code, const std::string &msg) { return set_last_error(code, msg.c_str()); }
+
+bool fmt3d(int fmt) { return fmt == SKR_FMT_DARCY3D || fmt == SKR_FMT_STENCIL7; }
+
+long long n_of(int fmt, int nx, int ny, int nz) { return (long long)nx * ny * (fmt3d(fmt) ? nz : 1); }
+
+long long coef_len(int fmt, int nx, int ny, int nz) {
+    const long long n = n_of(fmt, nx, ny, nz);
+    switch (fmt) {
+        case SKR_FMT_DARCY2D: return (long long)(nx + 2) * (ny + 2);
+        case SKR_FMT_DARCY3D: return (long long)(nx + 2) * (ny + 2) * (nz + 2);
+        case SKR_FMT_STENCIL5: return 5 * n;
+        case SKR_FMT_STENCIL7: return 7 * n;
+        default: return 0;
+    }
+}
+
+struct Request {
+    uint64_t ticket = 0;
+    int fmt = 0, nx = 0, ny = 0, nz = 1;
+    long long n = 0;
+    double params[4] = {0, 0, 0, 0};
+    std::vector<double> coef, rhs, key;
+    int state = 0;   // 0 queued, 1 running, 2 done
+    std::vector<double> x;
+    skr_result res{};
+    Clock::time_point t_submit, t_done;
+};
+
+struct Chain {
+    int fmt = 0, nx = 0, ny = 0, nz = 1;
+    long long n = 0, clen = 0;
+    size_t p = 0;
+    std::vector<double> key;
+    int cs = 1;
+    long long ld = 0, nodecap = 1;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    char *slab = nullptr;
+    size_t bytes = 0;
+    Workspace ws{};
+    double *dcoef = nullptr, *drhs = nullptr, *dx = nullptr;
+    DevSystem *dsys = nullptr;
+    DevResult *dres = nullptr;
+    int *dorder = nullptr, *dctr = nullptr, *dkc = nullptr;
+    long long *doff = nullptr;
+    unsigned long long *dbytes = nullptr;
+    char *pinned = nullptr;   // host staging
+    double *hcoef = nullptr, *hrhs = nullptr, *hx = nullptr;
+    DevSystem *hsys = nullptr;
+    DevResult *hres = nullptr;
+    bool busy = false;
+    uint64_t ticket = 0;
+};
+
+size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+struct skr_server {
+    skr_options opt{};
+    size_t budget = 0, used = 0, smem = 0;
+    int max_chains = 64, device = 0, threads = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<uint64_t> queue;
+    std::unordered_map<uint64_t, Request *> reqs;
+    std::vector<Chain *> chains;
+    std::vector<double> lat_ms;
+    uint64_t next = 1;
+    int64_t submitted = 0, completed = 0;
+    bool stop = false;
+    std::thread th;
+};
+
+namespace {
+
+int auto_cs(long long n, int requested) {
+    if (requested > 0) return requested;
+    return (int)std::min<long long>(8, std::max<long long>(1, (n + 8191) / 8192));
+}
+
+size_t chain_bytes(const skr_server *S, const Request &r, int cs) {
+    const size_t esz = S->opt.precision == SKR_PREC_FP64 ? 8 : 4;
+    const long long ld = chain_ld(r.n, cs);
+    const long long nodecap = std::max<long long>(1, (r.fmt == SKR_FMT_DARCY2D || r.fmt == SKR_FMT_DARCY3D)
+                                                         ? coef_len(r.fmt, r.nx, r.ny, r.nz)
+                                                         : 1);
+    const SlabLayout L = slab_layout(1, ld, nodecap, esz);
+    const long long clen = std::max<long long>(1, coef_len(r.fmt, r.nx, r.ny, r.nz));
+    return L.total + al256(clen * 8) + 2 * al256(r.n * 8) + 4096;
+}
+
+void destroy_chain(Chain *c) {
+    if (c->st) cudaStreamSynchronize(c->st);
+    if (c->slab) cudaFree(c->slab);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->ev) cudaEventDestroy(c->ev);
+    if (c->st) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+// New chain shaped like request r (called with the server lock held).
+Chain *create_chain(skr_server *S, const Request &r) {
+    Chain *c = new Chain();
+    c->fmt = r.fmt;
+    c->nx = r.nx;
+    c->ny = r.ny;
+    c->nz = r.nz;
+    c->n = r.n;
+    c->p = r.key.size();
+    c->clen = std::max<long long>(1, coef_len(r.fmt, r.nx, r.ny, r.nz));
+    c->cs = auto_cs(r.n, S->opt.cluster_size);
+    const size_t esz = S->opt.precision == SKR_PREC_FP64 ? 8 : 4;
+    c->ld = chain_ld(r.n, c->cs);
+    c->nodecap = std::max<long long>(1, (r.fmt == SKR_FMT_DARCY2D || r.fmt == SKR_FMT_DARCY3D)
+                                            ? coef_len(r.fmt, r.nx, r.ny, r.nz)
+                                            : 1);
+    const SlabLayout L = slab_layout(1, c->ld, c->nodecap, esz);
+    size_t o = L.total;
+    const size_t o_coef = o;  o += al256(c->clen * 8);
+    const size_t o_rhs = o;   o += al256(r.n * 8);
+    const size_t o_x = o;     o += al256(r.n * 8);
+    const size_t o_sys = o;   o += 256;
+    const size_t o_res = o;   o += 256;
+    const size_t o_ord = o;   o += 256;
+    const size_t o_off = o;   o += 256;
+    const size_t o_ctr = o;   o += 256;
+    const size_t o_kc = o;    o += 256;
+    c->bytes = o;
+    if (cudaMalloc(&c->slab, c->bytes) != cudaSuccess) {
+        cudaGetLastError();
+        c->slab = nullptr;
+        destroy_chain(c);
+        return nullptr;
+    }
+    const size_t pin = al256(c->clen * 8) + 2 * al256(r.n * 8) + 512;
+    if (cudaMallocHost(&c->pinned, pin) != cudaSuccess || cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        destroy_chain(c);
+        return nullptr;
+    }
+    c->ws = slab_bind(c->slab, L, 1, c->ld, c->nodecap);
+    c->dcoef = reinterpret_cast<double *>(c->slab + o_coef);
+    c->drhs = reinterpret_cast<double *>(c->slab + o_rhs);
+    c->dx = reinterpret_cast<double *>(c->slab + o_x);
+    c->dsys = reinterpret_cast<DevSystem *>(c->slab + o_sys);
+    c->dres = reinterpret_cast<DevResult *>(c->slab + o_res);
+    c->dorder = reinterpret_cast<int *>(c->slab + o_ord);
+    c->doff = reinterpret_cast<long long *>(c->slab + o_off);
+    c->dctr = reinterpret_cast<int *>(c->slab + o_ctr);
+    c->dbytes = reinterpret_cast<unsigned long long *>(c->slab + o_ctr + 64);
+    c->dkc = reinterpret_cast<int *>(c->slab + o_kc);
+    c->hcoef = reinterpret_cast<double *>(c->pinned);
+    c->hrhs = reinterpret_cast<double *>(c->pinned + al256(c->clen * 8));
+    c->hx = reinterpret_cast<double *>(c->pinned + al256(c->clen * 8) + al256(r.n * 8));
+    c->hsys = reinterpret_cast<DevSystem *>(c->pinned + al256(c->clen * 8) + 2 * al256(r.n * 8));
+    c->hres = reinterpret_cast<DevResult *>(c->pinned + al256(c->clen * 8) + 2 * al256(r.n * 8) + 256);
+    // constant descriptors: one chain of one system, starting with no recycle space
+    cudaMemsetAsync(c->ws.basis, 0, (size_t)NCOLS * c->ld * esz, c->st);
+    cudaMemsetAsync(c->slab + o_ord, 0, c->bytes - o_ord, c->st);
+    const long long off[2] = {0, 1};
+    cudaMemcpyAsync(c->doff, off, sizeof(off), cudaMemcpyHostToDevice, c->st);
+    cudaStreamSynchronize(c->st);
+    if (cudaGetLastError() != cudaSuccess) {
+        destroy_chain(c);
+        return nullptr;
+    }
+    return c;
+}
+
+// Launch request r on chain c (server lock held).  Returns false on a CUDA error.
+bool launch(skr_server *S, Chain *c, Request *r) {
+    cudaStream_t st = c->st;
+    std::memcpy(c->hcoef, r->coef.data(), r->coef.size() * 8);
+    if (!r->coef.empty()) cudaMemcpyAsync(c->dcoef, c->hcoef, r->coef.size() * 8, cudaMemcpyHostToDevice, st);
+    if (!r->rhs.empty()) {
+        std::memcpy(c->hrhs, r->rhs.data(), r->n * 8);
+        cudaMemcpyAsync(c->drhs, c->hrhs, r->n * 8, cudaMemcpyHostToDevice, st);
+    }
+    DevSystem ds;
+    ds.fmt = r->fmt;
+    ds.nx = r->nx;
+    ds.ny = r->ny;
+    ds.nz = r->nz;
+    ds.coef = r->coef.empty() ? nullptr : c->dcoef;
+    ds.rhs = r->rhs.empty() ? nullptr : c->drhs;
+    for (int i = 0; i < 4; i++) ds.params[i] = r->params[i];
+    ds.x_out = c->dx;
+    *c->hsys = ds;
+    cudaMemcpyAsync(c->dsys, c->hsys, sizeof(DevSystem), cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(c->dctr, 0, 128, st);
+    ChainArgs a;
+    a.systems = c->dsys;
+    a.order = c->dorder;
+    a.chain_off = c->doff;
+    a.nchains = 1;
+    a.chain_counter = c->dctr;
+    a.ws = c->ws;
+    a.results = c->dres;
+    a.m = S->opt.m;
+    a.k = S->opt.k;
+    a.maxit = S->opt.maxit;
+    a.max_refine = S->opt.max_refine;
+    a.precond = S->opt.precond;
+    a.tol = S->opt.tol;
+    a.inner_tol = S->opt.inner_tol;
+    a.bytes = c->dbytes;
+    a.prof = nullptr;
+    a.chain_kc = c->dkc;
+    const cudaError_t e = (S->opt.precision == SKR_PREC_FP64)
+                              ? launch_chain_f64(a, 1, c->cs, S->threads, S->smem, st)
+                              : launch_chain_f32(a, 1, c->cs, S->threads, S->smem, st);
+    if (e != cudaSuccess) return false;
+    cudaMemcpyAsync(c->hx, c->dx, r->n * 8, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(c->hres, c->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, st);
+    cudaEventRecord(c->ev, st);
+    c->busy = true;
+    c->ticket = r->ticket;
+    c->key = r->key;
+    r->state = 1;
+    return cudaGetLastError() == cudaSuccess;
+}
+
+void finish(skr_server *S, Request *r, const DevResult *d, bool ok) {
+    r->t_done = Clock::now();
+    if (ok) {
+        r->res.steps = d->steps;
+        r->res.cycles = d->cycles;
+        r->res.matvecs = d->matvecs;
+        r->res.refinements = d->refinements;
+        r->res.flag = d->flag;
+        r->res.k_final = d->k_final;
+        r->res.relres = d->relres;
+        r->res.seconds = (d->t_end >= d->t_begin) ? (double)(d->t_end - d->t_begin) * 1e-9 : 0.0;
+    } else {
+        r->res = skr_result{};
+        r->res.flag = SKR_NUMERICAL;
+        r->res.relres = NAN;
+    }
+    r->state = 2;
+    S->completed += 1;
+    S->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+}
+
+double sqdist(const std::vector<double> &a, const std::vector<double> &b) {
+    double s = 0.0;
+    for (size_t i = 0; i < a.size(); i++) {
+        const double d = a[i] - b[i];
+        s += d * d;
+    }
+    return s;
+}
+
+void loop(skr_server *S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        bool any_busy = false;
+        for (Chain *c : S->chains) {
+            if (!c->busy) continue;
+            const cudaError_t q = cudaEventQuery(c->ev);
+            if (q == cudaErrorNotReady) {
+                any_busy = true;
+                continue;
+            }
+            auto it = S->reqs.find(c->ticket);
+            if (it != S->reqs.end()) {
+                Request *r = it->second;
+                if (q == cudaSuccess) {
+                    finish(S, r, c->hres, true);
+                    r->x.assign(c->hx, c->hx + r->n);
+                } else {
+                    cudaGetLastError();
+                    finish(S, r, nullptr, false);
+                }
+            }
+            c->busy = false;
+        }
+        if (S->stop && !any_busy) break;
+        if (!S->stop) {
+            for (auto it = S->queue.begin(); it != S->queue.end();) {
+                Request *r = S->reqs[*it];
+                Chain *best = nullptr;
+                double bd = INFINITY;
+                for (Chain *c : S->chains) {
+                    if (c->busy || c->fmt != r->fmt || c->nx != r->nx || c->ny != r->ny || c->nz != r->nz ||
+                        c->p != r->key.size())
+                        continue;
+                    const double d = c->key.empty() ? 0.0 : sqdist(c->key, r->key);
+                    if (d < bd) {
+                        bd = d;
+                        best = c;
+                    }
+                }
+                if (!best && (int)S->chains.size() < S->max_chains) {
+                    const size_t need = chain_bytes(S, *r, auto_cs(r->n, S->opt.cluster_size));
+                    if (S->budget == 0 || S->used + need <= S->budget) {
+                        best = create_chain(S, *r);
+                        if (best) {
+                            S->chains.push_back(best);
+                            S->used += best->bytes;
+                        } else {
+                            // device memory could not be obtained: fail the request
+                            // rather than keep it queued
+                            finish(S, r, nullptr, false);
+                            it = S->queue.erase(it);
+                            continue;
+                        }
+                    }
+                }
+                if (!best) {
+                    ++it;
+                    continue;
+                }
+                if (!launch(S, best, r)) {
+                    cudaGetLastError();
+                    finish(S, r, nullptr, false);
+                    best->busy = false;
+                }
+                it = S->queue.erase(it);
+            }
+        }
+        S->cv.wait_for(lk, std::chrono::microseconds(50));
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+skr_status skr_server_create(const skr_options *opt_in, size_t hbm_budget, int32_t max_chains, skr_server **out) {
+    if (!out) return err(SKR_ERR_INVALID_ARG, "srv is NULL");
+    *out = nullptr;
+    skr_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        skr_options_default(&opt);
+    if (opt.m < 2 || opt.m > SKR_MAX_M) return err(SKR_ERR_INVALID_ARG, "m out of range");
+    if (opt.k < 0 || opt.k > SKR_MAX_K || (opt.k > 0 && opt.k > opt.m - 2)) return err(SKR_ERR_INVALID_ARG, "k out of range");
+    if (opt.maxit < 1 || opt.max_refine < 1 || !(opt.tol > 0.0 && opt.tol < 1.0))
+        return err(SKR_ERR_INVALID_ARG, "bad maxit, max_refine or tol");
+    if (opt.precision == SKR_PREC_MIXED && !(opt.inner_tol > 0.0 && opt.inner_tol < 1.0))
+        return err(SKR_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
+    if (opt.precond != SKR_PC_NONE && opt.precond != SKR_PC_JACOBI) return err(SKR_ERR_INVALID_ARG, "preconditioner not available");
+    if (opt.precision != SKR_PREC_FP64 && opt.precision != SKR_PREC_MIXED) return err(SKR_ERR_INVALID_ARG, "bad precision");
+    if (opt.cluster_size < 0 || opt.cluster_size > 16) return err(SKR_ERR_INVALID_ARG, "cluster_size in [0, 16]");
+    if (max_chains < 0) return err(SKR_ERR_INVALID_ARG, "max_chains < 0");
+    skr_server *S = new skr_server();
+    S->opt = opt;
+    S->budget = hbm_budget;
+    S->max_chains = max_chains > 0 ? max_chains : 64;
+    S->threads = chain_threads();
+    S->smem = chain_smem_bytes(opt.m, opt.k, S->threads, opt.precision == SKR_PREC_FP64 ? 8 : 4);
+    if (S->smem > 227 * 1024) {
+        delete S;
+        return err(SKR_ERR_INVALID_ARG, "m, k too large for shared memory");
+    }
+    if (cudaGetDevice(&S->device) != cudaSuccess) {
+        delete S;
+        return err(SKR_ERR_CUDA, "no CUDA device");
+    }
+    S->th = std::thread(loop, S);
+    *out = S;
+    return SKR_OK;
+}
+
+skr_status skr_submit(skr_server *S, const skr_system *sys, const double *key, int64_t p, uint64_t *ticket) {
+    if (!S || !sys || !ticket) return err(SKR_ERR_INVALID_ARG, "NULL pointer");
+    if (sys->fmt < SKR_FMT_DARCY2D || sys->fmt > SKR_FMT_STENCIL7) return err(SKR_ERR_INVALID_ARG, "unknown format");
+    if (sys->nx < 1 || sys->ny < 1 || (fmt3d(sys->fmt) && sys->nz < 1)) return err(SKR_ERR_INVALID_ARG, "empty grid");
+    if (sys->fmt == SKR_FMT_CONVDIFF2D && (sys->nx != sys->ny || !(sys->params[0] > 0.0)))
+        return err(SKR_ERR_INVALID_ARG, "convection-diffusion needs nx == ny and nu > 0");
+    if (sys->fmt != SKR_FMT_CONVDIFF2D && !sys->coef) return err(SKR_ERR_INVALID_ARG, "coef is NULL");
+    if (p < 0 || (p > 0 && !key)) return err(SKR_ERR_INVALID_ARG, "bad key");
+    Request *r = new Request();
+    r->fmt = sys->fmt;
+    r->nx = sys->nx;
+    r->ny = sys->ny;
+    r->nz = fmt3d(sys->fmt) ? sys->nz : 1;
+    r->n = n_of(r->fmt, r->nx, r->ny, r->nz);
+    for (int i = 0; i < 4; i++) r->params[i] = sys->params[i];
+    const long long clen = coef_len(r->fmt, r->nx, r->ny, r->nz);
+    if (clen > 0) r->coef.assign(sys->coef, sys->coef + clen);
+    if (sys->rhs) r->rhs.assign(sys->rhs, sys->rhs + r->n);
+    if (p > 0)
+        r->key.assign(key, key + p);
+    else if (clen > 0)
+        r->key = r->coef;
+    else
+        r->key.assign(r->params, r->params + 3);
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->budget > 0 && chain_bytes(S, *r, auto_cs(r->n, S->opt.cluster_size)) > S->budget) {
+            delete r;
+            return err(SKR_ERR_OOM, "request does not fit in the server's device-memory budget");
+        }
+        r->ticket = S->next++;
+        S->reqs[r->ticket] = r;
+        S->queue.push_back(r->ticket);
+        S->submitted += 1;
+        *ticket = r->ticket;
+    }
+    S->cv.notify_one();
+    return SKR_OK;
+}
+
+skr_status skr_poll(skr_server *S, uint64_t ticket, double *x_out, skr_result *res) {
+    if (!S) return err(SKR_ERR_INVALID_ARG, "srv is NULL");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return err(SKR_ERR_INVALID_ARG, "unknown ticket");
+    Request *r = it->second;
+    if (r->state != 2) return SKR_NOT_READY;
+    if (x_out && !r->x.empty()) std::memcpy(x_out, r->x.data(), r->x.size() * 8);
+    if (res) *res = r->res;
+    S->reqs.erase(it);
+    delete r;
+    return SKR_OK;
+}
+
+skr_status skr_server_stats(skr_server *S, skr_server_info *info) {
+    if (!S || !info) return err(SKR_ERR_INVALID_ARG, "NULL pointer");
+    std::lock_guard<std::mutex> lk(S->mu);
+    std::memset(info, 0, sizeof(*info));
+    info->submitted = S->submitted;
+    info->completed = S->completed;
+    info->queued = (int64_t)S->queue.size();
+    int64_t running = 0;
+    for (Chain *c : S->chains) running += c->busy ? 1 : 0;
+    info->running = running;
+    info->chains = (int32_t)S->chains.size();
+    info->hbm_bytes = (double)S->used;
+    if (!S->lat_ms.empty()) {
+        std::vector<double> v = S->lat_ms;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) {
+            const size_t i = std::min(v.size() - 1, (size_t)std::floor(q * (double)(v.size() - 1) + 0.5));
+            return v[i];
+        };
+        info->p50_ms = pct(0.50);
+        info->p99_ms = pct(0.99);
+        double s = 0.0;
+        for (double x : v) s += x;
+        info->mean_ms = s / (double)v.size();
+    }
+    return SKR_OK;
+}
+
+skr_status skr_server_destroy(skr_server *S) {
+    if (!S) return SKR_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->queue.clear();
+    }
+    S->cv.notify_one();
+    if (S->th.joinable()) S->th.join();
+    for (Chain *c : S->chains) destroy_chain(c);
+    for (auto &kv : S->reqs) delete kv.second;
+    delete S;
+    return SKR_OK;
+}
+
+}  // extern "C"

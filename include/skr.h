@@ -68,7 +68,8 @@ typedef int32_t skr_status;
 /* right preconditioner M (App. D.3): the Krylov method solves A M^-1 y = b, x = M^-1 y */
 #define SKR_PC_NONE           0
 #define SKR_PC_JACOBI         1   /* M = diag(A) */
-#define SKR_PC_ILU0           2   /* M = L U with the pattern of A (reserved) */
+#define SKR_PC_ILU0           2   /* M = L U, ILU(0) of A in red-black order (no fill; both
+                                     triangular solves are two parallel colour sweeps) */
 
 /* precision form */
 #define SKR_PREC_FP64         0   /* all vectors and reductions in FP64 */

@@ -6,6 +6,12 @@ App. D.3 lists the preconditioners; this build uses three of them:
   * ilu0:   M = L U, the incomplete LU factorisation with no fill, i.e. L
             and U keep exactly the sparsity pattern of A (App. D.3 item 7).
 
+Reading for ILU(0) (the paper does not fix the ordering): the unknowns of
+the 5/7-point grid are taken in red-black order (red: even i + j [+ l]),
+ILU(0) is computed for that reordered matrix, and M is mapped back to the
+natural numbering.  With this ordering both triangular solves are two
+parallel sweeps over one colour each.
+
 Right preconditioning (a reading; the paper does not state the side): the
 Krylov method solves (A M^-1) x_hat = b and x = M^-1 x_hat, so its residual
 is the unpreconditioned residual b - A x.
@@ -64,17 +70,42 @@ def ilu0(A):
     return L.tocsr(), U.tocsr()
 
 
-class RightPreconditioner:
-    """M^-1 as an operator, for M in {none, jacobi, ilu0}."""
+def redblack_permutation(grid):
+    """Red unknowns (even coordinate sum) first, then black; ascending within a colour.
 
-    def __init__(self, A, kind):
+    grid: (nx, ny) or (nx, ny, nz), unknowns numbered with the last index fastest.
+    Returns perm with perm[new] = old.
+    """
+    coords = np.indices(grid).reshape(len(grid), -1)
+    color = coords.sum(axis=0) % 2
+    return np.concatenate([np.nonzero(color == 0)[0], np.nonzero(color == 1)[0]])
+
+
+def ilu0_redblack(A, grid):
+    """ILU(0) of the red-black reordered matrix: (perm, L, U) with
+    A[perm][:, perm] ~ L U on the pattern."""
+    perm = redblack_permutation(grid)
+    Ap = sp.csr_matrix(A)[perm][:, perm]
+    L, U = ilu0(Ap)
+    return perm, L, U
+
+
+class RightPreconditioner:
+    """M^-1 as an operator, for M in {none, jacobi, ilu0}.
+
+    ilu0 needs the grid shape (red-black ordering, see the module readings).
+    """
+
+    def __init__(self, A, kind, grid=None):
         self.kind = kind
         if kind == "none":
             pass
         elif kind == "jacobi":
             self.dinv = jacobi_inv_diag(A)
         elif kind == "ilu0":
-            self.L, self.U = ilu0(A)
+            if grid is None:
+                raise ValueError("ilu0 needs the grid shape")
+            self.perm, self.L, self.U = ilu0_redblack(A, grid)
         else:
             raise ValueError(kind)
 
@@ -83,5 +114,9 @@ class RightPreconditioner:
             return np.array(v, dtype=np.float64, copy=True)
         if self.kind == "jacobi":
             return self.dinv * v
-        y = spla.spsolve_triangular(self.L, v, lower=True, unit_diagonal=True)
-        return spla.spsolve_triangular(self.U, y, lower=False)
+        vp = np.asarray(v, dtype=np.float64)[self.perm]
+        y = spla.spsolve_triangular(self.L, vp, lower=True, unit_diagonal=True)
+        z = spla.spsolve_triangular(self.U, y, lower=False)
+        out = np.empty_like(z)
+        out[self.perm] = z
+        return out

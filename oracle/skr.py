@@ -22,6 +22,16 @@ from .precond import RightPreconditioner
 from .krylov import RecycleState, refresh, gcrodr_solve
 
 
+def grid_of(system):
+    """Interior grid shape of a system description (None for a bare matrix)."""
+    kind = system["kind"]
+    if kind in ("darcy2d", "darcy3d"):
+        return tuple(s - 2 for s in np.shape(system["loga"]))
+    if kind == "convdiff2d":
+        return (system["nside"], system["nside"])
+    return system.get("grid")
+
+
 def assemble(system):
     """Build (A, b) for one system description (a dict from the workload module)."""
     kind = system["kind"]
@@ -38,14 +48,14 @@ def assemble(system):
 
 
 def solve_system(A, b, precond, m, k, tol, state, precision="fp64", inner_tol=1e-5,
-                 max_refine=10, max_steps=10**4):
+                 max_refine=10, max_steps=10**4, grid=None):
     """Solve one system, updating the carried recycle state in place.
 
     Returns (x, info) with info = dict(steps, cycles, matvecs, refinements,
     relres, converged).  `steps` counts Arnoldi steps (one operator
     application each); `matvecs` also counts the k products of the refresh.
     """
-    M = RightPreconditioner(A, precond)
+    M = RightPreconditioner(A, precond, grid)
 
     def op(v):
         return A @ M.apply(v)
@@ -96,7 +106,7 @@ def solve_sequence(systems, order, precond, m, k, tol, precision="fp64", nchains
         for idx in chain:
             A, b = assemble(systems[idx])
             x, info = solve_system(A, b, precond, m, k, tol, state, precision, inner_tol,
-                                   max_refine, max_steps)
+                                   max_refine, max_steps, grid=grid_of(systems[idx]))
             xs[idx] = x
             infos[idx] = info
     return xs, infos

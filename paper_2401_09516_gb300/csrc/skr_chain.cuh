@@ -353,6 +353,47 @@ __device__ void spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
                (unsigned long long)(vout ? 0 : 1) * c.g.n * sizeof(T);
 }
 
+// Operator pass with the red-black ILU(0) right preconditioner:
+// vout = s * src (if vout), z = M^-1 (s * src) in two colour sweeps, then
+// y = A z (= s * src on red rows).  Two extra cluster barriers: the second
+// sweep reads the neighbours' black z, the last one their red z.
+template <typename T>
+__device__ void ilu_spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
+    const T *inv = c.Aw + (long long)7 * c.ld;
+    T *z = c.col(COL_Z);
+    const long long hi = c.lo + c.cnt;
+    for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
+        if (p < c.g.n) {
+            if (vout) vout[p] = s * __ldcg(src + p);
+            if (grid_color(c.g, p) == 1) z[p] = ilu_sweep1_row<T, T>(c.g, c.Aw, c.ld, inv, src, s, p);
+        } else {
+            if (vout) vout[p] = T(0);
+            z[p] = T(0);
+            y[p] = T(0);
+        }
+    }
+    cl_sync();
+    for (long long p = c.lo + threadIdx.x; p < hi && p < c.g.n; p += blockDim.x) {
+        if (grid_color(c.g, p) == 0) {
+            z[p] = ilu_sweep2_row<T, T>(c.g, c.Aw, c.ld, inv, src, s, z, p);
+            y[p] = s * __ldcg(src + p);
+        }
+    }
+    cl_sync();
+    for (long long p = c.lo + threadIdx.x; p < hi && p < c.g.n; p += blockDim.x)
+        if (grid_color(c.g, p) == 1) y[p] = ilu_black_apply_row(c.g, c.Aw, c.ld, z, p);
+    __syncthreads();
+    c.bytes += (unsigned long long)(6 + (vout ? 1 : 0) + 2 * c.g.nst) * c.g.n * sizeof(T);
+}
+
+template <typename T>
+__device__ __forceinline__ void operator_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
+    if (c.precond == SKR_PC_ILU0)
+        ilu_spmv_pass(c, src, s, vout, y);
+    else
+        spmv_pass(c, src, s, vout, y);
+}
+
 // Tiled CTA partials of X_a . Y_b (a < na from column xa0, b < nb from
 // column yb0), into out[a * nb + b].
 template <typename T>
@@ -421,7 +462,7 @@ __device__ void assemble_system(Ctx<T> &c, const DevSystem &sys) {
             system_row(sys, c.g, c.anode, p, row);
             for (int s = 0; s < c.g.nst; s++) c.A64[(long long)s * c.ld + p] = row[s];
             c.b[p] = sys.rhs ? sys.rhs[p] : 1.0;
-            c.dinv[p] = (c.precond == SKR_PC_JACOBI) ? 1.0 / row[0] : 1.0;
+            c.dinv[p] = (c.precond == SKR_PC_NONE) ? 1.0 : 1.0 / row[0];
         } else {
             for (int s = 0; s < c.g.nst; s++) c.A64[(long long)s * c.ld + p] = 0.0;
             c.b[p] = 0.0;
@@ -429,15 +470,32 @@ __device__ void assemble_system(Ctx<T> &c, const DevSystem &sys) {
         }
     }
     cl_sync();
-    for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
-        if (p < c.g.n) {
-            for (int s = 0; s < c.g.nst; s++) {
-                const long long q = nb_index(c.g, p, s);
-                const double a = c.A64[(long long)s * c.ld + p];
-                c.Aw[(long long)s * c.ld + p] = (T)(a * __ldcg(c.dinv + q));
+    if (c.precond == SKR_PC_ILU0) {
+        // red-black ILU(0): inverse pivots (black ones need the neighbours'
+        // rows), and the unscaled operator in working precision
+        T *inv = c.Aw + (long long)7 * c.ld;
+        for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
+            if (p < c.g.n) {
+                const double ip = ilu_inv_pivot(c.g, c.A64, c.ld, p);
+                c.dinv[p] = ip;
+                inv[p] = (T)ip;
+                for (int s = 0; s < c.g.nst; s++) c.Aw[(long long)s * c.ld + p] = (T)c.A64[(long long)s * c.ld + p];
+            } else {
+                inv[p] = T(0);
+                for (int s = 0; s < c.g.nst; s++) c.Aw[(long long)s * c.ld + p] = T(0);
             }
-        } else {
-            for (int s = 0; s < c.g.nst; s++) c.Aw[(long long)s * c.ld + p] = T(0);
+        }
+    } else {
+        for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
+            if (p < c.g.n) {
+                for (int s = 0; s < c.g.nst; s++) {
+                    const long long q = nb_index(c.g, p, s);
+                    const double a = c.A64[(long long)s * c.ld + p];
+                    c.Aw[(long long)s * c.ld + p] = (T)(a * __ldcg(c.dinv + q));
+                }
+            } else {
+                for (int s = 0; s < c.g.nst; s++) c.Aw[(long long)s * c.ld + p] = T(0);
+            }
         }
     }
     __syncthreads();
@@ -476,6 +534,9 @@ __device__ void refresh_recycle(Ctx<T> &c) {
     const int cC0 = COL_C_END - kc;
     // W = A M^-1 U into the C columns
     const long long hi = c.lo + c.cnt;
+    if (c.precond == SKR_PC_ILU0) {
+        for (int b = 0; b < kc; b++) ilu_spmv_pass(c, c.col(COL_U0 + b), T(1), (T *)nullptr, c.col(cC0 + b));
+    } else
     for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
         T acc[KMAX];
 #pragma unroll
@@ -629,7 +690,7 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
     for (int j = 0; j < L; j++) {
         T *y = c.col(ycur);
         // S: V_j = s * src; y = A M^-1 V_j; dots [C, V_0..V_j] . y and y . y
-        spmv_pass(c, src, s, c.col(COL_V0 + j), y);
+        operator_pass(c, src, s, c.col(COL_V0 + j), y);
         c.tick(PH_SPMV);
         const int q = kc + j + 1;
         part_multidot(c, cQ0, q, y, c.template red<T>());
@@ -1036,9 +1097,22 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx) {
                 c.tick(PH_REFRESH);
             }
         }
-        // x += M^-1 d
-        for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x)
-            c.x[p] += c.dinv[p] * (double)dh[p];
+        // x += M^-1 d (FP64)
+        if (c.precond == SKR_PC_ILU0) {
+            cl_sync();   // d of the neighbours
+            for (long long p = c.lo + threadIdx.x; p < hi && p < c.g.n; p += blockDim.x)
+                if (grid_color(c.g, p) == 1)
+                    c.r[p] = ilu_sweep1_row<double, T>(c.g, c.A64, c.ld, c.dinv, dh, 1.0, p);
+            cl_sync();
+            for (long long p = c.lo + threadIdx.x; p < hi && p < c.g.n; p += blockDim.x)
+                if (grid_color(c.g, p) == 0)
+                    c.r[p] = ilu_sweep2_row<double, T>(c.g, c.A64, c.ld, c.dinv, dh, 1.0, c.r, p);
+            __syncthreads();
+            for (long long p = c.lo + threadIdx.x; p < hi && p < c.g.n; p += blockDim.x) c.x[p] += c.r[p];
+        } else {
+            for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x)
+                c.x[p] += c.dinv[p] * (double)dh[p];
+        }
         __syncthreads();
         c.refinements += 1;
         c.bytes += (unsigned long long)c.g.n * (8 * 3 + sizeof(T));
@@ -1081,7 +1155,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS, CHAIN_MIN_BLOCKS) chain_kernel(
     c.ld = a.ws.ld;
     c.basis = reinterpret_cast<T *>(a.ws.basis) + (long long)slot * NCOLS * c.ld;
     c.A64 = a.ws.A64 + (long long)slot * 7 * c.ld;
-    c.Aw = reinterpret_cast<T *>(a.ws.Aw) + (long long)slot * 7 * c.ld;
+    c.Aw = reinterpret_cast<T *>(a.ws.Aw) + (long long)slot * AW_SLOTS * c.ld;
     c.dinv = a.ws.dinv + (long long)slot * c.ld;
     c.x = a.ws.x + (long long)slot * c.ld;
     c.r = a.ws.r + (long long)slot * c.ld;

@@ -19,6 +19,7 @@ constexpr int LDH = MMAX + 1;     // leading dimension of the small FP64 matrice
 //   Y0, Y1                    ping-pong scratch for the Arnoldi vector w
 //   RW                        inner residual (working precision)
 //   DH                        inner correction d (working precision)
+//   Z                         ILU(0) sweep scratch
 // C directly precedes V, so [C_k, V_1..V_j] is one contiguous column range.
 constexpr int COL_C_END = KMAX;
 constexpr int COL_V0 = KMAX;
@@ -27,7 +28,10 @@ constexpr int COL_Y0 = COL_U0 + KMAX;
 constexpr int COL_Y1 = COL_Y0 + 1;
 constexpr int COL_RW = COL_Y0 + 2;
 constexpr int COL_DH = COL_Y0 + 3;
-constexpr int NCOLS = COL_Y0 + 4;
+constexpr int COL_Z = COL_Y0 + 4;
+constexpr int NCOLS = COL_Y0 + 5;
+// Operator slots per slot: NST coefficient arrays, plus (ILU) the inverse pivots in slot 7.
+constexpr int AW_SLOTS = 8;
 
 // One system as the kernels see it (device pointers).
 struct DevSystem {
@@ -49,7 +53,7 @@ struct DevResult {
 struct Workspace {
     void *basis;              // NCOLS * ld elements of T per slot
     double *A64;              // 7 * ld doubles per slot (unfolded matrix)
-    void *Aw;                 // 7 * ld elements of T per slot (right-preconditioned operator)
+    void *Aw;                 // AW_SLOTS * ld elements of T per slot (right-preconditioned operator)
     double *dinv;             // ld per slot (Jacobi: 1/diag, else 1)
     double *x, *r, *b;        // ld per slot each (FP64 solution, residual, rhs)
     double *anode;            // node scratch per slot (exp(log a)), nodecap doubles

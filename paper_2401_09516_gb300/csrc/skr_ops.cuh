@@ -52,4 +52,35 @@ __global__ void apply_kernel(Geom g, const T *Aw, long long ld, const T *v, doub
         y[p] = (double)stencil_apply_row(g, Aw, ld, v, T(1), p);
 }
 
+// red-black ILU(0) for the stand-alone operator entry point
+__global__ void ilu_pivot_kernel(Geom g, const double *A, long long ld, double *inv) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n;
+         p += (long long)gridDim.x * blockDim.x)
+        inv[p] = ilu_inv_pivot(g, A, ld, p);
+}
+
+template <typename T>
+__global__ void ilu_fold_kernel(Geom g, const double *A, long long ld, const double *inv, T *Aw, T *invw) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n;
+         p += (long long)gridDim.x * blockDim.x) {
+        for (int s = 0; s < g.nst; s++) Aw[(long long)s * ld + p] = (T)A[(long long)s * ld + p];
+        invw[p] = (T)inv[p];
+    }
+}
+
+template <typename T>
+__global__ void ilu_sweep_kernel(Geom g, const T *Aw, long long ld, const T *inv, const T *v, T *z, double *y,
+                                 int stage) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int col = grid_color(g, p);
+        if (stage == 1 && col == 1) z[p] = ilu_sweep1_row<T, T>(g, Aw, ld, inv, v, T(1), p);
+        if (stage == 2 && col == 0) {
+            z[p] = ilu_sweep2_row<T, T>(g, Aw, ld, inv, v, T(1), z, p);
+            y[p] = (double)v[p];
+        }
+        if (stage == 3 && col == 1) y[p] = (double)ilu_black_apply_row(g, Aw, ld, z, p);
+    }
+}
+
 }  // namespace skr

@@ -383,7 +383,8 @@ skr_status skr_server_create(const skr_options *opt_in, size_t hbm_budget, int32
         return err(SKR_ERR_INVALID_ARG, "bad maxit, max_refine or tol");
     if (opt.precision == SKR_PREC_MIXED && !(opt.inner_tol > 0.0 && opt.inner_tol < 1.0))
         return err(SKR_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
-    if (opt.precond != SKR_PC_NONE && opt.precond != SKR_PC_JACOBI) return err(SKR_ERR_INVALID_ARG, "preconditioner not available");
+    if (opt.precond != SKR_PC_NONE && opt.precond != SKR_PC_JACOBI && opt.precond != SKR_PC_ILU0)
+        return err(SKR_ERR_INVALID_ARG, "unknown preconditioner");
     if (opt.precision != SKR_PREC_FP64 && opt.precision != SKR_PREC_MIXED) return err(SKR_ERR_INVALID_ARG, "bad precision");
     if (opt.cluster_size < 0 || opt.cluster_size > 16) return err(SKR_ERR_INVALID_ARG, "cluster_size in [0, 16]");
     if (max_chains < 0) return err(SKR_ERR_INVALID_ARG, "max_chains < 0");

@@ -176,4 +176,78 @@ __device__ __forceinline__ double residual_row(const Geom &g, const double *A, l
     return b[p] - acc;
 }
 
+// ---------------------------------------------------------------- ILU(0), red-black
+//
+// ILU(0) of the matrix reordered red (even coordinate sum) before black.
+// Every neighbour of a black unknown is red and vice versa, so L and U keep
+// A's pattern with no elimination in the red rows: M = L U has
+//   red rows:   M_rr = a_rr, M_rb = a_rb,
+//   black rows: L_br = a_br / a_rr, U_bb = d_b = a_bb - sum_r a_br a_rb / a_rr,
+// and M^-1 v is two sweeps: z_b = (v_b - sum_r (a_br / a_rr) v_r) / d_b, then
+// z_r = (v_r - sum_b a_rb z_b) / a_rr.  The red rows of A M^-1 are unit rows,
+// and A M^-1 v = v on red rows, a_bb z_b + sum_r a_br z_r on black rows.
+
+__device__ __forceinline__ int grid_color(const Geom &g, long long p) {
+    if (g.nst == 5) {
+        const long long i = p / g.ny, j = p - i * g.ny;
+        return (int)((i + j) & 1);
+    }
+    const long long nyz = (long long)g.ny * g.nz;
+    const long long i = p / nyz, rem = p - i * nyz, j = rem / g.nz, l = rem - j * g.nz;
+    return (int)((i + j + l) & 1);
+}
+
+// slot of the coefficient that couples the neighbour back to p
+__device__ __forceinline__ int opposite_slot(int s) { return (s & 1) ? s + 1 : s - 1; }
+
+// 1 / pivot of row p: 1/a_pp (red) or 1/d_p (black).  A: FP64 rows, halo through L2.
+__device__ __forceinline__ double ilu_inv_pivot(const Geom &g, const double *A, long long ld, long long p) {
+    const double app = A[p];
+    if (grid_color(g, p) == 0) return 1.0 / app;
+    double d = app;
+    for (int s = 1; s < g.nst; s++) {
+        const double apq = A[(long long)s * ld + p];
+        if (apq == 0.0) continue;
+        const long long q = p + g.off[s];
+        const double aqp = __ldcg(A + (long long)opposite_slot(s) * ld + q);
+        d -= apq * aqp / __ldcg(A + q);
+    }
+    return 1.0 / d;
+}
+
+// sweep 1 (black rows): z_b = inv_b (v_b - sum_r a_br inv_r v_r), v = scale * src
+template <typename R, typename Tv>
+__device__ __forceinline__ R ilu_sweep1_row(const Geom &g, const R *Aw, long long ld, const R *inv, const Tv *src,
+                                            R scale, long long p) {
+    R acc = scale * (R)__ldcg(src + p);
+    for (int s = 1; s < g.nst; s++) {
+        const long long q = nb_index(g, p, s);
+        acc -= Aw[(long long)s * ld + p] * __ldcg(inv + q) * (scale * (R)__ldcg(src + q));
+    }
+    return inv[p] * acc;
+}
+
+// sweep 2 (red rows): z_r = inv_r (v_r - sum_b a_rb z_b)
+template <typename R, typename Tv>
+__device__ __forceinline__ R ilu_sweep2_row(const Geom &g, const R *Aw, long long ld, const R *inv, const Tv *src,
+                                            R scale, const R *z, long long p) {
+    R acc = scale * (R)__ldcg(src + p);
+    for (int s = 1; s < g.nst; s++) {
+        const long long q = nb_index(g, p, s);
+        acc -= Aw[(long long)s * ld + p] * __ldcg(z + q);
+    }
+    return inv[p] * acc;
+}
+
+// A z on a black row: a_bb z_b + sum_r a_br z_r
+template <typename R>
+__device__ __forceinline__ R ilu_black_apply_row(const Geom &g, const R *Aw, long long ld, const R *z, long long p) {
+    R acc = Aw[p] * __ldcg(z + p);
+    for (int s = 1; s < g.nst; s++) {
+        const long long q = nb_index(g, p, s);
+        acc += Aw[(long long)s * ld + p] * __ldcg(z + q);
+    }
+    return acc;
+}
+
 }  // namespace skr

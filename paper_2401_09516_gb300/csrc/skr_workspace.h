@@ -29,7 +29,7 @@ inline SlabLayout slab_layout(int nslots, long long ld, long long nodecap, size_
     };
     L.o_basis = take((size_t)nslots * NCOLS * ld * esz);
     L.o_A64 = take((size_t)nslots * 7 * ld * 8);
-    L.o_Aw = take((size_t)nslots * 7 * ld * esz);
+    L.o_Aw = take((size_t)nslots * AW_SLOTS * ld * esz);
     L.o_dinv = take((size_t)nslots * ld * 8);
     L.o_x = take((size_t)nslots * ld * 8);
     L.o_r = take((size_t)nslots * ld * 8);

@@ -5,6 +5,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from oracle import assembly, krylov, precond, skr
+from oracle import precond as oprecond
 from workloads import darcy2d_sequence
 
 
@@ -35,6 +36,32 @@ def test_ilu0_matches_a_on_its_pattern_and_has_no_fill():
     assert set(zip(*U.nonzero())) <= set(zip(*np.nonzero(np.triu(Ad))))
     # and ILU(0) is not the exact LU for the 5-point pattern (fill is dropped)
     assert np.abs(LU - Ad).max() > 1e-6
+
+
+@pytest.mark.parametrize("grid", [(6, 5), (6, 6), (4, 3, 5)])
+def test_redblack_ilu0_closed_form(grid):
+    # in red-black order the red rows of L and U carry no elimination, the
+    # black pivots are a_bb - sum_r a_br a_rb / a_rr, and the red rows of
+    # A M^-1 are unit rows
+    rng = np.random.default_rng(len(grid))
+    if len(grid) == 2:
+        A, _ = assembly.convdiff2d(0.05, (17.0, -9.0), grid[0]) if grid[0] == grid[1] else \
+            assembly.darcy2d(rng.standard_normal((grid[0] + 2, grid[1] + 2)))
+    else:
+        A, _ = assembly.darcy3d(rng.standard_normal(tuple(g + 2 for g in grid)))
+    perm, L, U = oprecond.ilu0_redblack(A, grid)
+    Ap = A.toarray()[perm][:, perm]
+    nred = int((np.indices(grid).reshape(len(grid), -1).sum(0) % 2 == 0).sum())
+    Ud = U.diagonal()
+    np.testing.assert_allclose(Ud[:nred], np.diag(Ap)[:nred], rtol=1e-15)
+    for bi in range(nred, Ap.shape[0]):
+        reds = np.nonzero(Ap[bi, :nred])[0]
+        want = Ap[bi, bi] - sum(Ap[bi, r] * Ap[r, bi] / Ap[r, r] for r in reds)
+        assert np.isclose(Ud[bi], want, rtol=1e-13)
+    M = oprecond.RightPreconditioner(A, "ilu0", grid)
+    AM = np.stack([A @ M.apply(e) for e in np.eye(A.shape[0])], axis=1)
+    reds_nat = perm[:nred]
+    np.testing.assert_allclose(AM[reds_nat], np.eye(A.shape[0])[reds_nat], atol=1e-12)
 
 
 def test_jacobi_right_preconditioner():
@@ -80,7 +107,7 @@ def test_projected_arnoldi_relation_eq4():
 def test_solution_matches_dense_lu(k, pc):
     A, b = _darcy(10, seed=2)
     state = krylov.RecycleState()
-    x, info = skr.solve_system(A, b, pc, 12, k, 1e-10, state)
+    x, info = skr.solve_system(A, b, pc, 12, k, 1e-10, state, grid=(10, 10))
     xd = np.linalg.solve(A.toarray(), b)
     assert info["converged"] and info["relres"] <= 1e-10
     assert np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)

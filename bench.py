@@ -280,32 +280,55 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def cpu_baseline(budget_s, systems_cap=None):
-    """The FP64 oracle on the host, on a prefix of the sorted chain, as it stands."""
-    import numpy as np
-    from oracle import skr as oskr, sort as osort
-    from workloads import darcy2d_sequence
+class OracleChain:
+    """The FP64 oracle walking the sorted 200-system chain on the host, as it stands.
 
-    W = WORKLOAD
-    L = darcy2d_sequence(W["nside"], W["nsys"], W["ell"], W["sigma"], seed=W["seed"])
-    t0 = time.perf_counter()
-    order = osort.greedy_sort(L.reshape(W["nsys"], -1))
-    t_sort = time.perf_counter() - t0
-    state = None
-    from oracle.krylov import RecycleState
-    state = RecycleState()
-    done = 0
-    t1 = time.perf_counter()
-    for idx in order:
-        A, b = oskr.assemble(dict(kind="darcy2d", loga=L[idx]))
-        oskr.solve_system(A, b, W["precond"], W["m"], W["k"], W["tol"], state, precision="mixed",
-                          inner_tol=W["inner_tol"])
-        done += 1
-        if time.perf_counter() - t1 > budget_s or (systems_cap and done >= systems_cap):
-            break
-    t_solve = time.perf_counter() - t1
-    per_sys = t_solve / done + t_sort / W["nsys"]
-    return {"value": round(1.0 / per_sys, 4), "unit": "systems/s", "cores": 1, "kind": "oracle",
+    The greedy sort of all 200 systems runs once and its cost is amortised
+    over the 200 systems; each sample then solves consecutive systems of the
+    sorted order (carrying the recycle space along the chain) until its time
+    budget is spent, at least one system.
+    """
+
+    def __init__(self):
+        from oracle import sort as osort
+        from oracle.krylov import RecycleState
+        from workloads import darcy2d_sequence
+
+        W = WORKLOAD
+        self.L = darcy2d_sequence(W["nside"], W["nsys"], W["ell"], W["sigma"], seed=W["seed"])
+        t0 = time.perf_counter()
+        self.order = osort.greedy_sort(self.L.reshape(W["nsys"], -1))
+        self.t_sort = time.perf_counter() - t0
+        self._new_state = RecycleState
+        self.state = RecycleState()
+        self.pos = 0
+
+    def sample(self, budget_s):
+        """Solve along the chain for about budget_s seconds; returns (systems/s, systems done)."""
+        from oracle import skr as oskr
+
+        W = WORKLOAD
+        done = 0
+        t1 = time.perf_counter()
+        while True:
+            if self.pos == len(self.order):
+                self.pos, self.state = 0, self._new_state()
+            A, b = oskr.assemble(dict(kind="darcy2d", loga=self.L[self.order[self.pos]]))
+            oskr.solve_system(A, b, W["precond"], W["m"], W["k"], W["tol"], self.state,
+                              precision="mixed", inner_tol=W["inner_tol"])
+            self.pos += 1
+            done += 1
+            if time.perf_counter() - t1 > budget_s:
+                break
+        per_sys = (time.perf_counter() - t1) / done + self.t_sort / W["nsys"]
+        return 1.0 / per_sys, done
+
+
+def cpu_baseline(budget_s):
+    """One bounded oracle sample beside the GPU line."""
+    ch = OracleChain()
+    v, done = ch.sample(budget_s)
+    return {"value": round(v, 4), "unit": "systems/s", "cores": 1, "kind": "oracle",
             "sample": "first %d systems of the sorted 200-system chain (sort of all 200 amortised), "
                       "numpy/scipy FP64, BLAS threads = 1" % done}
 
@@ -314,11 +337,25 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    cb = cpu_baseline(args.ref_seconds)
+    ch = OracleChain()
+    budget = max(1.0, min(args.ref_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        ch.sample(budget)
+    vals, counts = [], []
+    for _ in range(args.steps):
+        v, done = ch.sample(budget)
+        vals.append(v)
+        counts.append(done)
+    value = sum(vals) / len(vals)
+    cb = {"value": round(value, 4), "unit": "systems/s", "cores": 1, "kind": "oracle",
+          "sample": "%d timed samples of consecutive systems along the sorted 200-system chain "
+                    "(%s systems each, after %d untimed samples; sort of all 200 amortised), "
+                    "numpy/scipy FP64, BLAS threads = 1" % (args.steps, "/".join(map(str, counts)),
+                                                           args.warmup)}
     line = {
         "metric": METRIC, "value": cb["value"], "unit": "systems/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(WORKLOAD["nsys"] / cb["value"] * 1e3, 3),
+        "ms_per_step": round(WORKLOAD["nsys"] / value * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
         "config": {"workload": "darcy2d 256x256 (n=65536), 200 systems, a=exp(GRF ell=0.1 sigma=1), f=1, "
@@ -342,7 +379,8 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-seconds", type=float, default=20.0)
+    ap.add_argument("--ref-seconds", type=float, default=20.0,
+                    help="upper bound on one reference sample")
     args = ap.parse_args()
     for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ.setdefault(var, "1")

@@ -361,3 +361,29 @@ def test_solve_convdiff_ilu0_matches_oracle(skr, precision):
 def spla_solve(A, b):
     import scipy.sparse.linalg as spla
     return spla.spsolve(A.tocsc(), b)
+
+
+def test_batched_chains_of_mixed_grids_in_one_launch(skr):
+    # independent sorted chains of different grid sides, one launch
+    from workloads import batched_chains
+    chains = batched_chains(5, 3, sides=(16, 24, 40), ell_range=(0.1, 0.3), seed=31)
+    systems, order, offs, fields = [], [], [0], []
+    for side, ell, sub in chains:
+        perm = osort.greedy_sort(sub.reshape(len(sub), -1))
+        base = len(systems)
+        for l in sub:
+            systems.append(skr.darcy2d(_dev(l)))
+            fields.append(l)
+        order += [base + p for p in perm]
+        offs.append(len(systems))
+    opt = skr.skr_options_default(m=30, k=8, tol=1e-8, precond="jacobi", precision="mixed")
+    xs, res = skr.skr_solve_sequence(systems, order=order, chain_offsets=offs, nchains=len(chains),
+                                     options=opt)
+    for i, l in enumerate(fields):
+        A, b = assembly.darcy2d(l)
+        assert res[i]["flag"] == 0, res[i]
+        _check_solution(xs[i], A, b, 1e-8, spla_solve(A, b), 1e-6)
+    # chains mixing grids are rejected
+    with pytest.raises(skr.SkrError):
+        skr.skr_solve_sequence(systems, order=order, chain_offsets=[0, 2, len(systems)], nchains=2,
+                               options=opt)

@@ -34,11 +34,13 @@ constexpr int CHAIN_MIN_BLOCKS = 1;
 
 template <> struct Tiles<float> {
     static constexpr int G = 32;   // columns per multi-dot group
+    static constexpr int G2 = 16;  // columns per group of the two-target multi-dot
     static constexpr int TA = 8;   // Gram tile rows
     static constexpr int TB = 8;   // Gram tile cols
 };
 template <> struct Tiles<double> {
     static constexpr int G = 16;
+    static constexpr int G2 = 8;
     static constexpr int TA = 4;
     static constexpr int TB = 8;
 };
@@ -74,7 +76,7 @@ struct SmemPlan {
         o_Z, o_wr, o_wi, o_xr, o_xi, o_vscr, o_P, o_GP, o_Qc, o_Rc, o_tau, o_D, o_sc, o_Tco, o_mon,
         o_int, total;
     // offsets inside the T coefficient region (in T elements)
-    int t_h, t_cC, t_cU, t_cr, t_cd, t_total;
+    int t_h, t_cC, t_cU, t_cr, t_cd, t_s, t_al, t_total;
 };
 
 __host__ __device__ inline int align2(int x) { return (x + 1) & ~1; }
@@ -85,7 +87,7 @@ __host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads, int es
     P.k = k;
     P.nwarps = nthreads / 32;
     P.ldh = m + 1;
-    int rc = m + 8;
+    int rc = 2 * m + 8;   // the Arnoldi step reduces 2 q + 3 <= 2 m + 3 values
     if ((m + 1) * k + 2 * k + 8 > rc) rc = (m + 1) * k + 2 * k + 8;
     if (k * k + 8 > rc) rc = k * k + 8;
     P.redcap = align2(rc);
@@ -126,7 +128,9 @@ __host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads, int es
     P.t_cU = P.t_cC + align2((m + 1) * ks);
     P.t_cr = P.t_cU + align2(m * ks);
     P.t_cd = P.t_cr + align2(m + 2);
-    P.t_total = P.t_cd + align2(m + k + 2);
+    P.t_s = (P.t_cd + m + k + 2 + 3) & ~3;   // 16-byte aligned
+    P.t_al = P.t_s + ((m + 4 + 3) & ~3);
+    P.t_total = P.t_al + ((m + 4 + 3) & ~3);
     // the eigenvector workspace (xr, xi, in the eigen-solve precision, which
     // has the working element size) and the Gram tile buffer live in the
     // coefficient region: it is written only after the eigen-solve
@@ -240,31 +244,103 @@ __device__ void part_multidot(Ctx<T> &c, int c0, int q, const T *y, T *out) {
     c.bytes += (unsigned long long)(q + 1) * c.g.n * sizeof(T);
 }
 
-// y -= sum_j h[j] Q_j over own rows (q columns from c0); optionally the CTA
-// partial of ||y||^2 into *nrm_out.
-template <typename T>
-__device__ void update_rows(Ctx<T> &c, int c0, int q, const T *h, T *y, T *nrm_out) {
+// CTA partials of the dots of one Arnoldi step with delayed
+// re-orthogonalisation, over own rows, for the q basis columns Z from c0:
+//   out[0..q) = Z^T u (if DU), out[q..2q) = Z^T w (if DW),
+//   out[2q] = u.u (if DU), out[2q+1] = u.w (if DW), out[2q+2] = w.w (if DW).
+// u is the not yet re-orthogonalised candidate, w = A M^-1 u.  Columns go in
+// groups of G2 with two accumulators each; u and w are re-read per group.
+template <typename T, bool DU, bool DW>
+__device__ void part_dual_dots(Ctx<T> &c, int c0, int q, const T *u, const T *w, T *out) {
+    typedef typename Vec<T>::type VT;
+    constexpr int E = Vec<T>::N, G = Tiles<T>::G2, NV = 2 * G + 3;
+    const int nvec = (int)(c.cnt / E);
+    const VT *uv = reinterpret_cast<const VT *>(u + c.lo);
+    const VT *wv = reinterpret_cast<const VT *>(w + c.lo);
+    T *wsum = reinterpret_cast<T *>(c.D(c.P.o_wsum));
+    const int ng = max(1, (q + G - 1) / G);
+    for (int gi = 0; gi < ng; gi++) {
+        const int g0 = gi * G;
+        const int gq = max(0, min(G, q - g0));
+        const bool first = (gi == 0);
+        T acc[NV];
+#pragma unroll
+        for (int e = 0; e < NV; e++) acc[e] = T(0);
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+            const VT uu = uv[i];
+            const VT ww = DW ? wv[i] : uu;
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                if (j < gq) {
+                    const VT xv = reinterpret_cast<const VT *>(c.col(c0 + g0 + j) + c.lo)[i];
+                    if (DU) acc[j] += vdot(xv, uu);
+                    if (DW) acc[G + j] += vdot(xv, ww);
+                }
+            }
+            if (first) {
+                if (DU) acc[2 * G] += vdot(uu, uu);
+                if (DW) {
+                    acc[2 * G + 1] += vdot(uu, ww);
+                    acc[2 * G + 2] += vdot(ww, ww);
+                }
+            }
+        }
+        // warp sums, then warps in index order, scattered into out
+        const int lane = lane_id(), wp = warp_id(), nw = num_warps();
+#pragma unroll
+        for (int e = 0; e < NV; e++) {
+            const T v = warp_sum(acc[e]);
+            if (lane == 0) wsum[wp * NV + e] = v;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < NV; e += blockDim.x) {
+            int dst = -1;
+            if (e < G) {
+                if (DU && e < gq) dst = g0 + e;
+            } else if (e < 2 * G) {
+                if (DW && e - G < gq) dst = q + g0 + (e - G);
+            } else if (first) {
+                dst = 2 * q + (e - 2 * G);
+            }
+            if (dst >= 0) {
+                T sacc = T(0);
+                for (int r = 0; r < nw; r++) sacc += wsum[r * NV + e];
+                out[dst] = sacc;
+            }
+        }
+        __syncthreads();
+    }
+    c.bytes += (unsigned long long)(q + (DU ? 1 : 0) + (DW ? 1 : 0)) * c.g.n * sizeof(T);
+}
+
+// The update of one Arnoldi step with delayed re-orthogonalisation, over own
+// rows: vout = (u - Z sv) * rinv (the finished basis vector) and, if NEXT,
+// the next candidate w <- w * rinv - Z al - bet * vout, in place over w.
+template <typename T, bool NEXT>
+__device__ void dual_update(Ctx<T> &c, int c0, int q, const T *sv, const T *al, T bet, T rinv, const T *u,
+                            T *w, T *vout) {
     typedef typename Vec<T>::type VT;
     constexpr int E = Vec<T>::N;
     const int nvec = (int)(c.cnt / E);
-    VT *yv = reinterpret_cast<VT *>(y + c.lo);
-    T acc[1] = {T(0)};
+    const VT *uv = reinterpret_cast<const VT *>(u + c.lo);
+    VT *wv = reinterpret_cast<VT *>(w + c.lo);
+    VT *ov = reinterpret_cast<VT *>(vout + c.lo);
     for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-        VT yy = yv[i];
+        VT vv = uv[i];
+        VT nx = vv;
+        if (NEXT) nx = vscale(wv[i], rinv);
 #pragma unroll 8
         for (int j = 0; j < q; j++) {
             const VT xv = reinterpret_cast<const VT *>(c.col(c0 + j) + c.lo)[i];
-            yy = vaxmy(yy, h[j], xv);
+            vv = vaxmy(vv, sv[j], xv);
+            if (NEXT) nx = vaxmy(nx, al[j], xv);
         }
-        yv[i] = yy;
-        acc[0] += vdot(yy, yy);
+        vv = vscale(vv, rinv);
+        ov[i] = vv;
+        if (NEXT) wv[i] = vaxmy(nx, bet, vv);
     }
-    if (nrm_out) {
-        block_sum<1>(acc, 1, reinterpret_cast<T *>(c.D(c.P.o_wsum)), nrm_out);
-    } else {
-        __syncthreads();
-    }
-    c.bytes += (unsigned long long)(q + 2) * c.g.n * sizeof(T);
+    __syncthreads();
+    c.bytes += (unsigned long long)(q + 2 + (NEXT ? 2 : 0)) * c.g.n * sizeof(T);
 }
 
 // Operator pass of an Arnoldi step: for own rows, vout = s * src (the new
@@ -679,88 +755,119 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
     const int ldh = c.P.ldh;
     double *H = c.D(c.P.o_H), *Bm = c.D(c.P.o_B);
     const int cQ0 = COL_C_END - kc;   // [C, V_1, ...] start
-    T *h = c.tco(c.P.t_h);
+    if (L <= 0) return rnw;
     const T tiny = (sizeof(T) == 4) ? T(1e-6) : T(1e-13);
 
-    const T *src = c.col(COL_RW);
-    T s = (T)(1.0 / rnw);
-    int ycur = COL_Y0;
-    int jdone = 0;
+    // Arnoldi with delayed re-orthogonalisation.  Step j holds the
+    // candidate u for V_j after one classical Gram-Schmidt pass against
+    // Z = [C, V_0..V_{j-1}] (u = rw for j = 0).  One operator pass gives
+    // w = A M^-1 u; one reduction gives Z^T u, Z^T w, u.u, u.w, w.w.  From
+    // them: the second-pass coefficients s = Z^T u finish column j-1 of
+    // [B; H] and V_j = (u - Z s) / rho; A M^-1 V_j follows from w and the
+    // Arnoldi relation of the finished columns, which gives column j's
+    // first-pass coefficients without another pass over Z; one update pass
+    // writes V_j and the next candidate.  The term A M^-1 C s_C (s_C: the
+    // rounding-level second-pass coefficients against C) is not available
+    // and is dropped.
+    T *sv = c.tco(c.P.t_s), *al = c.tco(c.P.t_al);
+    double *gq = c.D(c.P.o_dscr);   // e = B s_V (kc entries), then g = H s_V (j + 1 entries)
+    int ucol = COL_RW, wcol = COL_Y0;
+    double rho = rnw, anorm = 0.0;
+    int Ld = 0;
     bool early = false;
-    for (int j = 0; j < L; j++) {
-        T *y = c.col(ycur);
-        // S: V_j = s * src; y = A M^-1 V_j; dots [C, V_0..V_j] . y and y . y
-        operator_pass(c, src, s, c.col(COL_V0 + j), y);
+    cl_sync();   // the operator reads the neighbours' rows of rw
+    for (int j = 0;; j++) {
+        const bool last = (j == L);
+        T *u = c.col(ucol), *w = c.col(wcol);
+        if (!last) {
+            operator_pass(c, u, T(1), (T *)nullptr, w);
+            c.matvecs += 1;
+        }
         c.tick(PH_SPMV);
-        const int q = kc + j + 1;
-        part_multidot(c, cQ0, q, y, c.template red<T>());
-        {
-            T acc[1] = {T(0)};
-            typedef typename Vec<T>::type VT;
-            const int nvec = (int)(c.cnt / Vec<T>::N);
-            for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-                const VT yy = reinterpret_cast<const VT *>(y + c.lo)[i];
-                acc[0] += vdot(yy, yy);
+        const int q = kc + j;
+        T *red = c.template red<T>();
+        if (j == 0)
+            part_dual_dots<T, false, true>(c, cQ0, q, u, w, red);
+        else if (last)
+            part_dual_dots<T, true, false>(c, cQ0, q, u, w, red);
+        else
+            part_dual_dots<T, true, true>(c, cQ0, q, u, w, red);
+        allreduce<T, T>(c, 2 * q + 3);
+        c.tick(PH_DOT);
+        const T *vv = c.template vals<T>();
+        bool stop = last, brk = false;
+        double st = 0.0;
+        if (j > 0) {
+            // finish column j-1: add the second-pass coefficients, H(j, j-1) = rho
+            double ss = 0.0;
+            for (int i = 0; i < q; i++) {
+                const double si = (double)vv[i];
+                ss += si * si;
+                if (!last) st += si * (double)vv[q + i];
             }
-            block_sum<1>(acc, 1, reinterpret_cast<T *>(c.D(c.P.o_wsum)), c.template red<T>() + q);
+            const double r2 = (double)vv[2 * q] - ss;
+            rho = (r2 > 0.0) ? sqrt(r2) : 0.0;
+            for (int i = threadIdx.x; i < q; i += blockDim.x) {
+                if (i < kc)
+                    M_(Bm, kc, i, j - 1) += (double)vv[i];
+                else
+                    M_(H, ldh, i - kc, j - 1) += (double)vv[i];
+            }
+            if (threadIdx.x == 0) M_(H, ldh, j, j - 1) = rho;
+            for (int i = j + 1 + threadIdx.x; i <= c.m; i += blockDim.x) M_(H, ldh, i, j - 1) = 0.0;
+            __syncthreads();
+            c.steps += 1;
+            const float est = monitor_step(c, j - 1, (float)rnw);
+            brk = !(rho > (double)tiny * anorm);
+            if (brk) c.breakdown = true;
+            if (est <= (float)target || brk) {
+                stop = true;
+                early = true;
+            }
         }
-        allreduce<T, T>(c, q + 1);
-        c.tick(PH_DOT);
-        const T ynorm = sqrt(c.template vals<T>()[q]);
-        for (int i = threadIdx.x; i < q; i += blockDim.x) {
-            const T v = c.template vals<T>()[i];
-            h[i] = v;
-            if (i < kc)
-                M_(Bm, kc, i, j) = (double)v;
-            else
-                M_(H, ldh, i - kc, j) = (double)v;
-        }
-        __syncthreads();
-        update_rows(c, cQ0, q, h, y, (T *)nullptr);
-        c.tick(PH_UPD);
-        // second Gram-Schmidt pass
-        part_multidot(c, cQ0, q, y, c.template red<T>());
-        allreduce<T, T>(c, q);
-        c.tick(PH_DOT);
-        for (int i = threadIdx.x; i < q; i += blockDim.x) {
-            const T v = c.template vals<T>()[i];
-            h[i] = v;
-            if (i < kc)
-                M_(Bm, kc, i, j) += (double)v;
-            else
-                M_(H, ldh, i - kc, j) += (double)v;
-        }
-        __syncthreads();
-        update_rows(c, cQ0, q, h, y, c.template red<T>());
-        allreduce<T, T>(c, 1);
-        c.tick(PH_UPD);
-        const T hn = sqrt(c.template vals<T>()[0]);
-        if (threadIdx.x == 0) M_(H, ldh, j + 1, j) = (double)hn;
-        for (int i = j + 2 + threadIdx.x; i <= c.m; i += blockDim.x) M_(H, ldh, i, j) = 0.0;
-        __syncthreads();
-        c.steps += 1;
-        c.matvecs += 1;
-        const float est = monitor_step(c, j, (float)rnw);
-        c.tick(PH_OTHER);
-        const bool brk = !(hn > tiny * ynorm);
-        src = y;
-        s = brk ? T(0) : T(1) / hn;
-        ycur = (ycur == COL_Y0) ? COL_Y1 : COL_Y0;
-        jdone = j + 1;
-        if (brk) c.breakdown = true;
-        if (est <= (float)target || brk) {
-            early = true;
+        const double rinv = brk ? 0.0 : 1.0 / rho;
+        for (int i = threadIdx.x; i < q; i += blockDim.x) sv[i] = (j > 0) ? vv[i] : T(0);
+        if (stop) {
+            __syncthreads();
+            c.tick(PH_OTHER);
+            dual_update<T, false>(c, cQ0, q, sv, al, T(0), (T)rinv, u, w, c.col(COL_V0 + j));
+            c.tick(PH_UPD);
+            Ld = j;
             break;
         }
-    }
-    if (jdone == 0) return rnw;
-    // materialise V_{jdone} = s * src (own rows only)
-    {
-        T *v = c.col(COL_V0 + jdone);
-        for (long long p = c.lo + threadIdx.x; p < c.lo + c.cnt; p += blockDim.x) v[p] = s * src[p];
+        // e = B(:, 0:j) s_V, g = H(0:j+1, 0:j) s_V over the finished columns
+        for (int i = threadIdx.x; i <= q; i += blockDim.x) {
+            double acc = 0.0;
+            for (int l = 0; l < j; l++) {
+                const double sl = (double)vv[kc + l];
+                acc += ((i < kc) ? M_(Bm, kc, i, l) : M_(H, ldh, i - kc, l)) * sl;
+            }
+            gq[i] = acc;
+        }
         __syncthreads();
+        // column j (first pass): Z^T A M^-1 V_j and V_j^T A M^-1 V_j; the
+        // update coefficients al (Z) and al[q] (V_j)
+        for (int i = threadIdx.x; i <= q; i += blockDim.x) {
+            double h1;
+            if (i < q)
+                h1 = ((double)vv[q + i] - gq[i]) * rinv;
+            else
+                h1 = (((double)vv[2 * q + 1] - st) * rinv - gq[q]) * rinv;
+            if (i < kc)
+                M_(Bm, kc, i, j) = h1;
+            else
+                M_(H, ldh, i - kc, j) = h1;
+            al[i] = (T)(gq[i] * rinv + h1);
+        }
+        anorm = sqrt(fmax((double)vv[2 * q + 2], 0.0)) * rinv;
+        __syncthreads();
+        c.tick(PH_OTHER);
+        dual_update<T, true>(c, cQ0, q, sv, al, al[q], (T)rinv, u, w, c.col(COL_V0 + j));
+        c.tick(PH_UPD);
+        cl_sync();   // the next operator pass reads the neighbours' rows of the candidate
+        ucol = wcol;
+        wcol = (wcol == COL_Y0) ? COL_Y1 : COL_Y0;
     }
-    const int Ld = jdone;
     const bool full = (!early) && (Ld == Lmax) && (c.k > 0);
     const int mt = kc + Ld;
     // Gram pass for the harmonic-Ritz problem: [C, V_0..V_Ld]^T U and ||u_b||^2

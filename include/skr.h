@@ -52,6 +52,8 @@ typedef int32_t skr_status;
 #define SKR_NOT_CONVERGED     1   /* Arnoldi step cap (maxit) or refinement cap hit */
 #define SKR_BREAKDOWN         2   /* Arnoldi or QR breakdown without convergence */
 #define SKR_NUMERICAL         3   /* NaN or Inf in a residual */
+#define SKR_DEVICE_STALL      4   /* a bounded device-side wait for a staged copy ran out (2 s);
+                                     the system's result is not valid */
 
 /* problem formats (skr_system.fmt).  Unknowns are numbered row-major with
  * the last grid index fastest: p = i*ny + j (2D), p = (i*ny + j)*nz + l (3D),

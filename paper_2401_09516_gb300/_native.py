@@ -26,6 +26,7 @@ SKR_CONVERGED = 0
 SKR_NOT_CONVERGED = 1
 SKR_BREAKDOWN = 2
 SKR_NUMERICAL = 3
+SKR_DEVICE_STALL = 4
 SKR_FMT_DARCY2D = 1
 SKR_FMT_DARCY3D = 2
 SKR_FMT_CONVDIFF2D = 3

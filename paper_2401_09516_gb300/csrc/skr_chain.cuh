@@ -68,18 +68,34 @@ __device__ __forceinline__ void ld4(const double *p, double &a, double &b, doubl
 }
 
 // Shared-memory layout, computed identically on host and device.
+//
+// The regions that live through the Arnoldi steps (reductions, H, B, the
+// coefficient vectors, the monitor, control ints, mbarriers) come first.
+// Behind them one region holds, at different times, either the small dense
+// scratch of a cycle end and of a recycle refresh (R_H, the Givens data, F/M,
+// the Schur vectors, P_k, the QR factors) or the staging ring of the
+// streaming passes; no streaming pass runs while that scratch is live.
 struct SmemPlan {
     int m, k, nwarps;
     int ldh, redcap, redsz;   // redsz: one reduction buffer, in doubles
     // offsets in doubles
     int o_red, o_vals, o_wsum, o_H, o_B, o_Rw, o_gvec, o_y2, o_gam, o_avec, o_gc, o_gs, o_dscr, o_F,
         o_Z, o_wr, o_wi, o_xr, o_xi, o_vscr, o_P, o_GP, o_Qc, o_Rc, o_tau, o_D, o_sc, o_Tco, o_mon,
-        o_int, total;
+        o_int, o_bar, o_ring, total;
+    // staging ring: ring_ns stages of (m + 2) column segments of ring_rows rows
+    int ring_ns, ring_rows, ring_stage;   // ring_stage in doubles
     // offsets inside the T coefficient region (in T elements)
     int t_h, t_cC, t_cU, t_cr, t_cd, t_s, t_al, t_total;
 };
 
 __host__ __device__ inline int align2(int x) { return (x + 1) & ~1; }
+
+// Shared memory of one CTA on sm_103 (opt-in maximum) and the staging
+// ring's depth (its segment is RING_SEG_BYTES: one row of a TMA box).
+constexpr int SMEM_LIMIT_BYTES = 227 * 1024;
+constexpr int RING_MAX_NS = 3;
+// A staged copy that has not landed after this long is recorded as a stall.
+constexpr unsigned long long RING_WAIT_NS = 2000000000ull;
 
 __host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads, int esz) {
     SmemPlan P;
@@ -94,33 +110,13 @@ __host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads, int es
     P.redsz = align2((P.redcap * esz + 7) / 8);   // reductions are in the working precision
     const int kk = k + 1;
     int o = 0;
+    // ---- live through the Arnoldi steps
     P.o_red = o;   o += 2 * P.redsz;
     P.o_vals = o;  o += P.redsz;
     P.o_wsum = o;  o += align2(P.nwarps * 32);
     P.o_H = o;     o += align2(P.ldh * m);
     P.o_B = o;     o += align2(k * m);
-    P.o_Rw = o;    o += align2(P.ldh * m);
-    P.o_gvec = o;  o += align2(m + 2);
-    P.o_y2 = o;    o += align2(m + 2);
-    P.o_gam = o;   o += align2(m + 2);
-    P.o_avec = o;  o += align2(k + 2);
-    P.o_gc = o;    o += align2(m + 2);
-    P.o_gs = o;    o += align2(m + 2);
     P.o_dscr = o;  o += align2(2 * m + 4);
-    P.o_F = o;     o += align2(P.ldh * (m > k ? m : k));   // F / M; also the refresh Gram
-    P.o_Z = o;     o += align2(m * m > 2 * k * k ? m * m : 2 * k * k);  // Schur vectors; also R, R^-1
-    P.o_wr = o;    o += align2(m);
-    P.o_wi = o;    o += align2(m);
-    P.o_vscr = o;  o += align2(m + 2);
-    P.o_P = o;     o += align2(m * kk);
-    // G P_k and its Q factor are formed after the eigen-solve, when the F/M
-    // and R_H regions are free again
-    P.o_GP = P.o_F;
-    P.o_Qc = P.o_Rw;
-    P.o_Rc = o;    o += align2(kk * kk);
-    P.o_tau = o;   o += align2(kk + 1);
-    P.o_D = o;     o += align2(k + 2);
-    P.o_sc = o;    o += 16;
     // T coefficient region (sized in doubles: T is at most 8 bytes)
     P.t_h = 0;
     P.t_cC = P.t_h + ((m + 4 + 3) & ~3);   // multiple of 4 elements: float4 loads
@@ -143,7 +139,41 @@ __host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads, int es
     P.o_xi = P.o_Tco + xsz;
     P.o_mon = o;   o += align2(3 * m + 4);             // FP32 Givens monitor (as floats, room to spare)
     P.o_int = o;   o += align2(64 + 8 + 3 * MMAX);      // control ints
-    P.total = o;
+    P.o_bar = o;   o += 8;                              // one mbarrier per stage (<= 8)
+    // ---- shared region, 1024-byte aligned: dense scratch or staging ring
+    o = (o + 127) & ~127;
+    const int u0 = o;
+    P.o_Rw = o;    o += align2(P.ldh * m);
+    P.o_gvec = o;  o += align2(m + 2);
+    P.o_y2 = o;    o += align2(m + 2);
+    P.o_gam = o;   o += align2(m + 2);
+    P.o_avec = o;  o += align2(k + 2);
+    P.o_gc = o;    o += align2(m + 2);
+    P.o_gs = o;    o += align2(m + 2);
+    P.o_F = o;     o += align2(P.ldh * (m > k ? m : k));   // F / M; also the refresh Gram
+    P.o_Z = o;     o += align2(m * m > 2 * k * k ? m * m : 2 * k * k);  // Schur vectors; also R, R^-1
+    P.o_wr = o;    o += align2(m);
+    P.o_wi = o;    o += align2(m);
+    P.o_vscr = o;  o += align2(m + 2);
+    P.o_P = o;     o += align2(m * kk);
+    // G P_k and its Q factor are formed after the eigen-solve, when the F/M
+    // and R_H regions are free again
+    P.o_GP = P.o_F;
+    P.o_Qc = P.o_Rw;
+    P.o_Rc = o;    o += align2(kk * kk);
+    P.o_tau = o;   o += align2(kk + 1);
+    P.o_D = o;     o += align2(k + 2);
+    P.o_sc = o;    o += 16;
+    const int dense_end = o;
+    P.o_ring = u0;
+    P.ring_rows = RING_SEG_BYTES / esz;
+    P.ring_stage = (m + 2) * RING_SEG_BYTES / 8;
+    int ns = (int)((SMEM_LIMIT_BYTES / 8 - u0) / P.ring_stage);
+    if (ns > RING_MAX_NS) ns = RING_MAX_NS;
+    if (ns < 2) ns = 2;   // the plan then exceeds the limit and the launch is refused
+    P.ring_ns = ns;
+    const int ring_end = u0 + ns * P.ring_stage;
+    P.total = dense_end > ring_end ? dense_end : ring_end;
     return P;
 }
 
@@ -177,6 +207,13 @@ struct Ctx {
     // optional per-phase device time (rank 0, thread 0)
     unsigned long long *prof;
     unsigned long long tmark;
+    // staging ring: stage buffers, one mbarrier per stage, and the number of
+    // row blocks staged so far (block t uses stage t % ns, phase t / ns)
+    T *ring;
+    unsigned long long *bars;
+    unsigned long long ring_seq;
+    const CUtensorMap *tm8, *tm1;   // basis boxes of 8 and 1 columns
+    int ybase;                      // first column of this slot in the tensor maps
 
     __device__ __forceinline__ void tick(int ph) {
         if (prof != nullptr && rank == 0 && threadIdx.x == 0) {
@@ -244,73 +281,131 @@ __device__ void part_multidot(Ctx<T> &c, int c0, int q, const T *y, T *out) {
     c.bytes += (unsigned long long)(q + 1) * c.g.n * sizeof(T);
 }
 
+// Control int set when a staged copy did not land within RING_WAIT_NS.
+constexpr int INT_STALL = 6;
+
 // CTA partials of the dots of one Arnoldi step with delayed
 // re-orthogonalisation, over own rows, for the q basis columns Z from c0:
 //   out[0..q) = Z^T u (if DU), out[q..2q) = Z^T w (if DW),
 //   out[2q] = u.u (if DU), out[2q+1] = u.w (if DW), out[2q+2] = w.w (if DW).
-// u is the not yet re-orthogonalised candidate, w = A M^-1 u.  Columns go in
-// groups of G2 with two accumulators each; u and w are re-read per group.
+// u (column ucol) is the not yet re-orthogonalised candidate, w (column
+// wcol) = A M^-1 u.
+//
+// The rows stream through the shared-memory ring: for every block of R rows,
+// warp 0 issues TMA boxes of {R rows x 8 columns} (and single columns for the
+// remainder, u and w) onto the stage's mbarrier, ring_ns - 1 blocks ahead of
+// the block being consumed, so the bytes in flight do not depend on
+// registers.  Thread t owns row t % R of every block and the columns
+// j = t / R (mod NGRP); each column's partial is then summed over its
+// group's warps in index order.
 template <typename T, bool DU, bool DW>
-__device__ void part_dual_dots(Ctx<T> &c, int c0, int q, const T *u, const T *w, T *out) {
-    typedef typename Vec<T>::type VT;
-    constexpr int E = Vec<T>::N, G = Tiles<T>::G2, NV = 2 * G + 3;
-    const int nvec = (int)(c.cnt / E);
-    const VT *uv = reinterpret_cast<const VT *>(u + c.lo);
-    const VT *wv = reinterpret_cast<const VT *>(w + c.lo);
-    T *wsum = reinterpret_cast<T *>(c.D(c.P.o_wsum));
-    const int ng = max(1, (q + G - 1) / G);
-    for (int gi = 0; gi < ng; gi++) {
-        const int g0 = gi * G;
-        const int gq = max(0, min(G, q - g0));
-        const bool first = (gi == 0);
-        T acc[NV];
+__device__ void staged_dual_dots(Ctx<T> &c, int c0, int q, int ucol, int wcol, T *out) {
+    constexpr int R = RING_SEG_BYTES / (int)sizeof(T);
+    constexpr int NGRP = CHAIN_THREADS / R;
+    constexpr int WPG = R / 32;   // warps per column group
+    constexpr int CM = (MMAX + NGRP - 1) / NGRP;
+    constexpr int NVW = 2 * CM + 3;
+    static_assert(NGRP >= 1 && R % 32 == 0, "ring geometry");
+    const int NS = c.P.ring_ns;
+    const int stage_elems = (c.m + 2) * R;
+    const int nseg = q + 1 + (DW ? 1 : 0);
+    const int n8 = q / 8, nreq = n8 + (q % 8) + 1 + (DW ? 1 : 0);
+    const long long cnt = c.cnt;
+    const int nblk = (int)((cnt + R - 1) / R);
+    const int lane = lane_id(), wp = warp_id();
+    const int gi = threadIdx.x / R, row = threadIdx.x % R;
+    // the columns were written by generic stores of this CTA's threads
+    fence_proxy_async_global();
+    __syncthreads();
+    auto issue = [&](int blk) {
+        const unsigned long long seq = c.ring_seq + (unsigned long long)blk;
+        const int st = (int)(seq % (unsigned long long)NS);
+        T *dst = c.ring + (long long)st * stage_elems;
+        const int x = (int)(c.lo + (long long)blk * R);
+        if (lane == 0) mbar_arrive_expect(c.bars + st, (unsigned)(nseg * R * (int)sizeof(T)));
+        __syncwarp();
+        for (int t = lane; t < nreq; t += 32) {
+            if (t < n8) {
+                tma_load_2d(dst + 8 * t * R, c.tm8, x, c.ybase + c0 + 8 * t, c.bars + st);
+            } else {
+                const int r = t - n8;   // single columns: Z remainder, then u, then w
+                int sg, colx;
+                if (8 * n8 + r < q) {
+                    sg = 8 * n8 + r;
+                    colx = c0 + sg;
+                } else {
+                    sg = q + (8 * n8 + r - q);
+                    colx = (sg == q) ? ucol : wcol;
+                }
+                tma_load_2d(dst + sg * R, c.tm1, x, c.ybase + colx, c.bars + st);
+            }
+        }
+    };
+    if (wp == 0)
+        for (int b0 = 0; b0 < NS - 1 && b0 < nblk; b0++) issue(b0);
+    T acc[NVW];
 #pragma unroll
-        for (int e = 0; e < NV; e++) acc[e] = T(0);
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-            const VT uu = uv[i];
-            const VT ww = DW ? wv[i] : uu;
+    for (int e = 0; e < NVW; e++) acc[e] = T(0);
+    for (int b0 = 0; b0 < nblk; b0++) {
+        if (wp == 0 && b0 + NS - 1 < nblk) issue(b0 + NS - 1);
+        const unsigned long long seq = c.ring_seq + (unsigned long long)b0;
+        const int st = (int)(seq % (unsigned long long)NS);
+        if (!mbar_wait_bounded(c.bars + st, (unsigned)((seq / (unsigned long long)NS) & 1ull), RING_WAIT_NS))
+            c.ints()[INT_STALL] = 1;
+        const T *sb = c.ring + (long long)st * stage_elems;
+        const long long rows = min((long long)R, cnt - (long long)b0 * R);
+        if (row < rows) {
+            const T uu = sb[q * R + row];
+            const T ww = DW ? sb[(q + 1) * R + row] : T(0);
 #pragma unroll
-            for (int j = 0; j < G; j++) {
-                if (j < gq) {
-                    const VT xv = reinterpret_cast<const VT *>(c.col(c0 + g0 + j) + c.lo)[i];
-                    if (DU) acc[j] += vdot(xv, uu);
-                    if (DW) acc[G + j] += vdot(xv, ww);
+            for (int jj = 0; jj < CM; jj++) {
+                const int j = jj * NGRP + gi;
+                if (j < q) {
+                    const T z = sb[j * R + row];
+                    if (DU) acc[2 * jj] += z * uu;
+                    if (DW) acc[2 * jj + 1] += z * ww;
                 }
             }
-            if (first) {
-                if (DU) acc[2 * G] += vdot(uu, uu);
+            if (gi == 0) {
+                if (DU) acc[2 * CM] += uu * uu;
                 if (DW) {
-                    acc[2 * G + 1] += vdot(uu, ww);
-                    acc[2 * G + 2] += vdot(ww, ww);
+                    acc[2 * CM + 1] += uu * ww;
+                    acc[2 * CM + 2] += ww * ww;
                 }
             }
         }
-        // warp sums, then warps in index order, scattered into out
-        const int lane = lane_id(), wp = warp_id(), nw = num_warps();
-#pragma unroll
-        for (int e = 0; e < NV; e++) {
-            const T v = warp_sum(acc[e]);
-            if (lane == 0) wsum[wp * NV + e] = v;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < NV; e += blockDim.x) {
-            int dst = -1;
-            if (e < G) {
-                if (DU && e < gq) dst = g0 + e;
-            } else if (e < 2 * G) {
-                if (DW && e - G < gq) dst = q + g0 + (e - G);
-            } else if (first) {
-                dst = 2 * q + (e - 2 * G);
-            }
-            if (dst >= 0) {
-                T sacc = T(0);
-                for (int r = 0; r < nw; r++) sacc += wsum[r * NV + e];
-                out[dst] = sacc;
-            }
-        }
-        __syncthreads();
+        __syncthreads();   // the stage may be refilled
     }
-    c.bytes += (unsigned long long)(q + (DU ? 1 : 0) + (DW ? 1 : 0)) * c.g.n * sizeof(T);
+    c.ring_seq += (unsigned long long)nblk;
+    // warp sums, then the warps of each column group in index order
+    T *wsum = reinterpret_cast<T *>(c.D(c.P.o_wsum));
+#pragma unroll
+    for (int e = 0; e < NVW; e++) {
+        const T v = warp_sum(acc[e]);
+        if (lane == 0) wsum[wp * NVW + e] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * q + 3; e += blockDim.x) {
+        int g, slot;
+        bool want;
+        if (e < 2 * q) {
+            const int j = (e < q) ? e : e - q;
+            g = j % NGRP;
+            slot = 2 * (j / NGRP) + ((e < q) ? 0 : 1);
+            want = (e < q) ? DU : DW;
+        } else {
+            g = 0;   // u.u, u.w, w.w are accumulated by group 0
+            slot = 2 * CM + (e - 2 * q);
+            want = (e == 2 * q) ? DU : DW;
+        }
+        if (want) {
+            T sacc = T(0);
+            for (int r = 0; r < WPG; r++) sacc += wsum[(g * WPG + r) * NVW + slot];
+            out[e] = sacc;
+        }
+    }
+    __syncthreads();
+    c.bytes += (unsigned long long)nseg * c.g.n * sizeof(T);
 }
 
 // The update of one Arnoldi step with delayed re-orthogonalisation, over own
@@ -787,11 +882,11 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
         const int q = kc + j;
         T *red = c.template red<T>();
         if (j == 0)
-            part_dual_dots<T, false, true>(c, cQ0, q, u, w, red);
+            staged_dual_dots<T, false, true>(c, cQ0, q, ucol, wcol, red);
         else if (last)
-            part_dual_dots<T, true, false>(c, cQ0, q, u, w, red);
+            staged_dual_dots<T, true, false>(c, cQ0, q, ucol, wcol, red);
         else
-            part_dual_dots<T, true, true>(c, cQ0, q, u, w, red);
+            staged_dual_dots<T, true, true>(c, cQ0, q, ucol, wcol, red);
         allreduce<T, T>(c, 2 * q + 3);
         c.tick(PH_DOT);
         const T *vv = c.template vals<T>();
@@ -1229,6 +1324,9 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx) {
     c.bytes += (unsigned long long)c.g.n * 16;
     cl_sync();
     if (c.rank == 0 && threadIdx.x == 0) {
+        int stall = 0;
+        for (unsigned q = 0; q < c.cs; q++) stall |= *cl_map(c.ints() + INT_STALL, q);
+        if (stall) flag = SKR_DEVICE_STALL;
         DevResult res;
         res.steps = c.steps;
         res.cycles = c.cycles;
@@ -1246,8 +1344,8 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(CHAIN_THREADS, CHAIN_MIN_BLOCKS) chain_kernel(const ChainArgs a) {
-    extern __shared__ __align__(16) double smem_dyn[];
+__global__ void __launch_bounds__(CHAIN_THREADS, CHAIN_MIN_BLOCKS) chain_kernel(const __grid_constant__ ChainArgs a) {
+    extern __shared__ __align__(1024) double smem_dyn[];
     Ctx<T> c;
     c.rank = cl_rank();
     c.cs = cl_size();
@@ -1271,7 +1369,19 @@ __global__ void __launch_bounds__(CHAIN_THREADS, CHAIN_MIN_BLOCKS) chain_kernel(
     c.bytes = 0;
     c.prof = a.prof;
     c.tmark = 0;
+    c.ring = reinterpret_cast<T *>(smem_dyn + c.P.o_ring);
+    c.bars = reinterpret_cast<unsigned long long *>(smem_dyn + c.P.o_bar);
+    c.ring_seq = 0;
+    c.tm8 = &a.tm8;
+    c.tm1 = &a.tm1;
+    c.ybase = slot * NCOLS;
     int *ictl = c.ints();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < c.P.ring_ns; i++) mbar_init(c.bars + i, 1);
+        mbar_init_fence();
+        ictl[INT_STALL] = 0;   // sticky for the launch
+    }
+    __syncthreads();
     for (;;) {
         if (c.rank == 0 && threadIdx.x == 0) ictl[0] = atomicAdd(a.chain_counter, 1);
         cl_sync();

@@ -2,6 +2,7 @@
 // kernels.  Nothing here is part of the public ABI (include/skr.h).
 #pragma once
 
+#include <cuda.h>
 #include <stdint.h>
 
 #include "../../include/skr.h"
@@ -32,6 +33,11 @@ constexpr int COL_Z = COL_Y0 + 4;
 constexpr int NCOLS = COL_Y0 + 5;
 // Operator slots per slot: NST coefficient arrays, plus (ILU) the inverse pivots in slot 7.
 constexpr int AW_SLOTS = 8;
+
+// Streaming passes stage the basis through shared memory in blocks of rows:
+// one segment is one column over RING_SEG_BYTES / sizeof(T) rows.  The TMA
+// boxes are {segment rows x 8 columns} and {segment rows x 1 column}.
+constexpr int RING_SEG_BYTES = 1024;
 
 // One system as the kernels see it (device pointers).
 struct DevSystem {
@@ -77,6 +83,9 @@ struct ChainArgs {
     int *chain_kc;                // per-chain recycle dimension carried between launches
                                   // (optional: read at chain start, written at chain end;
                                   // the chain's U_k, C_k stay in its workspace slot)
+    // TMA descriptors of the basis slab of all slots, seen as one 2D array:
+    // ld rows (contiguous) x nslots * NCOLS columns (stride ld elements)
+    CUtensorMap tm8, tm1;
 };
 
 enum Phase { PH_ASM, PH_REFRESH, PH_PROJ, PH_SPMV, PH_DOT, PH_UPD, PH_GRAM, PH_DENSE, PH_CUPD, PH_RESID, PH_OTHER };

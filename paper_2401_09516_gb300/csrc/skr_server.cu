@@ -25,6 +25,7 @@
 
 #include "skr_common.h"
 #include "skr_launch.h"
+#include "skr_tma.h"
 #include "skr_workspace.h"
 
 namespace skr {
@@ -248,6 +249,9 @@ bool launch(skr_server *S, Chain *c, Request *r) {
     a.bytes = c->dbytes;
     a.prof = nullptr;
     a.chain_kc = c->dkc;
+    if (encode_basis_maps(a.ws.basis, a.ws.ld, a.ws.nslots, S->opt.precision == SKR_PREC_FP64 ? 8 : 4, &a.tm8,
+                          &a.tm1) != cudaSuccess)
+        return false;
     const cudaError_t e = (S->opt.precision == SKR_PREC_FP64)
                               ? launch_chain_f64(a, 1, c->cs, S->threads, S->smem, st)
                               : launch_chain_f32(a, 1, c->cs, S->threads, S->smem, st);

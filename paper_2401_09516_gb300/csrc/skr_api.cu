@@ -498,7 +498,7 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     a.bytes = reinterpret_cast<unsigned long long *>(dctr.as<char>() + 32);
     a.prof = opt.profile ? reinterpret_cast<unsigned long long *>(dctr.as<char>() + 64) : nullptr;
     a.chain_kc = nullptr;
-    if (encode_basis_maps(a.ws.basis, ld, nslots, (int)esz, &a.tm8, &a.tm1) != cudaSuccess)
+    if (encode_basis_maps(a.ws.basis, ld, nslots, (int)esz, a.tmap) != cudaSuccess)
         return fail(SKR_ERR_CUDA, "TMA descriptors of the basis could not be encoded");
 
     cudaEvent_t e0, e1;

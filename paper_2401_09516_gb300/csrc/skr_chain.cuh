@@ -81,9 +81,10 @@ struct SmemPlan {
     // offsets in doubles
     int o_red, o_vals, o_wsum, o_H, o_B, o_Rw, o_gvec, o_y2, o_gam, o_avec, o_gc, o_gs, o_dscr, o_F,
         o_Z, o_wr, o_wi, o_xr, o_xi, o_vscr, o_P, o_GP, o_Qc, o_Rc, o_tau, o_D, o_sc, o_Tco, o_mon,
-        o_int, o_bar, o_ring, total;
-    // staging ring: ring_ns stages of (m + 2) column segments of ring_rows rows
-    int ring_ns, ring_rows, ring_stage;   // ring_stage in doubles
+        o_int, o_bar, o_req, o_ring, total;
+    // staging ring: ring_cap doubles; a pass with s segments per block of
+    // ring_rows rows uses min(RING_MAX_NS, ring_cap / (s segments)) stages
+    int ring_cap, ring_rows;
     // offsets inside the T coefficient region (in T elements)
     int t_h, t_cC, t_cU, t_cr, t_cd, t_s, t_al, t_total;
 };
@@ -91,11 +92,17 @@ struct SmemPlan {
 __host__ __device__ inline int align2(int x) { return (x + 1) & ~1; }
 
 // Shared memory of one CTA on sm_103 (opt-in maximum) and the staging
-// ring's depth (its segment is RING_SEG_BYTES: one row of a TMA box).
+// ring's largest depth (one mbarrier per stage; a segment is
+// RING_SEG_BYTES, one row of a TMA box).
 constexpr int SMEM_LIMIT_BYTES = 227 * 1024;
-constexpr int RING_MAX_NS = 3;
-// A staged copy that has not landed after this long is recorded as a stall.
+constexpr int RING_MAX_NS = 8;
+// TMA requests per staged block: at most 4 runs of at most MMAX + 1 columns,
+// each cut into boxes of 16 columns and a binary remainder.
+constexpr int RING_MAX_REQ = 32;
+// A staged copy that has not landed after this long is recorded as a stall;
+// after a stall, the launch waits this long for copies in flight before it ends.
 constexpr unsigned long long RING_WAIT_NS = 2000000000ull;
+constexpr unsigned long long RING_DRAIN_NS = 20000000ull;
 
 __host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads, int esz) {
     SmemPlan P;
@@ -140,6 +147,7 @@ __host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads, int es
     P.o_mon = o;   o += align2(3 * m + 4);             // FP32 Givens monitor (as floats, room to spare)
     P.o_int = o;   o += align2(64 + 8 + 3 * MMAX);      // control ints
     P.o_bar = o;   o += 8;                              // one mbarrier per stage (<= 8)
+    P.o_req = o;   o += RING_MAX_REQ * 3 / 2;           // TMA requests of the current pass (3 ints each)
     // ---- shared region, 1024-byte aligned: dense scratch or staging ring
     o = (o + 127) & ~127;
     const int u0 = o;
@@ -165,14 +173,17 @@ __host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads, int es
     P.o_D = o;     o += align2(k + 2);
     P.o_sc = o;    o += 16;
     const int dense_end = o;
+    // the ring: at least two stages of the widest pass (m + 2 segments)
     P.o_ring = u0;
     P.ring_rows = RING_SEG_BYTES / esz;
-    P.ring_stage = (m + 2) * RING_SEG_BYTES / 8;
-    int ns = (int)((SMEM_LIMIT_BYTES / 8 - u0) / P.ring_stage);
-    if (ns > RING_MAX_NS) ns = RING_MAX_NS;
-    if (ns < 2) ns = 2;   // the plan then exceeds the limit and the launch is refused
-    P.ring_ns = ns;
-    const int ring_end = u0 + ns * P.ring_stage;
+    const int seg = RING_SEG_BYTES / 8;
+    // three stages of the widest pass: a larger ring takes L1 capacity from the
+    // register-streamed passes and measured slower
+    int cap = (SMEM_LIMIT_BYTES / 8 - u0) / seg * seg;
+    if (cap > 3 * (m + 2) * seg) cap = 3 * (m + 2) * seg;
+    if (cap < 2 * (m + 2) * seg) cap = 2 * (m + 2) * seg;   // the plan then exceeds the limit: refused
+    P.ring_cap = cap;
+    const int ring_end = u0 + cap;
     P.total = dense_end > ring_end ? dense_end : ring_end;
     return P;
 }
@@ -207,12 +218,11 @@ struct Ctx {
     // optional per-phase device time (rank 0, thread 0)
     unsigned long long *prof;
     unsigned long long tmark;
-    // staging ring: stage buffers, one mbarrier per stage, and the number of
-    // row blocks staged so far (block t uses stage t % ns, phase t / ns)
+    // staging ring: stage buffers and one mbarrier per stage
     T *ring;
     unsigned long long *bars;
-    unsigned long long ring_seq;
-    const CUtensorMap *tm8, *tm1;   // basis boxes of 8 and 1 columns
+    unsigned phase;   // bit i: parity of the next phase of mbarrier i
+    const CUtensorMap *tmap;        // basis boxes of 16 >> i columns, i < NBOX
     int ybase;                      // first column of this slot in the tensor maps
 
     __device__ __forceinline__ void tick(int ph) {
@@ -284,99 +294,174 @@ __device__ void part_multidot(Ctx<T> &c, int c0, int q, const T *y, T *out) {
 // Control int set when a staged copy did not land within RING_WAIT_NS.
 constexpr int INT_STALL = 6;
 
+// ------------------------------------------------------------------ staged streaming
+
+// A pass that streams the CTA's own rows of up to four runs of contiguous
+// basis columns through the shared-memory ring.  For every block of
+// R = RING_SEG_BYTES / sizeof(T) rows, warp 0 issues TMA boxes of {R rows x
+// 16 columns} and a binary remainder of narrower boxes (one box per lane)
+// onto the stage's mbarrier, ns - 1 blocks ahead of the block being
+// consumed, so the bytes in flight do not depend on registers; ns is as
+// large as the ring allows for this pass's stage size.  In a stage, the runs' columns follow
+// each other, one segment (R elements) per column.  Use:
+//   RingPass rp = ring_begin(c, ...);
+//   for (b = 0; b < rp.nblk; b++) { sb = ring_acquire(c, rp, b); ...; __syncthreads(); }
+//   ring_end(c, rp);
+// Each pass starts at stage 0 and consumes every block it issues, so the
+// ring is empty between passes.
+struct RingPass {
+    int nseg, nreq, nblk, ns, stage_elems;
+};
+
+// Request i of the current pass: ints (segment, column, box index) at
+// ints + 3 i of the plan's request table.
+template <typename T>
+__device__ __forceinline__ int *ring_reqs(Ctx<T> &c) {
+    return reinterpret_cast<int *>(c.sm + c.P.o_req);
+}
+
+template <typename T>
+__device__ __forceinline__ void ring_issue(Ctx<T> &c, const RingPass &rp, int blk) {
+    constexpr int R = RING_SEG_BYTES / (int)sizeof(T);
+    const int lane = lane_id();
+    if (c.ints()[INT_STALL]) return;   // after a stall nothing more is staged
+    const int st = blk % rp.ns;
+    T *dst = c.ring + (long long)st * rp.stage_elems;
+    const int x = (int)(c.lo + (long long)blk * R);
+    if (lane == 0) mbar_arrive_expect(c.bars + st, (unsigned)(rp.nseg * R * (int)sizeof(T)));
+    __syncwarp();
+    if (lane < rp.nreq) {   // one request per lane
+        const int *rq = ring_reqs(c) + 3 * lane;
+        tma_load_2d(dst + rq[0] * R, c.tmap + rq[2], x, c.ybase + rq[1], c.bars + st);
+    }
+}
+
+// Start a pass over the runs (start, length) given in rs/rl (length 0: skipped).
+template <typename T>
+__device__ __forceinline__ RingPass ring_begin_runs(Ctx<T> &c, const int *rs, const int *rl, int nr) {
+    constexpr int R = RING_SEG_BYTES / (int)sizeof(T);
+    RingPass rp;
+    int nseg = 0, nreq = 0;
+    int *rq = ring_reqs(c);
+    // boxes of 16 columns, then a binary remainder (the same on every thread)
+    auto add = [&](int seg, int col, int w) {
+        if (threadIdx.x == 0 && nreq < RING_MAX_REQ) {
+            rq[3 * nreq] = seg;
+            rq[3 * nreq + 1] = col;
+            rq[3 * nreq + 2] = w;
+        }
+        nreq++;
+    };
+    for (int i = 0; i < nr; i++) {
+        if (rl[i] <= 0) continue;
+        int off = 0;
+        for (; rl[i] - off >= 16; off += 16) add(nseg + off, rs[i] + off, 0);
+        for (int w = 1; w < NBOX; w++) {   // remainder < 16: each narrower width at most once
+            const int width = 16 >> w;
+            if (rl[i] - off >= width) {
+                add(nseg + off, rs[i] + off, w);
+                off += width;
+            }
+        }
+        nseg += rl[i];
+    }
+    rp.nseg = nseg;
+    rp.nreq = nreq;
+    rp.nblk = (int)((c.cnt + R - 1) / R);
+    rp.stage_elems = rp.nseg * R;
+    // as many stages of exactly this pass's segments as the ring holds
+    const int cap_elems = (int)((long long)c.P.ring_cap * 8 / (long long)sizeof(T));
+    rp.ns = min(RING_MAX_NS, cap_elems / max(rp.stage_elems, 1));
+    // the columns were written by generic stores of this CTA's threads; the
+    // barrier also publishes the request table
+    fence_proxy_async_global();
+    __syncthreads();
+    if (warp_id() == 0)
+        for (int b0 = 0; b0 < rp.ns - 1 && b0 < rp.nblk; b0++) ring_issue(c, rp, b0);
+    return rp;
+}
+
+// q columns from c0, then the single columns xc0 and xc1 (-1: none).
+template <typename T>
+__device__ __forceinline__ RingPass ring_begin(Ctx<T> &c, int c0, int q, int xc0, int xc1) {
+    const int rs[3] = {c0, xc0, xc1};
+    const int rl[3] = {q, xc0 >= 0 ? 1 : 0, xc1 >= 0 ? 1 : 0};
+    return ring_begin_runs(c, rs, rl, 3);
+}
+
+// Issue the block ns - 1 ahead, wait for block b0; returns its stage.  The
+// caller ends its use of the stage with a CTA barrier.
+template <typename T>
+__device__ __forceinline__ const T *ring_acquire(Ctx<T> &c, const RingPass &rp, int b0) {
+    if (warp_id() == 0 && b0 + rp.ns - 1 < rp.nblk) ring_issue(c, rp, b0 + rp.ns - 1);
+    const int st = b0 % rp.ns;
+    // after a stall the waits are skipped: the launch finishes quickly and
+    // every later system of this CTA is flagged
+    if (c.ints()[INT_STALL] == 0 && !mbar_wait_bounded(c.bars + st, (c.phase >> st) & 1u, RING_WAIT_NS))
+        c.ints()[INT_STALL] = 1;
+    c.phase ^= 1u << st;
+    return c.ring + (long long)st * rp.stage_elems;
+}
+
+template <typename T>
+__device__ __forceinline__ void ring_end(Ctx<T> &c, const RingPass &rp) {
+    c.bytes += (unsigned long long)rp.nseg * c.g.n * sizeof(T);
+}
+
 // CTA partials of the dots of one Arnoldi step with delayed
 // re-orthogonalisation, over own rows, for the q basis columns Z from c0:
 //   out[0..q) = Z^T u (if DU), out[q..2q) = Z^T w (if DW),
 //   out[2q] = u.u (if DU), out[2q+1] = u.w (if DW), out[2q+2] = w.w (if DW).
 // u (column ucol) is the not yet re-orthogonalised candidate, w (column
-// wcol) = A M^-1 u.
-//
-// The rows stream through the shared-memory ring: for every block of R rows,
-// warp 0 issues TMA boxes of {R rows x 8 columns} (and single columns for the
-// remainder, u and w) onto the stage's mbarrier, ring_ns - 1 blocks ahead of
-// the block being consumed, so the bytes in flight do not depend on
-// registers.  Thread t owns row t % R of every block and the columns
-// j = t / R (mod NGRP); each column's partial is then summed over its
-// group's warps in index order.
+// wcol) = A M^-1 u.  The rows stream through the ring.  A staged block holds
+// 64 16-byte vectors per column; thread t owns vector t % 64 of every block
+// and the columns j = t / 64 (mod 8), so each shared-memory load feeds
+// 2 x E multiply-adds.  Each column's partial is then the sum over its
+// group's two warps.
 template <typename T, bool DU, bool DW>
 __device__ void staged_dual_dots(Ctx<T> &c, int c0, int q, int ucol, int wcol, T *out) {
+    typedef typename Vec<T>::type VT;
+    constexpr int E = Vec<T>::N;
     constexpr int R = RING_SEG_BYTES / (int)sizeof(T);
-    constexpr int NGRP = CHAIN_THREADS / R;
-    constexpr int WPG = R / 32;   // warps per column group
-    constexpr int CM = (MMAX + NGRP - 1) / NGRP;
+    constexpr int RV = R / E;                       // vectors per segment
+    constexpr int NGRP = CHAIN_THREADS / RV;        // column groups
+    constexpr int WPG = RV / 32;                    // warps per group
+    constexpr int CM = (MMAX + NGRP - 1) / NGRP;    // columns per thread
     constexpr int NVW = 2 * CM + 3;
-    static_assert(NGRP >= 1 && R % 32 == 0, "ring geometry");
-    const int NS = c.P.ring_ns;
-    const int stage_elems = (c.m + 2) * R;
-    const int nseg = q + 1 + (DW ? 1 : 0);
-    const int n8 = q / 8, nreq = n8 + (q % 8) + 1 + (DW ? 1 : 0);
-    const long long cnt = c.cnt;
-    const int nblk = (int)((cnt + R - 1) / R);
+    static_assert(RV % 32 == 0 && NGRP >= 1, "ring geometry");
     const int lane = lane_id(), wp = warp_id();
-    const int gi = threadIdx.x / R, row = threadIdx.x % R;
-    // the columns were written by generic stores of this CTA's threads
-    fence_proxy_async_global();
-    __syncthreads();
-    auto issue = [&](int blk) {
-        const unsigned long long seq = c.ring_seq + (unsigned long long)blk;
-        const int st = (int)(seq % (unsigned long long)NS);
-        T *dst = c.ring + (long long)st * stage_elems;
-        const int x = (int)(c.lo + (long long)blk * R);
-        if (lane == 0) mbar_arrive_expect(c.bars + st, (unsigned)(nseg * R * (int)sizeof(T)));
-        __syncwarp();
-        for (int t = lane; t < nreq; t += 32) {
-            if (t < n8) {
-                tma_load_2d(dst + 8 * t * R, c.tm8, x, c.ybase + c0 + 8 * t, c.bars + st);
-            } else {
-                const int r = t - n8;   // single columns: Z remainder, then u, then w
-                int sg, colx;
-                if (8 * n8 + r < q) {
-                    sg = 8 * n8 + r;
-                    colx = c0 + sg;
-                } else {
-                    sg = q + (8 * n8 + r - q);
-                    colx = (sg == q) ? ucol : wcol;
-                }
-                tma_load_2d(dst + sg * R, c.tm1, x, c.ybase + colx, c.bars + st);
-            }
-        }
-    };
-    if (wp == 0)
-        for (int b0 = 0; b0 < NS - 1 && b0 < nblk; b0++) issue(b0);
+    const int gi = threadIdx.x / RV, vi = threadIdx.x % RV;
     T acc[NVW];
 #pragma unroll
     for (int e = 0; e < NVW; e++) acc[e] = T(0);
-    for (int b0 = 0; b0 < nblk; b0++) {
-        if (wp == 0 && b0 + NS - 1 < nblk) issue(b0 + NS - 1);
-        const unsigned long long seq = c.ring_seq + (unsigned long long)b0;
-        const int st = (int)(seq % (unsigned long long)NS);
-        if (!mbar_wait_bounded(c.bars + st, (unsigned)((seq / (unsigned long long)NS) & 1ull), RING_WAIT_NS))
-            c.ints()[INT_STALL] = 1;
-        const T *sb = c.ring + (long long)st * stage_elems;
-        const long long rows = min((long long)R, cnt - (long long)b0 * R);
-        if (row < rows) {
-            const T uu = sb[q * R + row];
-            const T ww = DW ? sb[(q + 1) * R + row] : T(0);
+    const RingPass rp = ring_begin(c, c0, q, ucol, DW ? wcol : -1);
+    for (int b0 = 0; b0 < rp.nblk; b0++) {
+        const VT *sb = reinterpret_cast<const VT *>(ring_acquire(c, rp, b0));
+        // rows of the chunk are a multiple of 8, so whole vectors are valid
+        const int nv = (int)(min((long long)R, c.cnt - (long long)b0 * R) / E);
+        if (vi < nv) {
+            const VT uu = sb[q * RV + vi];
+            const VT ww = DW ? sb[(q + 1) * RV + vi] : uu;
 #pragma unroll
             for (int jj = 0; jj < CM; jj++) {
                 const int j = jj * NGRP + gi;
                 if (j < q) {
-                    const T z = sb[j * R + row];
-                    if (DU) acc[2 * jj] += z * uu;
-                    if (DW) acc[2 * jj + 1] += z * ww;
+                    const VT z = sb[j * RV + vi];
+                    if (DU) acc[2 * jj] += vdot(z, uu);
+                    if (DW) acc[2 * jj + 1] += vdot(z, ww);
                 }
             }
             if (gi == 0) {
-                if (DU) acc[2 * CM] += uu * uu;
+                if (DU) acc[2 * CM] += vdot(uu, uu);
                 if (DW) {
-                    acc[2 * CM + 1] += uu * ww;
-                    acc[2 * CM + 2] += ww * ww;
+                    acc[2 * CM + 1] += vdot(uu, ww);
+                    acc[2 * CM + 2] += vdot(ww, ww);
                 }
             }
         }
         __syncthreads();   // the stage may be refilled
     }
-    c.ring_seq += (unsigned long long)nblk;
+    ring_end(c, rp);
     // warp sums, then the warps of each column group in index order
     T *wsum = reinterpret_cast<T *>(c.D(c.P.o_wsum));
 #pragma unroll
@@ -405,37 +490,119 @@ __device__ void staged_dual_dots(Ctx<T> &c, int c0, int q, int ucol, int wcol, T
         }
     }
     __syncthreads();
-    c.bytes += (unsigned long long)nseg * c.g.n * sizeof(T);
 }
 
 // The update of one Arnoldi step with delayed re-orthogonalisation, over own
-// rows: vout = (u - Z sv) * rinv (the finished basis vector) and, if NEXT,
-// the next candidate w <- w * rinv - Z al - bet * vout, in place over w.
+// rows (registers, 16-byte loads): V_j = (u - Z sv) * rinv into column vcol
+// and, if NEXT, the next candidate ((w - bet u) - Z al) * rinv into column
+// wcol, in place over w.
 template <typename T, bool NEXT>
-__device__ void dual_update(Ctx<T> &c, int c0, int q, const T *sv, const T *al, T bet, T rinv, const T *u,
-                            T *w, T *vout) {
+__device__ void dual_update(Ctx<T> &c, int c0, int q, const T *sv, const T *al, T bet, T rinv, int ucol,
+                                   int wcol, int vcol) {
     typedef typename Vec<T>::type VT;
     constexpr int E = Vec<T>::N;
     const int nvec = (int)(c.cnt / E);
-    const VT *uv = reinterpret_cast<const VT *>(u + c.lo);
-    VT *wv = reinterpret_cast<VT *>(w + c.lo);
-    VT *ov = reinterpret_cast<VT *>(vout + c.lo);
+    const VT *uv = reinterpret_cast<const VT *>(c.col(ucol) + c.lo);
+    VT *wv = reinterpret_cast<VT *>(c.col(wcol) + c.lo);
+    VT *ov = reinterpret_cast<VT *>(c.col(vcol) + c.lo);
     for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
         VT vv = uv[i];
         VT nx = vv;
-        if (NEXT) nx = vscale(wv[i], rinv);
+        if (NEXT) nx = vaxmy(wv[i], bet, vv);
 #pragma unroll 8
         for (int j = 0; j < q; j++) {
             const VT xv = reinterpret_cast<const VT *>(c.col(c0 + j) + c.lo)[i];
             vv = vaxmy(vv, sv[j], xv);
             if (NEXT) nx = vaxmy(nx, al[j], xv);
         }
-        vv = vscale(vv, rinv);
-        ov[i] = vv;
-        if (NEXT) wv[i] = vaxmy(nx, bet, vv);
+        ov[i] = vscale(vv, rinv);
+        if (NEXT) wv[i] = vscale(nx, rinv);
     }
     __syncthreads();
     c.bytes += (unsigned long long)(q + 2 + (NEXT ? 2 : 0)) * c.g.n * sizeof(T);
+}
+
+// CTA partials of the Gram matrix of a cycle end, over own rows:
+//   out[a * nb + b] = Z_a . U_b  (a < na columns Z from a0, b < nb columns U from b0),
+//   out[na * nb + b] = U_b . U_b.
+// One staged pass per chunk of up to GB columns of U (and of up to 3 x warps
+// columns of Z).  Warp w owns the Z columns a = w (mod warps) and the lanes
+// consecutive 16-byte row vectors, so shared-memory loads are conflict free,
+// each U vector feeds up to 3 x E multiply-adds per lane, and every output
+// is one warp sum.
+template <typename T>
+__device__ __noinline__ void staged_gram(Ctx<T> &c, int a0, int na, int b0, int nb, T *out) {
+    typedef typename Vec<T>::type VT;
+    constexpr int E = Vec<T>::N;
+    constexpr int R = RING_SEG_BYTES / (int)sizeof(T);
+    constexpr int RV = R / E;   // vectors per segment
+    constexpr int NW = CHAIN_THREADS / 32;
+    constexpr int AW = 3;       // Z columns per warp and chunk
+    constexpr int GB = (sizeof(T) == 4) ? 20 : 8;   // U columns per chunk (registers)
+    static_assert(RV % 32 == 0, "ring geometry");
+    const int lane = lane_id(), wp = warp_id();
+    const int cap_segs = (int)((long long)c.P.ring_cap * 8 / RING_SEG_BYTES);
+    for (int ac = 0; ac < na; ac += NW * AW) {
+        const int nac = min(NW * AW, na - ac);
+        // two stages of nac + nbc segments fit: the ring holds >= 2 (m + 2)
+        const int gbmax = min(GB, cap_segs / 2 - nac);
+        for (int bc = 0; bc < nb; bc += gbmax) {
+            const int nbc = min(gbmax, nb - bc);
+            const bool norms = (ac == 0);
+            T acc[AW][GB];
+            T nrm[2] = {T(0), T(0)};
+#pragma unroll
+            for (int aa = 0; aa < AW; aa++)
+#pragma unroll
+                for (int bb = 0; bb < GB; bb++) acc[aa][bb] = T(0);
+            const int rs[2] = {a0 + ac, b0 + bc};
+            const int rl[2] = {nac, nbc};
+            const RingPass rp = ring_begin_runs(c, rs, rl, 2);
+            for (int blk = 0; blk < rp.nblk; blk++) {
+                const VT *sb = reinterpret_cast<const VT *>(ring_acquire(c, rp, blk));
+                const int nv = (int)(min((long long)R, c.cnt - (long long)blk * R) / E);
+#pragma unroll
+                for (int h = 0; h < RV / 32; h++) {
+                    const int vi = lane + 32 * h;
+                    if (vi < nv) {
+                        VT z[AW];
+#pragma unroll
+                        for (int aa = 0; aa < AW; aa++) {
+                            const int aidx = wp + NW * aa;
+                            z[aa] = (aidx < nac) ? sb[aidx * RV + vi] : vzero(T(0));
+                        }
+#pragma unroll
+                        for (int bb = 0; bb < GB; bb++) {
+                            if (bb < nbc) {
+                                const VT u = sb[(nac + bb) * RV + vi];
+#pragma unroll
+                                for (int aa = 0; aa < AW; aa++) acc[aa][bb] += vdot(z[aa], u);
+                                if (norms && bb == wp) nrm[0] += vdot(u, u);
+                                if (norms && bb == wp + NW) nrm[1] += vdot(u, u);
+                            }
+                        }
+                    }
+                }
+                __syncthreads();   // the stage may be refilled
+            }
+            ring_end(c, rp);
+#pragma unroll
+            for (int aa = 0; aa < AW; aa++) {
+                const int aidx = wp + NW * aa;
+#pragma unroll
+                for (int bb = 0; bb < GB; bb++) {
+                    const T v = warp_sum(acc[aa][bb]);
+                    if (lane == 0 && aidx < nac && bb < nbc) out[(ac + aidx) * nb + bc + bb] = v;
+                }
+            }
+            if (norms) {
+                const T v0 = warp_sum(nrm[0]), v1 = warp_sum(nrm[1]);
+                if (lane == 0 && wp < nbc) out[na * nb + bc + wp] = v0;
+                if (lane == 0 && wp + NW < nbc) out[na * nb + bc + wp + NW] = v1;
+            }
+        }
+    }
+    __syncthreads();
 }
 
 // Operator pass of an Arnoldi step: for own rows, vout = s * src (the new
@@ -618,7 +785,7 @@ __device__ void part_gram(Ctx<T> &c, int xa0, int na, int yb0, int nb, T *out) {
 // system `sys` into the slot.  Three phases separated by cluster barriers:
 // node values, rows of A, folded operator (needs the neighbours' diagonal).
 template <typename T>
-__device__ void assemble_system(Ctx<T> &c, const DevSystem &sys) {
+__device__ __noinline__ void assemble_system(Ctx<T> &c, const DevSystem &sys) {
     const long long nn = node_count(sys, c.g);
     if (nn > 0) {
         const long long per = (nn + c.cs - 1) / c.cs;
@@ -676,7 +843,7 @@ __device__ void assemble_system(Ctx<T> &c, const DevSystem &sys) {
 
 // True residual r = b - A x (FP64) over own rows; returns ||r|| (cluster-wide).
 template <typename T>
-__device__ double true_residual(Ctx<T> &c) {
+__device__ __noinline__ double true_residual(Ctx<T> &c) {
     cl_sync();   // x of the neighbours must be complete
     const long long hi = c.lo + c.cnt;
     double acc[1] = {0.0};
@@ -698,7 +865,7 @@ __device__ double true_residual(Ctx<T> &c) {
 // twice (the Gram matrices are reduced over the cluster, the k x k factors
 // are FP64).  On a failed Cholesky the recycle space is dropped (kc = 0).
 template <typename T>
-__device__ void refresh_recycle(Ctx<T> &c) {
+__device__ __noinline__ void refresh_recycle(Ctx<T> &c) {
     cl_sync();   // U of the neighbours (halo of the operator) must be complete
     c.updates_since_refresh = 0;
     const int kc = c.kc;
@@ -775,7 +942,7 @@ __device__ void refresh_recycle(Ctx<T> &c) {
 // Projection at the start of a recycled cycle (the first step of
 // Algorithm 2): z = C^T r, d += U z, r -= C z.  Returns ||r||.
 template <typename T>
-__device__ double project_recycle(Ctx<T> &c) {
+__device__ __noinline__ double project_recycle(Ctx<T> &c) {
     const int kc = c.kc;
     const int cC0 = COL_C_END - kc;
     T *rw = c.col(COL_RW), *dh = c.col(COL_DH);
@@ -866,6 +1033,8 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
     // and is dropped.
     T *sv = c.tco(c.P.t_s), *al = c.tco(c.P.t_al);
     double *gq = c.D(c.P.o_dscr);   // e = B s_V (kc entries), then g = H s_V (j + 1 entries)
+    double *sst = gq + c.m + 2;       // rho_j, s.t, 1/rho_j, ||A M^-1 V_{j-1}|| (one thread, shared)
+    const double rinv0 = 1.0 / rnw;
     int ucol = COL_RW, wcol = COL_Y0;
     double rho = rnw, anorm = 0.0;
     int Ld = 0;
@@ -893,15 +1062,30 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
         bool stop = last, brk = false;
         double st = 0.0;
         if (j > 0) {
-            // finish column j-1: add the second-pass coefficients, H(j, j-1) = rho
-            double ss = 0.0;
-            for (int i = 0; i < q; i++) {
-                const double si = (double)vv[i];
-                ss += si * si;
-                if (!last) st += si * (double)vv[q + i];
+            // finish column j-1: add the second-pass coefficients, H(j, j-1) = rho.
+            // s.s and s.t by warp 0 (lanes, then a fixed butterfly), shared
+            // through shared memory: FP64 is scarce, no thread repeats it
+            if (threadIdx.x < 32) {
+                double a0 = 0.0, a1 = 0.0;
+                for (int i = threadIdx.x; i < q; i += 32) {
+                    const double si = (double)vv[i];
+                    a0 += si * si;
+                    if (!last) a1 += si * (double)vv[q + i];
+                }
+                a0 = warp_sum(a0);
+                a1 = warp_sum(a1);
+                if (threadIdx.x == 0) {
+                    const double r2 = (double)vv[2 * q] - a0;
+                    const double rh = (r2 > 0.0) ? sqrt(r2) : 0.0;
+                    sst[0] = rh;
+                    sst[1] = a1;
+                    sst[2] = (rh > 0.0) ? 1.0 / rh : 0.0;
+                }
             }
-            const double r2 = (double)vv[2 * q] - ss;
-            rho = (r2 > 0.0) ? sqrt(r2) : 0.0;
+            __syncthreads();
+            rho = sst[0];
+            st = sst[1];
+            anorm = sst[3];
             for (int i = threadIdx.x; i < q; i += blockDim.x) {
                 if (i < kc)
                     M_(Bm, kc, i, j - 1) += (double)vv[i];
@@ -920,12 +1104,12 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
                 early = true;
             }
         }
-        const double rinv = brk ? 0.0 : 1.0 / rho;
+        const double rinv = brk ? 0.0 : ((j > 0) ? sst[2] : rinv0);
         for (int i = threadIdx.x; i < q; i += blockDim.x) sv[i] = (j > 0) ? vv[i] : T(0);
         if (stop) {
             __syncthreads();
             c.tick(PH_OTHER);
-            dual_update<T, false>(c, cQ0, q, sv, al, T(0), (T)rinv, u, w, c.col(COL_V0 + j));
+            dual_update<T, false>(c, cQ0, q, sv, al, T(0), (T)rinv, ucol, wcol, COL_V0 + j);
             c.tick(PH_UPD);
             Ld = j;
             break;
@@ -940,24 +1124,27 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
             gq[i] = acc;
         }
         __syncthreads();
-        // column j (first pass): Z^T A M^-1 V_j and V_j^T A M^-1 V_j; the
-        // update coefficients al (Z) and al[q] (V_j)
+        // column j (first pass): Z^T A M^-1 V_j and V_j^T A M^-1 V_j.  The
+        // next candidate is A M^-1 V_j - Z h1 - h1_j V_j
+        //   = (w - bet u) / rho - Z (e/rho + h1 - bet s/rho),  bet = g_j/rho + h1_j,
+        // written for the update pass as ((w - bet u) - Z al) / rho.
+        const double h1q = (((double)vv[2 * q + 1] - st) * rinv - gq[q]) * rinv;
+        const double bet = gq[q] * rinv + h1q;
         for (int i = threadIdx.x; i <= q; i += blockDim.x) {
-            double h1;
-            if (i < q)
-                h1 = ((double)vv[q + i] - gq[i]) * rinv;
-            else
-                h1 = (((double)vv[2 * q + 1] - st) * rinv - gq[q]) * rinv;
+            const double h1 = (i < q) ? ((double)vv[q + i] - gq[i]) * rinv : h1q;
             if (i < kc)
                 M_(Bm, kc, i, j) = h1;
             else
                 M_(H, ldh, i - kc, j) = h1;
-            al[i] = (T)(gq[i] * rinv + h1);
+            if (i < q) {
+                const double si = (j > 0) ? (double)vv[i] : 0.0;
+                al[i] = (T)(gq[i] + rho * h1 - bet * si);
+            }
         }
-        anorm = sqrt(fmax((double)vv[2 * q + 2], 0.0)) * rinv;
+        if (threadIdx.x == 0) sst[3] = sqrt(fmax((double)vv[2 * q + 2], 0.0)) * rinv;   // ||A M^-1 V_j||
         __syncthreads();
         c.tick(PH_OTHER);
-        dual_update<T, true>(c, cQ0, q, sv, al, al[q], (T)rinv, u, w, c.col(COL_V0 + j));
+        dual_update<T, true>(c, cQ0, q, sv, al, (T)bet, (T)rinv, ucol, wcol, COL_V0 + j);
         c.tick(PH_UPD);
         cl_sync();   // the next operator pass reads the neighbours' rows of the candidate
         ucol = wcol;
@@ -968,22 +1155,7 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
     // Gram pass for the harmonic-Ritz problem: [C, V_0..V_Ld]^T U and ||u_b||^2
     T *gram = c.template red<T>();
     if (full && kc > 0) {
-        part_gram(c, cQ0, kc + Ld + 1, COL_U0, kc, gram);
-        // ||u_b||^2
-        typedef typename Vec<T>::type VT;
-        const int nvec = (int)(c.cnt / Vec<T>::N);
-        T acc[KMAX];
-#pragma unroll
-        for (int b = 0; b < KMAX; b++) acc[b] = T(0);
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-#pragma unroll
-            for (int b = 0; b < KMAX; b++)
-                if (b < kc) {
-                    const VT u = reinterpret_cast<const VT *>(c.col(COL_U0 + b) + c.lo)[i];
-                    acc[b] += vdot(u, u);
-                }
-        }
-        block_sum<KMAX>(acc, kc, reinterpret_cast<T *>(c.D(c.P.o_wsum)), gram + (kc + Ld + 1) * kc);
+        staged_gram(c, cQ0, kc + Ld + 1, COL_U0, kc, gram);
         allreduce<T, T>(c, (kc + Ld + 1) * kc + kc);
     }
     c.tick(PH_GRAM);
@@ -1371,13 +1543,12 @@ __global__ void __launch_bounds__(CHAIN_THREADS, CHAIN_MIN_BLOCKS) chain_kernel(
     c.tmark = 0;
     c.ring = reinterpret_cast<T *>(smem_dyn + c.P.o_ring);
     c.bars = reinterpret_cast<unsigned long long *>(smem_dyn + c.P.o_bar);
-    c.ring_seq = 0;
-    c.tm8 = &a.tm8;
-    c.tm1 = &a.tm1;
+    c.phase = 0u;
+    c.tmap = a.tmap;
     c.ybase = slot * NCOLS;
     int *ictl = c.ints();
     if (threadIdx.x == 0) {
-        for (int i = 0; i < c.P.ring_ns; i++) mbar_init(c.bars + i, 1);
+        for (int i = 0; i < RING_MAX_NS; i++) mbar_init(c.bars + i, 1);
         mbar_init_fence();
         ictl[INT_STALL] = 0;   // sticky for the launch
     }
@@ -1397,6 +1568,12 @@ __global__ void __launch_bounds__(CHAIN_THREADS, CHAIN_MIN_BLOCKS) chain_kernel(
         for (long long pos = a.chain_off[chain]; pos < a.chain_off[chain + 1]; pos++)
             solve_system(c, a, a.order[pos]);
         if (a.chain_kc && c.rank == 0 && threadIdx.x == 0) a.chain_kc[chain] = c.kc;
+    }
+    // after a stall, give copies still in flight a bounded time to land
+    if (ictl[INT_STALL]) {
+        const unsigned long long t0 = global_ns();
+        while (global_ns() - t0 < RING_DRAIN_NS) {
+        }
     }
 }
 

@@ -36,8 +36,10 @@ constexpr int AW_SLOTS = 8;
 
 // Streaming passes stage the basis through shared memory in blocks of rows:
 // one segment is one column over RING_SEG_BYTES / sizeof(T) rows.  The TMA
-// boxes are {segment rows x 8 columns} and {segment rows x 1 column}.
+// boxes are {segment rows x (16 >> i) columns}, i < NBOX, so that any run of
+// columns is covered by a few boxes (16s, then a binary remainder).
 constexpr int RING_SEG_BYTES = 1024;
+constexpr int NBOX = 5;
 
 // One system as the kernels see it (device pointers).
 struct DevSystem {
@@ -84,8 +86,9 @@ struct ChainArgs {
                                   // (optional: read at chain start, written at chain end;
                                   // the chain's U_k, C_k stay in its workspace slot)
     // TMA descriptors of the basis slab of all slots, seen as one 2D array:
-    // ld rows (contiguous) x nslots * NCOLS columns (stride ld elements)
-    CUtensorMap tm8, tm1;
+    // ld rows (contiguous) x nslots * NCOLS columns (stride ld elements);
+    // tmap[i] has boxes of 16 >> i columns
+    CUtensorMap tmap[NBOX];
 };
 
 enum Phase { PH_ASM, PH_REFRESH, PH_PROJ, PH_SPMV, PH_DOT, PH_UPD, PH_GRAM, PH_DENSE, PH_CUPD, PH_RESID, PH_OTHER };

@@ -452,7 +452,7 @@ __device__ inline void schur_eigvec(const R *T, int ldt, int n, const R *wr, con
 // Schur vectors Zr (ldz = n).  Writes P (FP64, n x knew, ldp) and returns
 // knew (-1 if the QR iteration failed).
 template <typename R>
-__device__ inline int harmonic_select(const double *M64, int ld64, int n, int kwant, double *P, int ldp,
+__device__ __noinline__ int harmonic_select(const double *M64, int ld64, int n, int kwant, double *P, int ldp,
                                       R *Mr, int ldm, R *Zr, R *wr, R *wi, R *xr, R *xi, R *vscr,
                                       R *scr, int *isc, double *keys) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -555,7 +555,7 @@ __device__ inline int harmonic_select(const double *M64, int ld64, int n, int kw
 // ldq) holds the explicit orthonormal factor and R (kc x kc, ldr) the upper
 // triangle, normalised so that diag(R) > 0.  A is overwritten.
 // vnorm: scratch of KMAX doubles.  Returns 0, or 1 if a column is (numerically) dependent.
-__device__ inline int householder_qr(double *A, int lda, int rows, int kc, double *Q, int ldq, double *R,
+static __device__ __noinline__ int householder_qr(double *A, int lda, int rows, int kc, double *Q, int ldq, double *R,
                               int ldr, double *tau, double *sc) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = lane_id(), w = warp_id(), nw = num_warps();
@@ -640,7 +640,7 @@ __device__ inline int householder_qr(double *A, int lda, int rows, int kc, doubl
 
 // Cholesky G = R^T R of a kc x kc SPD matrix (ldg), R upper (ldr).
 // Returns 0, or 1 if a pivot is not positive relative to the diagonal.
-__device__ inline int cholesky_upper(const double *G, int ldg, int kc, double *R, int ldr, int *isc) {
+static __device__ __noinline__ int cholesky_upper(const double *G, int ldg, int kc, double *R, int ldr, int *isc) {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < kc * kc; e += nt) {
         const int i = e % kc, j = e / kc;
@@ -675,7 +675,7 @@ __device__ inline int cholesky_upper(const double *G, int ldg, int kc, double *R
 
 // Inverse of an upper-triangular kc x kc matrix R (ldr) into Ri (ldi); one
 // thread per column.
-__device__ inline void upper_inverse(const double *R, int ldr, int kc, double *Ri, int ldi) {
+static __device__ __noinline__ void upper_inverse(const double *R, int ldr, int kc, double *Ri, int ldi) {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < kc * kc; e += nt) M_(Ri, ldi, e % kc, e / kc) = 0.0;
     sync();

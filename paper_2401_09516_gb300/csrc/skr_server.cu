@@ -249,8 +249,8 @@ bool launch(skr_server *S, Chain *c, Request *r) {
     a.bytes = c->dbytes;
     a.prof = nullptr;
     a.chain_kc = c->dkc;
-    if (encode_basis_maps(a.ws.basis, a.ws.ld, a.ws.nslots, S->opt.precision == SKR_PREC_FP64 ? 8 : 4, &a.tm8,
-                          &a.tm1) != cudaSuccess)
+    if (encode_basis_maps(a.ws.basis, a.ws.ld, a.ws.nslots, S->opt.precision == SKR_PREC_FP64 ? 8 : 4, a.tmap) !=
+        cudaSuccess)
         return false;
     const cudaError_t e = (S->opt.precision == SKR_PREC_FP64)
                               ? launch_chain_f64(a, 1, c->cs, S->threads, S->smem, st)

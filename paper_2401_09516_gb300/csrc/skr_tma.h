@@ -15,11 +15,10 @@ namespace skr {
 
 // Describe the basis slab (nslots * NCOLS columns of ld elements of esz
 // bytes, column-contiguous) as a 2D tensor: dim 0 = rows (ld), dim 1 =
-// columns, with boxes of {RING_SEG_BYTES / esz rows x 8 columns} (m8) and
-// {RING_SEG_BYTES / esz rows x 1 column} (m1).  Boxes reaching past row ld
-// read zeros.  Returns cudaErrorInvalidValue when the driver rejects them.
-inline cudaError_t encode_basis_maps(void *basis, long long ld, int nslots, int esz, CUtensorMap *m8,
-                                     CUtensorMap *m1) {
+// columns, with boxes of {RING_SEG_BYTES / esz rows x (16 >> i) columns} in
+// maps[i], i < NBOX.  Boxes reaching past row ld read zeros.  Returns
+// cudaErrorInvalidValue when the driver rejects a descriptor.
+inline cudaError_t encode_basis_maps(void *basis, long long ld, int nslots, int esz, CUtensorMap *maps) {
     static std::once_flag once;
     static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
     static cudaError_t qerr = cudaSuccess;
@@ -35,14 +34,14 @@ inline cudaError_t encode_basis_maps(void *basis, long long ld, int nslots, int 
     cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)nslots * (cuuint64_t)NCOLS};
     cuuint64_t strides[1] = {(cuuint64_t)ld * (cuuint64_t)esz};
     cuuint32_t estr[2] = {1, 1};
-    cuuint32_t box8[2] = {(cuuint32_t)(RING_SEG_BYTES / esz), 8};
-    cuuint32_t box1[2] = {(cuuint32_t)(RING_SEG_BYTES / esz), 1};
-    CUresult r = enc(m8, dt, 2, basis, dims, strides, box8, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    r = enc(m1, dt, 2, basis, dims, strides, box1, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+    for (int i = 0; i < NBOX; i++) {
+        cuuint32_t box[2] = {(cuuint32_t)(RING_SEG_BYTES / esz), (cuuint32_t)(16 >> i)};
+        const CUresult r = enc(maps + i, dt, 2, basis, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace skr

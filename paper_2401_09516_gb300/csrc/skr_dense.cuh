@@ -184,13 +184,23 @@ __device__ inline int francis_schur(R *H, int ldh, R *Z, int ldz, int n, R *wr, 
         int hi = n - 1, its = 0, total = 0, fail = 0;
         while (hi >= 0) {
             // every lane takes the same scalar decisions from the same shared
-            // values, so no broadcast is needed
-            int l = hi;
-            while (l > 0) {
-                R s = fabs(M_(H, ldh, l - 1, l - 1)) + fabs(M_(H, ldh, l, l));
-                if (s == R(0)) s = R(1);
-                if (fabs(M_(H, ldh, l, l - 1)) <= EPS * s) break;
-                l--;
+            // values, so no broadcast is needed.  l: the largest index <= hi
+            // with a negligible subdiagonal H(l, l-1) (0 if none), 32
+            // candidates per ballot
+            int l = 0;
+            for (int base = hi; base > 0; base -= 32) {
+                const int i = base - lane;
+                bool neg = false;
+                if (i > 0) {
+                    R s = fabs(M_(H, ldh, i - 1, i - 1)) + fabs(M_(H, ldh, i, i));
+                    if (s == R(0)) s = R(1);
+                    neg = fabs(M_(H, ldh, i, i - 1)) <= EPS * s;
+                }
+                const unsigned m = __ballot_sync(FULL, neg);
+                if (m != 0u) {
+                    l = base - (__ffs(m) - 1);
+                    break;
+                }
             }
             __syncwarp();
             if (l > 0 && lane == 0) M_(H, ldh, l, l - 1) = R(0);
@@ -488,12 +498,21 @@ __device__ __noinline__ int harmonic_select(const double *M64, int ld64, int n, 
         rank[i] = r;
     }
     sync();
+    // position of each rank, and the max-norm of the Schur form (warp 0)
+    int *pos = isc + 8 + 3 * MMAX;
+    for (int i = tid; i < n; i += nt) pos[rank[i]] = i;
+    if (warp_id() == 0) {
+        R tn = R(0);
+        for (int e = lane_id(); e < n * n; e += 32) tn = fmax(tn, fabs(M_(Mr, ldm, e % n, e / n)));
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, off));
+        if (lane_id() == 0) scr[3] = tn;
+    }
+    sync();
     if (tid == 0) {
         int cols = 0, npick = 0;
         for (int r = 0; r < kwant && r < n; r++) {
-            int q = 0;
-            while (q < n && rank[q] != r) q++;
-            if (q >= n) break;
+            const int q = pos[r];
             if (wi[q] == R(0)) {
                 pick[npick++] = q;
                 cols += 1;
@@ -508,15 +527,15 @@ __device__ __noinline__ int harmonic_select(const double *M64, int ld64, int n, 
         }
         isc[1] = npick;
         isc[2] = cols;
-        R tn = R(0);
-        for (int e = 0; e < n * n; e++) tn = fmax(tn, fabs(M_(Mr, ldm, e % n, e / n)));
-        scr[3] = tn;
     }
     sync();
     const int npick = isc[1], knew = isc[2];
     const R tnorm = scr[3];
-    for (int q = tid; q < npick; q += nt)
-        schur_eigvec(Mr, ldm, n, wr, wi, pick[q], xr + q * n, xi + q * n, tnorm);
+    // one eigenvector per warp (lane 0): the back substitutions differ in
+    // length and branches, so lanes of one warp would serialise them
+    if (lane_id() == 0)
+        for (int q = warp_id(); q < npick; q += num_warps())
+            schur_eigvec(Mr, ldm, n, wr, wi, pick[q], xr + q * n, xi + q * n, tnorm);
     sync();
     int *colof = isc + 8 + 2 * MMAX;
     if (tid == 0) {

@@ -10,7 +10,9 @@ Krylov vectors, FP64 refinement, solution and small dense step).  The
 synthetic fields stand in for the paper's Darcy dataset.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
-oracle instead, on a bounded sample of the same workload.
+oracle instead, on a bounded sample of the same workload.  `--workload
+helmholtz100` measures the paper's Helmholtz set the same way (100^2
+unknowns, -lap u - k^2 u = 1 with k from a GRF: indefinite systems).
 """
 import argparse
 import glob
@@ -26,8 +28,35 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "systems/s to rel-res 1e-8, SKR vs plain GMRES on 1 GB300; HBM GB/s frac; p99"
-WORKLOAD = dict(nside=256, nsys=200, ell=0.1, sigma=1.0, seed=2, m=40, k=20, precond="jacobi",
-                precision="mixed", tol=1e-8, inner_tol=1e-5)
+WORKLOADS = {
+    # the headline workload: Darcy on 256^2 (n = 65,536), 200 systems
+    "darcy256": dict(kind="darcy2d", nside=256, nsys=200, ell=0.1, sigma=1.0, seed=2, m=40, k=20,
+                     precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5,
+                     desc="darcy2d 256x256 (n=65536), %d systems, a=exp(GRF ell=0.1 sigma=1), f=1, "
+                          "Jacobi, GCRO-DR m=40 k=20, mixed precision, tol 1e-8"),
+    # the paper's Helmholtz set (App. E): 100^2 unknowns, k from a GRF; indefinite
+    "helmholtz100": dict(kind="helmholtz2d", nside=100, nsys=200, kbar=10.0, ell=0.1, sigma=1.0, spread=0.2,
+                         seed=6, m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5,
+                         desc="helmholtz2d 100x100 (n=10000), %d systems, -lap u - k^2 u = 1, "
+                              "k=10 exp(0.2 GRF(ell=0.1 sigma=1)), Jacobi, GCRO-DR m=40 k=20, mixed precision, tol 1e-8"),
+}
+
+
+def _fields(W, nsys, seed):
+    """The seeded parameter fields of nsys systems (also the sort keys)."""
+    if W["kind"] == "darcy2d":
+        from workloads import darcy2d_sequence
+        return darcy2d_sequence(W["nside"], nsys, W["ell"], W["sigma"], seed=seed)
+    from workloads import helmholtz2d_sequence
+    return helmholtz2d_sequence(W["nside"], nsys, W["kbar"], W["ell"], W["sigma"], spread=W["spread"], seed=seed)
+
+
+def _system(skr, W, field):
+    return skr.darcy2d(field) if W["kind"] == "darcy2d" else skr.helmholtz2d(field)
+
+
+def _oracle_system(W, field):
+    return dict(kind="darcy2d", loga=field) if W["kind"] == "darcy2d" else dict(kind="helmholtz2d", k=field)
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one chain-
@@ -139,18 +168,15 @@ def run_gpu(args):
 
     import paper_2401_09516_gb300 as skr
     from paper_2401_09516_gb300 import _native
-    from workloads import darcy2d_sequence
-
-    W = WORKLOAD
+    W = WORKLOADS[args.workload]
     # weak scaling: every rank solves its own 200-system batch (independent chains)
-    L = darcy2d_sequence(W["nside"], max(W["nsys"], args.nsys), W["ell"], W["sigma"],
-                         seed=W["seed"] + 1000 * rank)
+    L = _fields(W, max(W["nsys"], args.nsys), W["seed"] + 1000 * rank)
     N = args.nsys
     L = L[:N]
     n = W["nside"] ** 2
     P_dev = torch.tensor(L.reshape(N, -1), device=dev)
-    fields = [P_dev[i].view(W["nside"] + 2, W["nside"] + 2) for i in range(N)]
-    systems = [skr.darcy2d(f) for f in fields]
+    fields = [P_dev[i].view(*L.shape[1:]) for i in range(N)]
+    systems = [_system(skr, W, f) for f in fields]
     x_dev = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(N)]
     stream = torch.cuda.current_stream(dev)
     nchains = args.chains
@@ -220,7 +246,7 @@ def run_gpu(args):
     kbytes = sum(s["bytes"] for s in st_skr) / len(st_skr)
     kms = sum(s["kernel_ms"] for s in st_skr) / len(st_skr)
     achieved = kbytes / (kms / 1e3) / 1e9
-    default_workload = (N == WORKLOAD["nsys"] and nchains == 76 and args.cluster_size == 2)
+    default_workload = (args.workload == "darcy256" and N == W["nsys"] and nchains == 76 and args.cluster_size == 2)
     traffic = None
     if default_workload and TRAFFIC["sources_sha256"] == _kernel_sources_sha256():
         traffic = TRAFFIC["bytes_per_launch"]
@@ -236,7 +262,7 @@ def run_gpu(args):
         Lh = [torch.from_numpy(np.ascontiguousarray(L[i])).pin_memory() for i in range(N)]
         Ph = torch.from_numpy(np.ascontiguousarray(L.reshape(N, -1))).pin_memory()
         xh = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(N)]
-        sys_h = [skr.darcy2d(Lh[i].numpy()) for i in range(N)]
+        sys_h = [_system(skr, W, Lh[i].numpy()) for i in range(N)]
         xh_np = [x.numpy() for x in xh]
 
         def e2e_step():
@@ -276,8 +302,7 @@ def run_gpu(args):
         "dtype": "f32+f64",
         "data": "synthetic",
         "config": {
-            "workload": "darcy2d 256x256 (n=65536), %d systems, a=exp(GRF ell=0.1 sigma=1), f=1, "
-                        "Jacobi, GCRO-DR m=40 k=20, mixed precision, tol 1e-8" % N,
+            "workload": W["desc"] % N,
             "chains": nchains, "cluster_size": st_skr[-1]["cluster_size"],
             "slots": st_skr[-1]["slots"], "l2": "flushed between steps (256 MB write)",
             "parallelism": "replicas" if ws > 1 else "single GPU",
@@ -300,7 +325,7 @@ def run_gpu(args):
         "clocks": clocks,
     }
     if args.cpu_baseline and rank == 0:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, W)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -316,13 +341,12 @@ class OracleChain:
     budget is spent, at least one system.
     """
 
-    def __init__(self):
+    def __init__(self, W):
         from oracle import sort as osort
         from oracle.krylov import RecycleState
-        from workloads import darcy2d_sequence
 
-        W = WORKLOAD
-        self.L = darcy2d_sequence(W["nside"], W["nsys"], W["ell"], W["sigma"], seed=W["seed"])
+        self.W = W
+        self.L = _fields(W, W["nsys"], W["seed"])
         t0 = time.perf_counter()
         self.order = osort.greedy_sort(self.L.reshape(W["nsys"], -1))
         self.t_sort = time.perf_counter() - t0
@@ -334,13 +358,13 @@ class OracleChain:
         """Solve along the chain for about budget_s seconds; returns (systems/s, systems done)."""
         from oracle import skr as oskr
 
-        W = WORKLOAD
+        W = self.W
         done = 0
         t1 = time.perf_counter()
         while True:
             if self.pos == len(self.order):
                 self.pos, self.state = 0, self._new_state()
-            A, b = oskr.assemble(dict(kind="darcy2d", loga=self.L[self.order[self.pos]]))
+            A, b = oskr.assemble(_oracle_system(W, self.L[self.order[self.pos]]))
             oskr.solve_system(A, b, W["precond"], W["m"], W["k"], W["tol"], self.state,
                               precision="mixed", inner_tol=W["inner_tol"])
             self.pos += 1
@@ -351,9 +375,9 @@ class OracleChain:
         return 1.0 / per_sys, done
 
 
-def cpu_baseline(budget_s):
+def cpu_baseline(budget_s, W):
     """One bounded oracle sample beside the GPU line."""
-    ch = OracleChain()
+    ch = OracleChain(W)
     v, done = ch.sample(budget_s)
     return {"value": round(v, 4), "unit": "systems/s", "cores": 1, "kind": "oracle",
             "sample": "first %d systems of the sorted 200-system chain (sort of all 200 amortised), "
@@ -364,7 +388,8 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    ch = OracleChain()
+    W = WORKLOADS[args.workload]
+    ch = OracleChain(W)
     budget = max(1.0, min(args.ref_seconds, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         ch.sample(budget)
@@ -382,11 +407,10 @@ def run_reference(args):
     line = {
         "metric": METRIC, "value": cb["value"], "unit": "systems/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(WORKLOAD["nsys"] / value * 1e3, 3),
+        "ms_per_step": round(W["nsys"] / value * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": "darcy2d 256x256 (n=65536), 200 systems, a=exp(GRF ell=0.1 sigma=1), f=1, "
-                               "Jacobi, GCRO-DR m=40 k=20, mixed-form refinement in FP64, tol 1e-8"},
+        "config": {"workload": W["desc"].replace("mixed precision", "mixed-form refinement in FP64") % W["nsys"]},
         "cpu_baseline": cb,
         "e2e": {"value": cb["value"], "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -399,6 +423,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="skr", choices=["skr", "reference"])
+    ap.add_argument("--workload", default="darcy256", choices=sorted(WORKLOADS),
+                    help="darcy256 (the headline workload) or helmholtz100")
     ap.add_argument("--chains", type=int, default=76, help="independent chains the sorted order is cut into")
     ap.add_argument("--cluster-size", type=int, default=2, help="CTAs per chain (thread-block cluster)")
     ap.add_argument("--nsys", type=int, default=200, help="systems per batch (200 = the full workload)")

@@ -66,6 +66,10 @@ typedef int32_t skr_status;
                                      diagonal, x-minus (p-ny), x-plus (p+ny), y-minus (p-1), y-plus (p+1) */
 #define SKR_FMT_STENCIL7      5   /* assembled 3D 7-point matrix; coef = 7 arrays: diagonal,
                                      x-minus, x-plus, y-minus, y-plus, z-minus, z-plus */
+#define SKR_FMT_HELMHOLTZ2D   6   /* Helmholtz (App. E, the fourth dataset), read as -lap u - k^2 u = f
+                                     with u = 0 on the boundary, 5-point Laplacian; coef = k at the
+                                     nx*ny interior nodes.  Indefinite once k^2 exceeds the smallest
+                                     eigenvalues of the discrete -lap (2 pi^2 for the unit square) */
 
 /* right preconditioner M (App. D.3): the Krylov method solves A M^-1 y = b, x = M^-1 y */
 #define SKR_PC_NONE           0

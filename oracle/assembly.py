@@ -8,13 +8,18 @@ example of Sec. 3.1), Dirichlet data folded into b (zero here).
 Readings where the paper is silent (listed in the design doc):
   * Darcy -div(a grad u) = f is discretised in conservative (flux) form; the
     face coefficient is the arithmetic mean of the two node values of a.
+  * The Helmholtz dataset (App. E, lap u + k^2 u = 0 with k from a GRF) is
+    taken as -lap u - k^2 u = f with u = 0 on the boundary and f = 1 by
+    default: the homogeneous equation with zero boundary data has only the
+    zero solution.
   * Convection-diffusion uses first-order upwinding for beta . grad u.
   * The unit square (cube) has h = 1/(N+1) for N interior nodes per side,
     unless h is passed explicitly (the worked example uses h = 1).
 
 Pins: the 2x2 worked example of Sec. 3.1 (Poisson, h = 1) and its Darcy
 negation for a = 1; O(h^2) convergence to a manufactured solution; the
-closed-form eigenvalues of the constant-coefficient Laplacian.
+closed-form eigenvalues of the constant-coefficient Laplacian, shifted by
+-k^2 for the Helmholtz operator.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -142,6 +147,39 @@ def convdiff2d(nu, beta, nside, rhs=None, h=None):
                                 (cyp, (slice(None), slice(None, -1)), 1)):
         pr = p[sl_row].ravel()
         rows.append(pr); cols.append(pr + shift); vals.append(np.full(pr.size, cval))
+    A = _coo_to_csr(np.concatenate(rows), np.concatenate(cols), np.concatenate(vals), n)
+    b = np.ones(n) if rhs is None else np.asarray(rhs, dtype=np.float64).copy()
+    return A, b
+
+
+def helmholtz2d(k, h=None, rhs=None):
+    """-lap u - k^2 u = f on an nx x ny interior grid (App. E, Helmholtz).
+
+    k     (nx, ny) wavenumber at the interior nodes
+    h     grid spacing (default 1/(nx+1) in x and 1/(ny+1) in y)
+    rhs   f at the interior nodes (n values); default f = 1
+    Returns (A as scipy CSR float64, b float64[n]).
+
+    Row p = i*ny + j: A[p, p] = 2/hx^2 + 2/hy^2 - k_p^2, A[p, p+-ny] = -1/hx^2,
+    A[p, p+-1] = -1/hy^2 (couplings to boundary nodes dropped, u = 0 there).
+    """
+    k = np.asarray(k, dtype=np.float64)
+    nx, ny = k.shape
+    hx = 1.0 / (nx + 1) if h is None else float(h)
+    hy = 1.0 / (ny + 1) if h is None else float(h)
+    n = nx * ny
+    p = np.arange(n).reshape(nx, ny)
+    rows = [p.ravel()]
+    cols = [p.ravel()]
+    vals = [(2.0 / hx**2 + 2.0 / hy**2 - k**2).ravel()]
+    for sl_row, shift, w in (((slice(1, None), slice(None)), -ny, 1.0 / hx**2),
+                             ((slice(None, -1), slice(None)), ny, 1.0 / hx**2),
+                             ((slice(None), slice(1, None)), -1, 1.0 / hy**2),
+                             ((slice(None), slice(None, -1)), 1, 1.0 / hy**2)):
+        pr = p[sl_row].ravel()
+        rows.append(pr)
+        cols.append(pr + shift)
+        vals.append(np.full(pr.size, -w))
     A = _coo_to_csr(np.concatenate(rows), np.concatenate(cols), np.concatenate(vals), n)
     b = np.ones(n) if rhs is None else np.asarray(rhs, dtype=np.float64).copy()
     return A, b

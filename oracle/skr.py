@@ -29,6 +29,8 @@ def grid_of(system):
         return tuple(s - 2 for s in np.shape(system["loga"]))
     if kind == "convdiff2d":
         return (system["nside"], system["nside"])
+    if kind == "helmholtz2d":
+        return tuple(np.shape(system["k"]))
     return system.get("grid")
 
 
@@ -42,6 +44,8 @@ def assemble(system):
     if kind == "convdiff2d":
         return assembly.convdiff2d(system["nu"], system["beta"], system["nside"],
                                    rhs=system.get("rhs"))
+    if kind == "helmholtz2d":
+        return assembly.helmholtz2d(system["k"], rhs=system.get("rhs"))
     if kind == "matrix":
         return system["A"], system["b"]
     raise ValueError(kind)

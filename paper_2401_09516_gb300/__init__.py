@@ -11,6 +11,7 @@ from ._native import (  # noqa: F401
     convdiff2d,
     darcy2d,
     darcy3d,
+    helmholtz2d,
     skr_apply,
     skr_assemble,
     skr_last_error,

@@ -32,6 +32,7 @@ SKR_FMT_DARCY3D = 2
 SKR_FMT_CONVDIFF2D = 3
 SKR_FMT_STENCIL5 = 4
 SKR_FMT_STENCIL7 = 5
+SKR_FMT_HELMHOLTZ2D = 6
 SKR_PC_NONE = 0
 SKR_PC_JACOBI = 1
 SKR_PC_ILU0 = 2
@@ -216,6 +217,11 @@ def darcy2d(loga, rhs=None):
 
 def darcy3d(loga, rhs=None):
     return System(SKR_FMT_DARCY3D, loga.shape[0] - 2, loga.shape[1] - 2, loga.shape[2] - 2, loga, rhs)
+
+
+def helmholtz2d(k, rhs=None):
+    """System -lap u - k^2 u = f from the wavenumber k at the nx x ny interior nodes."""
+    return System(SKR_FMT_HELMHOLTZ2D, k.shape[0], k.shape[1], 1, k, rhs)
 
 
 def convdiff2d(nu, beta, nside, rhs=None):

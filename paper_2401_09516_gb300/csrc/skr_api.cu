@@ -106,12 +106,13 @@ long long sys_coef_len(const skr_system &s) {
         case SKR_FMT_DARCY3D: return (long long)(s.nx + 2) * (s.ny + 2) * (s.nz + 2);
         case SKR_FMT_STENCIL5: return 5 * n;
         case SKR_FMT_STENCIL7: return 7 * n;
+        case SKR_FMT_HELMHOLTZ2D: return n;
         default: return 0;
     }
 }
 
 skr_status check_system(const skr_system &s, long long idx) {
-    if (s.fmt < SKR_FMT_DARCY2D || s.fmt > SKR_FMT_STENCIL7)
+    if (s.fmt < SKR_FMT_DARCY2D || s.fmt > SKR_FMT_HELMHOLTZ2D)
         return fail(SKR_ERR_INVALID_ARG, "system %lld: unknown format %d", idx, s.fmt);
     if (s.nx < 1 || s.ny < 1 || (is_3d(s.fmt) && s.nz < 1))
         return fail(SKR_ERR_INVALID_ARG, "system %lld: empty grid", idx);

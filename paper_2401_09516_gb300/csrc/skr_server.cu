@@ -51,6 +51,7 @@ long long coef_len(int fmt, int nx, int ny, int nz) {
         case SKR_FMT_DARCY3D: return (long long)(nx + 2) * (ny + 2) * (nz + 2);
         case SKR_FMT_STENCIL5: return 5 * n;
         case SKR_FMT_STENCIL7: return 7 * n;
+        case SKR_FMT_HELMHOLTZ2D: return n;
         default: return 0;
     }
 }
@@ -413,7 +414,7 @@ skr_status skr_server_create(const skr_options *opt_in, size_t hbm_budget, int32
 
 skr_status skr_submit(skr_server *S, const skr_system *sys, const double *key, int64_t p, uint64_t *ticket) {
     if (!S || !sys || !ticket) return err(SKR_ERR_INVALID_ARG, "NULL pointer");
-    if (sys->fmt < SKR_FMT_DARCY2D || sys->fmt > SKR_FMT_STENCIL7) return err(SKR_ERR_INVALID_ARG, "unknown format");
+    if (sys->fmt < SKR_FMT_DARCY2D || sys->fmt > SKR_FMT_HELMHOLTZ2D) return err(SKR_ERR_INVALID_ARG, "unknown format");
     if (sys->nx < 1 || sys->ny < 1 || (fmt3d(sys->fmt) && sys->nz < 1)) return err(SKR_ERR_INVALID_ARG, "empty grid");
     if (sys->fmt == SKR_FMT_CONVDIFF2D && (sys->nx != sys->ny || !(sys->params[0] > 0.0)))
         return err(SKR_ERR_INVALID_ARG, "convection-diffusion needs nx == ny and nu > 0");

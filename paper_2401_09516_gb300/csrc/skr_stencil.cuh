@@ -112,6 +112,20 @@ __device__ __forceinline__ void convdiff_row(const Geom &g, const double *prm, l
     c[4] = (j < g.ny - 1) ? cyp : 0.0;
 }
 
+// Helmholtz -lap u - k^2 u = f (2D, 5-point Laplacian); kfield = k at the
+// interior nodes, row-major like the unknowns.
+__device__ __forceinline__ void helmholtz_row(const Geom &g, const double *kfield, long long p, double *c) {
+    const long long i = p / g.ny, j = p - i * g.ny;
+    const double hx = 1.0 / (double)(g.nx + 1), hy = 1.0 / (double)(g.ny + 1);
+    const double ix2 = 1.0 / (hx * hx), iy2 = 1.0 / (hy * hy);
+    const double k = kfield[p];
+    c[0] = 2.0 * ix2 + 2.0 * iy2 - k * k;
+    c[1] = (i > 0) ? -ix2 : 0.0;
+    c[2] = (i < g.nx - 1) ? -ix2 : 0.0;
+    c[3] = (j > 0) ? -iy2 : 0.0;
+    c[4] = (j < g.ny - 1) ? -iy2 : 0.0;
+}
+
 // Assembled-input formats: copy the row, zeroing couplings that leave the grid.
 __device__ __forceinline__ void stencil_input_row(const Geom &g, const double *coef, long long p,
                                                   double *c) {
@@ -140,6 +154,8 @@ __device__ __forceinline__ void system_row(const DevSystem &sys, const Geom &g,
         darcy_row(g, anode, p, c);
     else if (sys.fmt == SKR_FMT_CONVDIFF2D)
         convdiff_row(g, sys.params, p, c);
+    else if (sys.fmt == SKR_FMT_HELMHOLTZ2D)
+        helmholtz_row(g, sys.coef, p, c);
     else
         stencil_input_row(g, sys.coef, p, c);
 }

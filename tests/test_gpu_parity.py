@@ -7,7 +7,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle import assembly, krylov, precond as oprecond, skr as oskr, sort as osort  # noqa: E402
-from workloads import convdiff2d_sequence, darcy2d_sequence, darcy3d_sequence  # noqa: E402
+from workloads import convdiff2d_sequence, darcy2d_sequence, darcy3d_sequence, helmholtz2d_sequence  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -387,3 +387,41 @@ def test_batched_chains_of_mixed_grids_in_one_launch(skr):
     with pytest.raises(skr.SkrError):
         skr.skr_solve_sequence(systems, order=order, chain_offsets=[0, 2, len(systems)], nchains=2,
                                options=opt)
+
+
+# ------------------------------------------------------------------ Helmholtz (App. E)
+
+def test_assemble_helmholtz2d(skr):
+    rng = np.random.default_rng(17)
+    k = rng.uniform(1.0, 12.0, size=(13, 11))
+    A, b = assembly.helmholtz2d(k)
+    want = _stencil_from_csr(A, 13, 11)
+    coef, rhs = skr.skr_assemble(skr.helmholtz2d(_dev(k)))
+    np.testing.assert_allclose(coef.cpu().numpy(), want, rtol=1e-14, atol=1e-14 * np.abs(want).max())
+    np.testing.assert_array_equal(rhs.cpu().numpy(), b)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_helmholtz_indefinite_matches_oracle(skr, precision):
+    """-lap u - k^2 u = 1, k from a GRF: indefinite systems (two negative eigenvalues)."""
+    K = helmholtz2d_sequence(32, 6, 8.0, 0.15, seed=7)
+    P = K.reshape(6, -1)
+    order = skr.skr_sort(_dev(P)).cpu().numpy().tolist()
+    assert order == osort.greedy_sort(P)
+    systems = [skr.helmholtz2d(_dev(K[i])) for i in range(6)]
+    opt = skr.skr_options_default(m=30, k=10, tol=1e-8, precond="jacobi", precision=precision)
+    xs, res = skr.skr_solve_sequence(systems, order=order, options=opt)
+    sysd = [dict(kind="helmholtz2d", k=K[i]) for i in range(6)]
+    xo, info = oskr.solve_sequence(sysd, order, "jacobi", 30, 10, 1e-8, precision="fp64")
+    for i in range(6):
+        A, b = assembly.helmholtz2d(K[i])
+        ev = np.linalg.eigvalsh(A.toarray())
+        assert (ev < 0).any()
+        kappa = np.abs(ev).max() / np.abs(ev).min()
+        assert res[i]["flag"] == 0, res[i]
+        # solution error bounded by the condition number times the residual
+        _check_solution(xs[i], A, b, 1e-8, spla_solve(A, b), 10 * kappa * 1e-8)
+    if precision == "fp64":
+        tot_g = sum(r["steps"] for r in res)
+        tot_o = sum(i["steps"] for i in info)
+        assert abs(tot_g - tot_o) <= 0.15 * tot_o, (tot_g, tot_o)

@@ -106,3 +106,50 @@ def test_convdiff_upwind_is_m_matrix_and_pure_diffusion_limit():
     np.testing.assert_allclose(B.toarray(), L.toarray(), rtol=1e-14)
     # nonsymmetric when beta != 0
     assert np.abs(D - D.T).max() > 0
+
+
+# ------------------------------------------------------------------ Helmholtz (App. E)
+
+def test_helmholtz_zero_wavenumber_is_unit_coefficient_darcy():
+    A0, b0 = assembly.helmholtz2d(np.zeros((7, 5)))
+    Ad, bd = assembly.darcy2d(np.zeros((9, 7)))
+    assert abs(A0 - Ad).max() == 0.0
+    np.testing.assert_array_equal(b0, bd)
+
+
+def test_helmholtz_constant_wavenumber_closed_form_spectrum():
+    # -lap_h - k^2 I on the unit square: lambda_ij - k^2 with the closed-form
+    # Dirichlet Laplacian eigenvalues; k = 9 makes it indefinite
+    nx = ny = 8
+    h = 1.0 / (nx + 1)
+    kk = 9.0
+    A, _ = assembly.helmholtz2d(np.full((nx, ny), kk))
+    ev = np.sort(np.linalg.eigvalsh(A.toarray()))
+    lam = np.sort([(4.0 / h**2) * (np.sin(i * np.pi * h / 2) ** 2 + np.sin(j * np.pi * h / 2) ** 2) - kk**2
+                   for i in range(1, nx + 1) for j in range(1, ny + 1)])
+    np.testing.assert_allclose(ev, lam, rtol=1e-12, atol=1e-9)
+    assert 0 < (ev < 0).sum() < ev.size
+
+
+def test_helmholtz_variable_wavenumber_enters_the_diagonal_only():
+    rng = np.random.default_rng(3)
+    k = rng.uniform(2.0, 9.0, size=(6, 4))
+    A, _ = assembly.helmholtz2d(k)
+    A0, _ = assembly.helmholtz2d(np.zeros((6, 4)))
+    D = (A0 - A).toarray()
+    np.testing.assert_allclose(D, np.diag(k.ravel() ** 2), rtol=1e-14, atol=0.0)
+
+
+def test_helmholtz_manufactured_solution_second_order():
+    kk = 3.0
+    errs = []
+    for N in (15, 31):
+        h = 1.0 / (N + 1)
+        x = np.arange(1, N + 1) * h
+        X, Y = np.meshgrid(x, x, indexing="ij")
+        u = np.sin(np.pi * X) * np.sin(2 * np.pi * Y)
+        f = (5 * np.pi**2 - kk**2) * u
+        A, b = assembly.helmholtz2d(np.full((N, N), kk), rhs=f.ravel())
+        xh = spla.spsolve(A.tocsc(), b)
+        errs.append(np.abs(xh - u.ravel()).max())
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs

@@ -276,3 +276,26 @@ def test_qr_pos_normalisation():
     assert np.all(np.diag(R) > 0)
     np.testing.assert_allclose(Q @ R, X, atol=1e-13)
     np.testing.assert_allclose(Q.T @ Q, np.eye(4), atol=1e-14)
+
+
+def test_recycling_solves_an_indefinite_helmholtz_sequence():
+    # -lap u - k^2 u = 1 with k from a GRF (App. E): indefinite, where
+    # restarted GMRES needs several times more steps than GCRO-DR
+    from workloads import helmholtz2d_sequence
+    from oracle import sort as osort
+    K = helmholtz2d_sequence(24, 4, 7.0, 0.15, seed=7)
+    A0, _ = assembly.helmholtz2d(K[0])
+    ev = np.linalg.eigvalsh(A0.toarray())
+    assert (ev < 0).any() and (ev > 0).any()
+    order = osort.greedy_sort(K.reshape(4, -1))
+    sysd = [dict(kind="helmholtz2d", k=K[i]) for i in range(4)]
+    x_r, info_r = skr.solve_sequence(sysd, order, "jacobi", 20, 8, 1e-8, precision="fp64")
+    x_g, info_g = skr.solve_sequence(sysd, order, "jacobi", 20, 0, 1e-8, precision="fp64")
+    for i in range(4):
+        A, b = assembly.helmholtz2d(K[i])
+        ev = np.abs(np.linalg.eigvalsh(A.toarray()))
+        kappa = ev.max() / ev.min()
+        xd = spla.spsolve(A.tocsc(), b)
+        assert np.linalg.norm(b - A @ x_r[i]) <= 1e-8 * np.linalg.norm(b) * 1.01
+        assert np.linalg.norm(x_r[i] - xd) <= 10 * kappa * 1e-8 * np.linalg.norm(xd)
+    assert sum(i["steps"] for i in info_r) * 3 < sum(i["steps"] for i in info_g)

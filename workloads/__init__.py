@@ -11,6 +11,7 @@ from .sequences import (
     darcy2d_sequence,
     darcy3d_sequence,
     convdiff2d_sequence,
+    helmholtz2d_sequence,
     batched_chains,
     serving_stream,
     CONFIGS,
@@ -21,6 +22,7 @@ __all__ = [
     "darcy2d_sequence",
     "darcy3d_sequence",
     "convdiff2d_sequence",
+    "helmholtz2d_sequence",
     "batched_chains",
     "serving_stream",
     "CONFIGS",

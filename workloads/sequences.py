@@ -54,6 +54,20 @@ def convdiff2d_sequence(nside, nsys, seed=0, nu_range=(0.01, 0.1), beta_max=50.0
     return nu, beta, f
 
 
+def helmholtz2d_sequence(nside, nsys, kbar, ell, sigma=1.0, spread=0.2, seed=0):
+    """N Helmholtz problems -lap u - k^2 u = 1 on an nside x nside interior grid.
+
+    The wavenumber is k = kbar * exp(spread * GRF(ell, sigma)) at the interior
+    nodes (positive, log-normal around kbar).  Returns k, shape
+    (nsys, nside, nside), float64; it is also the sort key.
+    """
+    rng = np.random.default_rng(seed)
+    out = np.empty((nsys, nside, nside))
+    for s in range(nsys):
+        out[s] = kbar * np.exp(spread * grf_field(rng, nside, ell, sigma, ndim=2))
+    return out
+
+
 def batched_chains(nchains, chain_len, sides=(64, 128, 192, 256, 384),
                    ell_range=(0.05, 0.3), sigma=1.0, seed=0):
     """Independent Darcy chains of mixed grid sides.
@@ -99,7 +113,7 @@ def serving_stream(nreq, rate, seed=0, sides2d=(128, 256, 512, 1024),
 
 
 # Named workloads: grid side, number of systems, GRF length scale, solver
-# settings.  Seeds 1..5 in table order.
+# settings.  Seeds 1..6 in table order.
 CONFIGS = {
     "darcy32_fp64": dict(kind="darcy2d", nside=32, nsys=20, ell=0.2, sigma=1.0, seed=1,
                           m=30, k=10, precond="none", precision="fp64", tol=1e-8),
@@ -111,4 +125,7 @@ CONFIGS = {
                           m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8),
     "serving": dict(kind="serving", nreq=2000, rate=200.0, seed=5,
                      m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8),
+    # the paper's Helmholtz set has 10,000 unknowns (100^2)
+    "helmholtz100": dict(kind="helmholtz2d", nside=100, nsys=200, kbar=10.0, ell=0.1, sigma=1.0,
+                          spread=0.2, seed=6, m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8),
 }

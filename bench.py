@@ -34,6 +34,13 @@ WORKLOADS = {
                      precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5,
                      desc="darcy2d 256x256 (n=65536), %d systems, a=exp(GRF ell=0.1 sigma=1), f=1, "
                           "Jacobi, GCRO-DR m=40 k=20, mixed precision, tol 1e-8"),
+    # Poisson with Dirichlet data and forcing from truncated Chebyshev series (App. E);
+    # one fixed matrix, the right-hand sides differ; sort keys = the 96 coefficients
+    "poisson_cheb256": dict(kind="poisson2d", nside=256, nsys=200, ncoef=8, decay=0.6, seed=7, m=40, k=20,
+                            precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5,
+                            desc="poisson2d 256x256 (n=65536), %d systems, lap u = f, f and boundary data "
+                                 "from truncated Chebyshev series (8 coefficients each, decay 0.6), "
+                                 "Jacobi, GCRO-DR m=40 k=20, mixed precision, tol 1e-8"),
     # the paper's Helmholtz set (App. E): 100^2 unknowns, k from a GRF; indefinite
     "helmholtz100": dict(kind="helmholtz2d", nside=100, nsys=200, kbar=10.0, ell=0.1, sigma=1.0, spread=0.2,
                          seed=6, m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5,
@@ -42,21 +49,41 @@ WORKLOADS = {
 }
 
 
-def _fields(W, nsys, seed):
-    """The seeded parameter fields of nsys systems (also the sort keys)."""
+def _inputs(W, nsys, seed):
+    """Seeded inputs of nsys systems: (sort keys [nsys, p], per-system payload)."""
     if W["kind"] == "darcy2d":
         from workloads import darcy2d_sequence
-        return darcy2d_sequence(W["nside"], nsys, W["ell"], W["sigma"], seed=seed)
-    from workloads import helmholtz2d_sequence
-    return helmholtz2d_sequence(W["nside"], nsys, W["kbar"], W["ell"], W["sigma"], spread=W["spread"], seed=seed)
+        L = darcy2d_sequence(W["nside"], nsys, W["ell"], W["sigma"], seed=seed)
+        return L.reshape(nsys, -1), [L[i] for i in range(nsys)]
+    if W["kind"] == "helmholtz2d":
+        from workloads import helmholtz2d_sequence
+        L = helmholtz2d_sequence(W["nside"], nsys, W["kbar"], W["ell"], W["sigma"], spread=W["spread"], seed=seed)
+        return L.reshape(nsys, -1), [L[i] for i in range(nsys)]
+    from workloads import chebyshev_poisson_sequence
+    K, F, G = chebyshev_poisson_sequence(W["nside"], nsys, W["ncoef"], W["decay"], seed=seed)
+    return K, [(F[i], G[i]) for i in range(nsys)]
 
 
-def _system(skr, W, field):
-    return skr.darcy2d(field) if W["kind"] == "darcy2d" else skr.helmholtz2d(field)
+def _to(payload, conv):
+    return tuple(conv(a) for a in payload) if isinstance(payload, tuple) else conv(payload)
 
 
-def _oracle_system(W, field):
-    return dict(kind="darcy2d", loga=field) if W["kind"] == "darcy2d" else dict(kind="helmholtz2d", k=field)
+def _system(skr, W, payload):
+    if W["kind"] == "darcy2d":
+        return skr.darcy2d(payload)
+    if W["kind"] == "helmholtz2d":
+        return skr.helmholtz2d(payload)
+    f, g = payload
+    return skr.poisson2d(f, tuple(g[e] for e in range(4)))
+
+
+def _oracle_system(W, payload):
+    if W["kind"] == "darcy2d":
+        return dict(kind="darcy2d", loga=payload)
+    if W["kind"] == "helmholtz2d":
+        return dict(kind="helmholtz2d", k=payload)
+    f, g = payload
+    return dict(kind="poisson2d", f=f, g=tuple(g))
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one chain-
@@ -170,13 +197,16 @@ def run_gpu(args):
     from paper_2401_09516_gb300 import _native
     W = WORKLOADS[args.workload]
     # weak scaling: every rank solves its own 200-system batch (independent chains)
-    L = _fields(W, max(W["nsys"], args.nsys), W["seed"] + 1000 * rank)
+    Kh, payload = _inputs(W, max(W["nsys"], args.nsys), W["seed"] + 1000 * rank)
     N = args.nsys
-    L = L[:N]
+    Kh, payload = Kh[:N], payload[:N]
     n = W["nside"] ** 2
-    P_dev = torch.tensor(L.reshape(N, -1), device=dev)
-    fields = [P_dev[i].view(*L.shape[1:]) for i in range(N)]
-    systems = [_system(skr, W, f) for f in fields]
+    P_dev = torch.tensor(Kh, device=dev)
+    if W["kind"] == "poisson2d":
+        pay_dev = [_to(p, lambda a: torch.tensor(a, device=dev)) for p in payload]
+    else:   # the keys are the fields themselves
+        pay_dev = [P_dev[i].view(*payload[i].shape) for i in range(N)]
+    systems = [_system(skr, W, p) for p in pay_dev]
     x_dev = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(N)]
     stream = torch.cuda.current_stream(dev)
     nchains = args.chains
@@ -184,7 +214,8 @@ def run_gpu(args):
     def opts(k):
         return skr.skr_options_default(m=W["m"], k=k, tol=W["tol"], inner_tol=W["inner_tol"],
                                        precond=W["precond"], precision=W["precision"],
-                                       cluster_size=args.cluster_size, stream=stream)
+                                       cluster_size=args.cluster_size, stream=stream,
+                                       warm_start=int(args.warm_start))
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -259,10 +290,11 @@ def run_gpu(args):
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if args.e2e:
-        Lh = [torch.from_numpy(np.ascontiguousarray(L[i])).pin_memory() for i in range(N)]
-        Ph = torch.from_numpy(np.ascontiguousarray(L.reshape(N, -1))).pin_memory()
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()   # noqa: E731
+        Lh = [_to(p, pin) for p in payload]
+        Ph = pin(Kh)
         xh = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(N)]
-        sys_h = [_system(skr, W, Lh[i].numpy()) for i in range(N)]
+        sys_h = [_system(skr, W, _to(Lh[i], lambda t: t.numpy())) for i in range(N)]
         xh_np = [x.numpy() for x in xh]
 
         def e2e_step():
@@ -283,7 +315,8 @@ def run_gpu(args):
             barrier()
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
         e2e_val = N * ws / (agg(e2e_ms) / 1e3)
-        h2d = Ph.numel() * 8 + sum(t.numel() for t in Lh) * 8
+        h2d = Ph.numel() * 8 + sum(sum(t.numel() for t in p) if isinstance(p, tuple) else p.numel()
+                                   for p in Lh) * 8
         d2h = N * n * 8 + N * 4
         e2e = {"value": round(e2e_val, 3), "unit": "systems/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
@@ -303,7 +336,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {
             "workload": W["desc"] % N,
-            "chains": nchains, "cluster_size": st_skr[-1]["cluster_size"],
+            "chains": nchains, "cluster_size": st_skr[-1]["cluster_size"], "warm_start": bool(args.warm_start),
             "slots": st_skr[-1]["slots"], "l2": "flushed between steps (256 MB write)",
             "parallelism": "replicas" if ws > 1 else "single GPU",
         },
@@ -325,7 +358,7 @@ def run_gpu(args):
         "clocks": clocks,
     }
     if args.cpu_baseline and rank == 0:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, W)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, W, args.warm_start)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -341,18 +374,20 @@ class OracleChain:
     budget is spent, at least one system.
     """
 
-    def __init__(self, W):
+    def __init__(self, W, warm=False):
         from oracle import sort as osort
         from oracle.krylov import RecycleState
 
         self.W = W
-        self.L = _fields(W, W["nsys"], W["seed"])
+        keys, self.L = _inputs(W, W["nsys"], W["seed"])
         t0 = time.perf_counter()
-        self.order = osort.greedy_sort(self.L.reshape(W["nsys"], -1))
+        self.order = osort.greedy_sort(keys)
         self.t_sort = time.perf_counter() - t0
         self._new_state = RecycleState
         self.state = RecycleState()
         self.pos = 0
+        self.warm = warm
+        self.prev = None
 
     def sample(self, budget_s):
         """Solve along the chain for about budget_s seconds; returns (systems/s, systems done)."""
@@ -363,10 +398,12 @@ class OracleChain:
         t1 = time.perf_counter()
         while True:
             if self.pos == len(self.order):
-                self.pos, self.state = 0, self._new_state()
+                self.pos, self.state, self.prev = 0, self._new_state(), None
             A, b = oskr.assemble(_oracle_system(W, self.L[self.order[self.pos]]))
-            oskr.solve_system(A, b, W["precond"], W["m"], W["k"], W["tol"], self.state,
-                              precision="mixed", inner_tol=W["inner_tol"])
+            x, _ = oskr.solve_system(A, b, W["precond"], W["m"], W["k"], W["tol"], self.state,
+                                     precision="mixed", inner_tol=W["inner_tol"],
+                                     x0=self.prev if self.warm else None)
+            self.prev = x
             self.pos += 1
             done += 1
             if time.perf_counter() - t1 > budget_s:
@@ -375,9 +412,9 @@ class OracleChain:
         return 1.0 / per_sys, done
 
 
-def cpu_baseline(budget_s, W):
+def cpu_baseline(budget_s, W, warm=False):
     """One bounded oracle sample beside the GPU line."""
-    ch = OracleChain(W)
+    ch = OracleChain(W, warm)
     v, done = ch.sample(budget_s)
     return {"value": round(v, 4), "unit": "systems/s", "cores": 1, "kind": "oracle",
             "sample": "first %d systems of the sorted 200-system chain (sort of all 200 amortised), "
@@ -389,7 +426,7 @@ def run_reference(args):
     if rank != 0:
         return
     W = WORKLOADS[args.workload]
-    ch = OracleChain(W)
+    ch = OracleChain(W, args.warm_start)
     budget = max(1.0, min(args.ref_seconds, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         ch.sample(budget)
@@ -424,7 +461,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="skr", choices=["skr", "reference"])
     ap.add_argument("--workload", default="darcy256", choices=sorted(WORKLOADS),
-                    help="darcy256 (the headline workload) or helmholtz100")
+                    help="darcy256 (the headline workload), helmholtz100 or poisson_cheb256")
+    ap.add_argument("--warm-start", action="store_true", help="x_0 = previous solution of the chain")
     ap.add_argument("--chains", type=int, default=76, help="independent chains the sorted order is cut into")
     ap.add_argument("--cluster-size", type=int, default=2, help="CTAs per chain (thread-block cluster)")
     ap.add_argument("--nsys", type=int, default=200, help="systems per batch (200 = the full workload)")

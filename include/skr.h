@@ -66,6 +66,11 @@ typedef int32_t skr_status;
                                      diagonal, x-minus (p-ny), x-plus (p+ny), y-minus (p-1), y-plus (p+1) */
 #define SKR_FMT_STENCIL7      5   /* assembled 3D 7-point matrix; coef = 7 arrays: diagonal,
                                      x-minus, x-plus, y-minus, y-plus, z-minus, z-plus */
+#define SKR_FMT_POISSON2D     7   /* Poisson lap u = f (App. E, the third dataset) with Dirichlet data,
+                                     the Sec. 3.1 sign (diagonal -2/hx^2 - 2/hy^2); coef = f at the nx*ny
+                                     interior nodes, then u on the boundary lines x = 0 (ny values,
+                                     j order), x = 1 (ny), y = 0 (nx, i order), y = 1 (nx); b = f minus
+                                     the boundary neighbours' values over h^2 (App. A.2); rhs must be NULL */
 #define SKR_FMT_HELMHOLTZ2D   6   /* Helmholtz (App. E, the fourth dataset), read as -lap u - k^2 u = f
                                      with u = 0 on the boundary, 5-point Laplacian; coef = k at the
                                      nx*ny interior nodes.  Indefinite once k^2 exceeds the smallest
@@ -113,6 +118,10 @@ typedef struct skr_options {
     int32_t mem;            /* SKR_MEM_DEVICE or SKR_MEM_HOST */
     int32_t profile;        /* nonzero: accumulate device time per phase (skr_last_profile) */
     void   *stream;         /* cudaStream_t */
+    int32_t warm_start;     /* nonzero: x_0 of a system is the solution of the previous system of
+                               its chain (Algorithm 2 leaves x_0 free); the first system of a chain,
+                               and every system when zero (default), starts from x_0 = 0 */
+    int32_t reserved;       /* must be 0 */
 } skr_options;
 
 typedef struct skr_result {

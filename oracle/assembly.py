@@ -8,6 +8,9 @@ example of Sec. 3.1), Dirichlet data folded into b (zero here).
 Readings where the paper is silent (listed in the design doc):
   * Darcy -div(a grad u) = f is discretised in conservative (flux) form; the
     face coefficient is the arithmetic mean of the two node values of a.
+  * The Poisson dataset with Chebyshev data (App. E) keeps the Sec. 3.1 sign
+    (lap u = f, diagonal -2/hx^2 - 2/hy^2) and folds the Dirichlet values of
+    boundary neighbours into b as f - g/h^2 (App. A.2).
   * The Helmholtz dataset (App. E, lap u + k^2 u = 0 with k from a GRF) is
     taken as -lap u - k^2 u = f with u = 0 on the boundary and f = 1 by
     default: the homogeneous equation with zero boundary data has only the
@@ -183,3 +186,25 @@ def helmholtz2d(k, h=None, rhs=None):
     A = _coo_to_csr(np.concatenate(rows), np.concatenate(cols), np.concatenate(vals), n)
     b = np.ones(n) if rhs is None else np.asarray(rhs, dtype=np.float64).copy()
     return A, b
+
+
+def poisson2d_dirichlet(f, g_x0, g_x1, g_y0, g_y1, h=None):
+    """lap u = f on an nx x ny interior grid with u = g on the boundary (Sec. 3.1 sign).
+
+    f (nx, ny) at the interior nodes; g_x0, g_x1 (ny values): u on the lines
+    x = 0 and x = 1 at y_j; g_y0, g_y1 (nx values): u on y = 0 and y = 1 at
+    x_i.  Row p = i*ny + j of A is poisson2d_paper's; b_p = f_p minus each
+    boundary neighbour's value times its coupling (1/hx^2 or 1/hy^2).
+    Returns (A as scipy CSR float64, b float64[n]).
+    """
+    f = np.asarray(f, dtype=np.float64)
+    nx, ny = f.shape
+    hx = 1.0 / (nx + 1) if h is None else float(h)
+    hy = 1.0 / (ny + 1) if h is None else float(h)
+    A = poisson2d_paper(nx, ny, hx, hy)
+    b = f.copy()
+    b[0, :] -= np.asarray(g_x0, dtype=np.float64) / hx**2
+    b[-1, :] -= np.asarray(g_x1, dtype=np.float64) / hx**2
+    b[:, 0] -= np.asarray(g_y0, dtype=np.float64) / hy**2
+    b[:, -1] -= np.asarray(g_y1, dtype=np.float64) / hy**2
+    return A, b.ravel()

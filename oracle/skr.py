@@ -31,6 +31,8 @@ def grid_of(system):
         return (system["nside"], system["nside"])
     if kind == "helmholtz2d":
         return tuple(np.shape(system["k"]))
+    if kind == "poisson2d":
+        return tuple(np.shape(system["f"]))
     return system.get("grid")
 
 
@@ -46,14 +48,18 @@ def assemble(system):
                                    rhs=system.get("rhs"))
     if kind == "helmholtz2d":
         return assembly.helmholtz2d(system["k"], rhs=system.get("rhs"))
+    if kind == "poisson2d":
+        return assembly.poisson2d_dirichlet(system["f"], *system["g"])
     if kind == "matrix":
         return system["A"], system["b"]
     raise ValueError(kind)
 
 
 def solve_system(A, b, precond, m, k, tol, state, precision="fp64", inner_tol=1e-5,
-                 max_refine=10, max_steps=10**4, grid=None):
+                 max_refine=10, max_steps=10**4, grid=None, x0=None):
     """Solve one system, updating the carried recycle state in place.
+
+    x0 is Algorithm 2's initial guess (default 0).
 
     Returns (x, info) with info = dict(steps, cycles, matvecs, refinements,
     relres, converged).  `steps` counts Arnoldi steps (one operator
@@ -67,7 +73,7 @@ def solve_system(A, b, precond, m, k, tol, state, precision="fp64", inner_tol=1e
     stats = dict(steps=0, cycles=0, matvecs=0, refinements=0)
     stats["matvecs"] += refresh(op, state)
     bnorm = np.linalg.norm(b)
-    x = np.zeros_like(b)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
     if bnorm == 0.0:
         stats.update(relres=0.0, converged=True)
         return x, stats
@@ -98,19 +104,24 @@ def split_chains(order, nchains):
 
 
 def solve_sequence(systems, order, precond, m, k, tol, precision="fp64", nchains=1,
-                   inner_tol=1e-5, max_refine=10, max_steps=10**4):
+                   inner_tol=1e-5, max_refine=10, max_steps=10**4, warm_start=False):
     """Solve systems[order[0]], systems[order[1]], ... carrying U_k along each chain.
 
-    Returns (xs, infos), lists indexed like `systems`.
+    warm_start: x0 of a system is the previous solution of its chain (the
+    first system of every chain starts from 0).  Returns (xs, infos), lists
+    indexed like `systems`.
     """
     xs = [None] * len(systems)
     infos = [None] * len(systems)
     for chain in split_chains(order, nchains):
         state = RecycleState()
+        prev = None
         for idx in chain:
             A, b = assemble(systems[idx])
             x, info = solve_system(A, b, precond, m, k, tol, state, precision, inner_tol,
-                                   max_refine, max_steps, grid=grid_of(systems[idx]))
+                                   max_refine, max_steps, grid=grid_of(systems[idx]),
+                                   x0=prev if warm_start else None)
             xs[idx] = x
             infos[idx] = info
+            prev = x
     return xs, infos

@@ -12,6 +12,7 @@ from ._native import (  # noqa: F401
     darcy2d,
     darcy3d,
     helmholtz2d,
+    poisson2d,
     skr_apply,
     skr_assemble,
     skr_last_error,

@@ -33,6 +33,7 @@ SKR_FMT_CONVDIFF2D = 3
 SKR_FMT_STENCIL5 = 4
 SKR_FMT_STENCIL7 = 5
 SKR_FMT_HELMHOLTZ2D = 6
+SKR_FMT_POISSON2D = 7
 SKR_PC_NONE = 0
 SKR_PC_JACOBI = 1
 SKR_PC_ILU0 = 2
@@ -59,7 +60,8 @@ class SkrOptions(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("precond", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
                 ("max_slots", ctypes.c_int32), ("mem", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("warm_start", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class SkrResult(ctypes.Structure):
@@ -222,6 +224,23 @@ def darcy3d(loga, rhs=None):
 def helmholtz2d(k, rhs=None):
     """System -lap u - k^2 u = f from the wavenumber k at the nx x ny interior nodes."""
     return System(SKR_FMT_HELMHOLTZ2D, k.shape[0], k.shape[1], 1, k, rhs)
+
+
+def poisson2d(f, g):
+    """System lap u = f with Dirichlet data (Sec. 3.1 sign).
+
+    f: nx x ny values at the interior nodes; g = (g_x0, g_x1, g_y0, g_y1):
+    u on the lines x = 0 and x = 1 (ny values each) and y = 0, y = 1 (nx
+    values each).  Host (numpy) or device (torch) arrays, all on one side.
+    """
+    nx, ny = f.shape
+    parts = [f.reshape(-1)] + [gi.reshape(-1) for gi in g]
+    if isinstance(f, np.ndarray):
+        coef = np.concatenate([np.asarray(t, dtype=np.float64) for t in parts])
+    else:
+        import torch
+        coef = torch.cat([t.to(torch.float64) for t in parts])
+    return System(SKR_FMT_POISSON2D, nx, ny, 1, coef, None)
 
 
 def convdiff2d(nu, beta, nside, rhs=None):

@@ -107,12 +107,13 @@ long long sys_coef_len(const skr_system &s) {
         case SKR_FMT_STENCIL5: return 5 * n;
         case SKR_FMT_STENCIL7: return 7 * n;
         case SKR_FMT_HELMHOLTZ2D: return n;
+        case SKR_FMT_POISSON2D: return n + 2LL * (s.nx + s.ny);
         default: return 0;
     }
 }
 
 skr_status check_system(const skr_system &s, long long idx) {
-    if (s.fmt < SKR_FMT_DARCY2D || s.fmt > SKR_FMT_HELMHOLTZ2D)
+    if (s.fmt < SKR_FMT_DARCY2D || s.fmt > SKR_FMT_POISSON2D)
         return fail(SKR_ERR_INVALID_ARG, "system %lld: unknown format %d", idx, s.fmt);
     if (s.nx < 1 || s.ny < 1 || (is_3d(s.fmt) && s.nz < 1))
         return fail(SKR_ERR_INVALID_ARG, "system %lld: empty grid", idx);
@@ -122,6 +123,8 @@ skr_status check_system(const skr_system &s, long long idx) {
         return fail(SKR_ERR_INVALID_ARG, "system %lld: nu must be positive", idx);
     if (s.fmt != SKR_FMT_CONVDIFF2D && s.coef == nullptr)
         return fail(SKR_ERR_INVALID_ARG, "system %lld: coef is NULL", idx);
+    if (s.fmt == SKR_FMT_POISSON2D && s.rhs != nullptr)
+        return fail(SKR_ERR_INVALID_ARG, "system %lld: the Poisson format takes f in coef; rhs must be NULL", idx);
     if (sys_n(s) > (1LL << 31) - 1024)
         return fail(SKR_ERR_INVALID_ARG, "system %lld: too many unknowns", idx);
     return SKR_OK;
@@ -390,6 +393,8 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
         return fail(SKR_ERR_INVALID_ARG, "bad precision");
     if (opt.mem != SKR_MEM_DEVICE && opt.mem != SKR_MEM_HOST) return fail(SKR_ERR_INVALID_ARG, "bad mem");
     if (opt.cluster_size < 0 || opt.cluster_size > 16) return fail(SKR_ERR_INVALID_ARG, "cluster_size in [0, 16]");
+    if (opt.warm_start != 0 && opt.warm_start != 1) return fail(SKR_ERR_INVALID_ARG, "warm_start must be 0 or 1");
+    if (opt.reserved != 0) return fail(SKR_ERR_INVALID_ARG, "reserved must be 0");
     cudaStream_t st = (cudaStream_t)opt.stream;
 
     // order and chains
@@ -499,6 +504,8 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     a.bytes = reinterpret_cast<unsigned long long *>(dctr.as<char>() + 32);
     a.prof = opt.profile ? reinterpret_cast<unsigned long long *>(dctr.as<char>() + 64) : nullptr;
     a.chain_kc = nullptr;
+    a.warm_start = opt.warm_start;
+    a.chain_xok = nullptr;   // every chain of the call starts from x_0 = 0
     if (encode_basis_maps(a.ws.basis, ld, nslots, (int)esz, a.tmap) != cudaSuccess)
         return fail(SKR_ERR_CUDA, "TMA descriptors of the basis could not be encoded");
 

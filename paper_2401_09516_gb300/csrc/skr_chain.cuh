@@ -799,7 +799,7 @@ __device__ __noinline__ void assemble_system(Ctx<T> &c, const DevSystem &sys) {
             double row[7];
             system_row(sys, c.g, c.anode, p, row);
             for (int s = 0; s < c.g.nst; s++) c.A64[(long long)s * c.ld + p] = row[s];
-            c.b[p] = sys.rhs ? sys.rhs[p] : 1.0;
+            c.b[p] = system_rhs(sys, c.g, p);
             c.dinv[p] = (c.precond == SKR_PC_NONE) ? 1.0 : 1.0 / row[0];
         } else {
             for (int s = 0; s < c.g.nst; s++) c.A64[(long long)s * c.ld + p] = 0.0;
@@ -1398,7 +1398,7 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
 constexpr int RECYCLE_REFRESH = 8;
 
 template <typename T>
-__device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx) {
+__device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx, bool warm) {
     const DevSystem sys = a.systems[sysidx];
     const unsigned long long t0 = global_ns();
     c.g = make_geom(sys.fmt, sys.nx, sys.ny, sys.nz);
@@ -1414,10 +1414,10 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx) {
     if (c.kc > 0) refresh_recycle(c);
     c.tick(PH_REFRESH);
     const long long hi = c.lo + c.cnt;
-    // ||b||
+    // ||b||; x_0 = 0, or the previous solution of the chain (warm start)
     double bacc[1] = {0.0};
     for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
-        c.x[p] = 0.0;
+        if (!warm) c.x[p] = 0.0;
         const double bv = c.b[p];
         c.r[p] = bv;
         bacc[0] += bv * bv;
@@ -1426,7 +1426,7 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx) {
     allreduce<T, double>(c, 1);
     const double bnorm = sqrt(c.template vals<double>()[0]);
     const bool fp64 = sizeof(T) == 8;
-    double rnorm = bnorm;
+    double rnorm = warm ? true_residual(c) : bnorm;
     int flag = SKR_NOT_CONVERGED;
     for (int it = 0;; it++) {
         if (it > 0) rnorm = true_residual(c);
@@ -1565,9 +1565,13 @@ __global__ void __launch_bounds__(CHAIN_THREADS, CHAIN_MIN_BLOCKS) chain_kernel(
             c.kc = (k0 > 0 && k0 <= a.k) ? k0 : 0;
         }
         c.updates_since_refresh = 0;
-        for (long long pos = a.chain_off[chain]; pos < a.chain_off[chain + 1]; pos++)
-            solve_system(c, a, a.order[pos]);
+        bool xok = a.chain_xok ? (a.chain_xok[chain] != 0) : false;
+        for (long long pos = a.chain_off[chain]; pos < a.chain_off[chain + 1]; pos++) {
+            solve_system(c, a, a.order[pos], a.warm_start && xok);
+            xok = true;
+        }
         if (a.chain_kc && c.rank == 0 && threadIdx.x == 0) a.chain_kc[chain] = c.kc;
+        if (a.chain_xok && c.rank == 0 && threadIdx.x == 0) a.chain_xok[chain] = 1;
     }
     // after a stall, give copies still in flight a bounded time to land
     if (ictl[INT_STALL]) {

@@ -82,6 +82,9 @@ struct ChainArgs {
     double tol, inner_tol;
     unsigned long long *bytes;    // algorithmic bytes counter (optional)
     unsigned long long *prof;     // SKR_NPHASE per-phase ns accumulators (optional)
+    int warm_start;               // x_0 = previous solution of the chain
+    int *chain_xok;               // per chain, optional: nonzero when the slot's x holds the
+                                  // previous solution (read at chain start, set at chain end)
     int *chain_kc;                // per-chain recycle dimension carried between launches
                                   // (optional: read at chain start, written at chain end;
                                   // the chain's U_k, C_k stay in its workspace slot)

@@ -22,7 +22,7 @@ __global__ void rows_kernel(DevSystem sys, Geom g, const double *anode, double *
         double row[7];
         system_row(sys, g, anode, p, row);
         for (int s = 0; s < g.nst; s++) A[(long long)s * ld + p] = row[s];
-        if (b) b[p] = sys.rhs ? sys.rhs[p] : 1.0;
+        if (b) b[p] = system_rhs(sys, g, p);
         if (dinv) dinv[p] = (precond == SKR_PC_JACOBI) ? 1.0 / row[0] : 1.0;
     }
 }

@@ -52,6 +52,7 @@ long long coef_len(int fmt, int nx, int ny, int nz) {
         case SKR_FMT_STENCIL5: return 5 * n;
         case SKR_FMT_STENCIL7: return 7 * n;
         case SKR_FMT_HELMHOLTZ2D: return n;
+        case SKR_FMT_POISSON2D: return n + 2LL * (nx + ny);
         default: return 0;
     }
 }
@@ -250,6 +251,8 @@ bool launch(skr_server *S, Chain *c, Request *r) {
     a.bytes = c->dbytes;
     a.prof = nullptr;
     a.chain_kc = c->dkc;
+    a.warm_start = S->opt.warm_start;
+    a.chain_xok = c->dkc + 16;   // the chain's x holds its previous request's solution
     if (encode_basis_maps(a.ws.basis, a.ws.ld, a.ws.nslots, S->opt.precision == SKR_PREC_FP64 ? 8 : 4, a.tmap) !=
         cudaSuccess)
         return false;
@@ -390,6 +393,8 @@ skr_status skr_server_create(const skr_options *opt_in, size_t hbm_budget, int32
         return err(SKR_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
     if (opt.precond != SKR_PC_NONE && opt.precond != SKR_PC_JACOBI && opt.precond != SKR_PC_ILU0)
         return err(SKR_ERR_INVALID_ARG, "unknown preconditioner");
+    if ((opt.warm_start != 0 && opt.warm_start != 1) || opt.reserved != 0)
+        return err(SKR_ERR_INVALID_ARG, "warm_start must be 0 or 1, reserved 0");
     if (opt.precision != SKR_PREC_FP64 && opt.precision != SKR_PREC_MIXED) return err(SKR_ERR_INVALID_ARG, "bad precision");
     if (opt.cluster_size < 0 || opt.cluster_size > 16) return err(SKR_ERR_INVALID_ARG, "cluster_size in [0, 16]");
     if (max_chains < 0) return err(SKR_ERR_INVALID_ARG, "max_chains < 0");
@@ -414,7 +419,8 @@ skr_status skr_server_create(const skr_options *opt_in, size_t hbm_budget, int32
 
 skr_status skr_submit(skr_server *S, const skr_system *sys, const double *key, int64_t p, uint64_t *ticket) {
     if (!S || !sys || !ticket) return err(SKR_ERR_INVALID_ARG, "NULL pointer");
-    if (sys->fmt < SKR_FMT_DARCY2D || sys->fmt > SKR_FMT_HELMHOLTZ2D) return err(SKR_ERR_INVALID_ARG, "unknown format");
+    if (sys->fmt < SKR_FMT_DARCY2D || sys->fmt > SKR_FMT_POISSON2D) return err(SKR_ERR_INVALID_ARG, "unknown format");
+    if (sys->fmt == SKR_FMT_POISSON2D && sys->rhs) return err(SKR_ERR_INVALID_ARG, "Poisson format: rhs must be NULL");
     if (sys->nx < 1 || sys->ny < 1 || (fmt3d(sys->fmt) && sys->nz < 1)) return err(SKR_ERR_INVALID_ARG, "empty grid");
     if (sys->fmt == SKR_FMT_CONVDIFF2D && (sys->nx != sys->ny || !(sys->params[0] > 0.0)))
         return err(SKR_ERR_INVALID_ARG, "convection-diffusion needs nx == ny and nu > 0");

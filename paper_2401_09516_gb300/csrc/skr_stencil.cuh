@@ -126,6 +126,34 @@ __device__ __forceinline__ void helmholtz_row(const Geom &g, const double *kfiel
     c[4] = (j < g.ny - 1) ? -iy2 : 0.0;
 }
 
+// Poisson lap u = f with the Sec. 3.1 sign (2D, 5-point).
+__device__ __forceinline__ void poisson_row(const Geom &g, long long p, double *c) {
+    const long long i = p / g.ny, j = p - i * g.ny;
+    const double hx = 1.0 / (double)(g.nx + 1), hy = 1.0 / (double)(g.ny + 1);
+    const double ix2 = 1.0 / (hx * hx), iy2 = 1.0 / (hy * hy);
+    c[0] = -2.0 * ix2 - 2.0 * iy2;
+    c[1] = (i > 0) ? ix2 : 0.0;
+    c[2] = (i < g.nx - 1) ? ix2 : 0.0;
+    c[3] = (j > 0) ? iy2 : 0.0;
+    c[4] = (j < g.ny - 1) ? iy2 : 0.0;
+}
+
+// Right-hand side of row p: f, minus the Dirichlet values of the boundary
+// neighbours times their coupling for the Poisson format (App. A.2); the
+// rhs array (or 1) for the others.
+__device__ __forceinline__ double system_rhs(const DevSystem &sys, const Geom &g, long long p) {
+    if (sys.fmt != SKR_FMT_POISSON2D) return sys.rhs ? sys.rhs[p] : 1.0;
+    const long long i = p / g.ny, j = p - i * g.ny;
+    const double hx = 1.0 / (double)(g.nx + 1), hy = 1.0 / (double)(g.ny + 1);
+    const double *f = sys.coef, *gxm = f + g.n, *gxp = gxm + g.ny, *gym = gxp + g.ny, *gyp = gym + g.nx;
+    double b = f[p];
+    if (i == 0) b -= gxm[j] / (hx * hx);
+    if (i == g.nx - 1) b -= gxp[j] / (hx * hx);
+    if (j == 0) b -= gym[i] / (hy * hy);
+    if (j == g.ny - 1) b -= gyp[i] / (hy * hy);
+    return b;
+}
+
 // Assembled-input formats: copy the row, zeroing couplings that leave the grid.
 __device__ __forceinline__ void stencil_input_row(const Geom &g, const double *coef, long long p,
                                                   double *c) {
@@ -156,6 +184,8 @@ __device__ __forceinline__ void system_row(const DevSystem &sys, const Geom &g,
         convdiff_row(g, sys.params, p, c);
     else if (sys.fmt == SKR_FMT_HELMHOLTZ2D)
         helmholtz_row(g, sys.coef, p, c);
+    else if (sys.fmt == SKR_FMT_POISSON2D)
+        poisson_row(g, p, c);
     else
         stencil_input_row(g, sys.coef, p, c);
 }

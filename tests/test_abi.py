@@ -45,6 +45,7 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(skr_system, coef), offsetof(skr_system, params),
          offsetof(skr_options, tol), offsetof(skr_options, stream));
   printf("%zu %zu\n", offsetof(skr_result, relres), offsetof(skr_result, seconds));
+  printf("%zu %zu\n", offsetof(skr_options, warm_start), offsetof(skr_options, reserved));
   return 0;
 }
 '''
@@ -60,6 +61,18 @@ int main(void) {
     assert vals[3:7] == [S.coef.offset, S.params.offset, O.tol.offset, O.stream.offset]
     assert O.profile.offset == 52
     assert vals[7:9] == [R.relres.offset, R.seconds.offset]
+    assert vals[9:11] == [O.warm_start.offset, O.reserved.offset]
+
+
+def test_binding_constants_match_header(native):
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    defines = dict(re.findall(r"#define\s+(SKR_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", text))
+    checked = 0
+    for name, val in defines.items():
+        if hasattr(native, name):
+            assert getattr(native, name) == int(val), name
+            checked += 1
+    assert checked >= 20
 
 
 def test_defaults_and_host_side_validation(native):

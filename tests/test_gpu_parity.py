@@ -7,7 +7,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle import assembly, krylov, precond as oprecond, skr as oskr, sort as osort  # noqa: E402
-from workloads import convdiff2d_sequence, darcy2d_sequence, darcy3d_sequence, helmholtz2d_sequence  # noqa: E402
+from workloads import (convdiff2d_sequence, darcy2d_sequence, darcy3d_sequence, helmholtz2d_sequence,  # noqa: E402
+                       chebyshev_poisson_sequence)
 
 
 @pytest.fixture(scope="module")
@@ -425,3 +426,70 @@ def test_solve_helmholtz_indefinite_matches_oracle(skr, precision):
         tot_g = sum(r["steps"] for r in res)
         tot_o = sum(i["steps"] for i in info)
         assert abs(tot_g - tot_o) <= 0.15 * tot_o, (tot_g, tot_o)
+
+
+# ------------------------------------------------------------------ Poisson with Chebyshev data, warm start
+
+def _poisson_system(skr, f, g):
+    return skr.poisson2d(_dev(f), tuple(_dev(gi) for gi in g))
+
+
+def test_assemble_poisson2d_dirichlet(skr):
+    K, F, G = chebyshev_poisson_sequence(11, 1, seed=5)
+    A, b = assembly.poisson2d_dirichlet(F[0], *G[0])
+    coef, rhs = skr.skr_assemble(_poisson_system(skr, F[0], G[0]))
+    want = _stencil_from_csr(A, 11, 11)
+    np.testing.assert_allclose(coef.cpu().numpy(), want, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(rhs.cpu().numpy(), b, rtol=1e-14, atol=1e-14 * np.abs(b).max())
+
+
+def test_poisson2d_exact_on_a_quadratic_rectangular_grid(skr):
+    nx, ny = 9, 6
+    x = np.arange(1, nx + 1) / (nx + 1.0)
+    y = np.arange(1, ny + 1) / (ny + 1.0)
+    u = lambda X, Y: X**2 + 2.0 * Y**2 + 0.5 * X * Y + X - 3.0 * Y + 0.25   # noqa: E731
+    X, Y = np.meshgrid(x, y, indexing="ij")
+    f = np.full((nx, ny), 6.0)
+    g = (u(0.0, y), u(1.0, y), u(x, 0.0), u(x, 1.0))
+    A, b = assembly.poisson2d_dirichlet(f, *g)
+    coef, rhs = skr.skr_assemble(_poisson_system(skr, f, g))
+    np.testing.assert_allclose(rhs.cpu().numpy(), b, rtol=1e-14, atol=1e-14 * np.abs(b).max())
+    opt = skr.skr_options_default(m=30, k=0, tol=1e-13, precond="jacobi", precision="fp64")
+    xs, res = skr.skr_solve_sequence([_poisson_system(skr, f, g)], options=opt)
+    assert res[0]["flag"] == 0
+    np.testing.assert_allclose(xs[0].cpu().numpy(), u(X, Y).ravel(), rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("warm", [0, 1])
+def test_solve_chebyshev_poisson_matches_oracle(skr, warm):
+    K, F, G = chebyshev_poisson_sequence(32, 8, seed=3)
+    order = skr.skr_sort(_dev(K)).cpu().numpy().tolist()
+    assert order == osort.greedy_sort(K)
+    systems = [_poisson_system(skr, F[i], G[i]) for i in range(8)]
+    opt = skr.skr_options_default(m=30, k=10, tol=1e-8, precond="jacobi", precision="fp64", warm_start=warm)
+    xs, res = skr.skr_solve_sequence(systems, order=order, options=opt)
+    sysd = [dict(kind="poisson2d", f=F[i], g=tuple(G[i])) for i in range(8)]
+    xo, info = oskr.solve_sequence(sysd, order, "jacobi", 30, 10, 1e-8, warm_start=bool(warm))
+    for i in range(8):
+        A, b = assembly.poisson2d_dirichlet(F[i], *G[i])
+        assert res[i]["flag"] == 0, res[i]
+        _check_solution(xs[i], A, b, 1e-8, spla_solve(A, b), 1e-6)
+    tot_g = sum(r["steps"] for r in res)
+    tot_o = sum(i["steps"] for i in info)
+    assert abs(tot_g - tot_o) <= 0.15 * tot_o, (tot_g, tot_o)
+
+
+def test_warm_start_repeated_system_takes_no_steps(skr):
+    L = darcy2d_sequence(16, 1, 0.2, seed=4)
+    sysd = skr.darcy2d(_dev(L[0]))
+    for prec in ("fp64", "mixed"):
+        opt = skr.skr_options_default(m=20, k=6, tol=1e-8, precond="jacobi", precision=prec, warm_start=1)
+        xs, res = skr.skr_solve_sequence([sysd, sysd], order=[0, 1], options=opt)
+        assert res[0]["steps"] > 0 and res[1]["steps"] == 0, res
+        np.testing.assert_array_equal(xs[1].cpu().numpy(), xs[0].cpu().numpy())
+        # each system first in its own chain: both start from x_0 = 0
+        xs, res = skr.skr_solve_sequence([sysd, sysd], order=[0, 1], nchains=2, options=opt)
+        assert res[0]["steps"] > 0 and res[1]["steps"] > 0, res
+    bad = skr.skr_options_default(warm_start=2)
+    with pytest.raises(skr.SkrError):
+        skr.skr_solve_sequence([sysd], options=bad)

@@ -110,3 +110,13 @@ def test_unknown_ticket_and_routing_key(skr):
         assert res["flag"] == 0
         with pytest.raises(skr.SkrError):
             skr.skr_poll(srv.handle, t, x.size)     # a ticket is forgotten once collected
+
+
+def test_warm_start_carries_the_previous_solution_of_a_chain(skr):
+    loga = darcy2d_sequence(24, 1, 0.2, seed=9)[0]
+    with skr.Server(_opts(skr, precision="fp64", warm_start=1), max_chains=1) as srv:
+        x1, r1 = srv.wait(srv.submit(_system(skr, loga)))
+        x2, r2 = srv.wait(srv.submit(_system(skr, loga)))
+    assert r1["flag"] == 0 and r2["flag"] == 0
+    assert r1["steps"] > 0 and r2["steps"] == 0, (r1, r2)
+    np.testing.assert_array_equal(x2, x1)

@@ -153,3 +153,29 @@ def test_helmholtz_manufactured_solution_second_order():
         xh = spla.spsolve(A.tocsc(), b)
         errs.append(np.abs(xh - u.ravel()).max())
     assert 3.5 < errs[0] / errs[1] < 4.5, errs
+
+
+# ------------------------------------------------------------------ Poisson with Dirichlet data
+
+def test_poisson_dirichlet_zero_data_is_the_paper_example():
+    f = np.array([[1.0, 2.0], [3.0, 4.0]])
+    z = np.zeros(2)
+    A, b = assembly.poisson2d_dirichlet(f, z, z, z, z, h=1.0)
+    np.testing.assert_array_equal(A.toarray(), _paper_matrix())
+    np.testing.assert_array_equal(b, f.ravel())
+
+
+def test_poisson_dirichlet_exact_on_a_quadratic():
+    # the 5-point Laplacian is exact on quadratics, so the discrete solution
+    # equals u at the nodes; the x/y asymmetry of u pins which boundary line
+    # is which and the sign of the folded values
+    nx, ny = 9, 6
+    hx, hy = 1.0 / (nx + 1), 1.0 / (ny + 1)
+    x = np.arange(1, nx + 1) * hx
+    y = np.arange(1, ny + 1) * hy
+    u = lambda X, Y: X**2 + 2.0 * Y**2 + 0.5 * X * Y + X - 3.0 * Y + 0.25   # noqa: E731
+    X, Y = np.meshgrid(x, y, indexing="ij")
+    f = np.full((nx, ny), 2.0 + 4.0)
+    A, b = assembly.poisson2d_dirichlet(f, u(0.0, y), u(1.0, y), u(x, 0.0), u(x, 1.0))
+    xs = spla.spsolve(A.tocsc(), b)
+    np.testing.assert_allclose(xs, u(X, Y).ravel(), rtol=0, atol=1e-11)

@@ -299,3 +299,32 @@ def test_recycling_solves_an_indefinite_helmholtz_sequence():
         assert np.linalg.norm(b - A @ x_r[i]) <= 1e-8 * np.linalg.norm(b) * 1.01
         assert np.linalg.norm(x_r[i] - xd) <= 10 * kappa * 1e-8 * np.linalg.norm(xd)
     assert sum(i["steps"] for i in info_r) * 3 < sum(i["steps"] for i in info_g)
+
+
+def test_warm_start_takes_no_steps_on_a_repeated_system():
+    # Algorithm 2 leaves x_0 free; with x_0 = the previous solution of an
+    # identical system the initial residual already meets the tolerance
+    L = darcy2d_sequence(12, 1, 0.2, seed=3)
+    sysd = [dict(kind="darcy2d", loga=L[0])] * 2
+    xs, info = skr.solve_sequence(sysd, [0, 1], "jacobi", 20, 6, 1e-8, warm_start=True)
+    assert info[0]["steps"] > 0 and info[1]["steps"] == 0
+    np.testing.assert_array_equal(xs[1], xs[0])
+    xs_c, info_c = skr.solve_sequence(sysd, [0, 1], "jacobi", 20, 6, 1e-8, warm_start=False)
+    assert info_c[1]["steps"] > 0
+
+
+def test_warm_start_on_a_sorted_chebyshev_poisson_sequence():
+    from workloads import chebyshev_poisson_sequence
+    from oracle import sort as osort
+    K, F, G = chebyshev_poisson_sequence(20, 8, seed=2)
+    order = osort.greedy_sort(K)
+    sysd = [dict(kind="poisson2d", f=F[i], g=tuple(G[i])) for i in range(8)]
+    xw, iw = skr.solve_sequence(sysd, order, "jacobi", 20, 6, 1e-8, warm_start=True)
+    xc, ic = skr.solve_sequence(sysd, order, "jacobi", 20, 6, 1e-8, warm_start=False)
+    for i in range(8):
+        A, b = assembly.poisson2d_dirichlet(F[i], *G[i])
+        xd = spla.spsolve(A.tocsc(), b)
+        for x in (xw[i], xc[i]):
+            assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b) * 1.01
+            assert np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)
+    assert iw[order[0]]["steps"] == ic[order[0]]["steps"]   # the first system starts from 0 either way

@@ -12,6 +12,7 @@ from .sequences import (
     darcy3d_sequence,
     convdiff2d_sequence,
     helmholtz2d_sequence,
+    chebyshev_poisson_sequence,
     batched_chains,
     serving_stream,
     CONFIGS,
@@ -23,6 +24,7 @@ __all__ = [
     "darcy3d_sequence",
     "convdiff2d_sequence",
     "helmholtz2d_sequence",
+    "chebyshev_poisson_sequence",
     "batched_chains",
     "serving_stream",
     "CONFIGS",

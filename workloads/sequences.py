@@ -68,6 +68,37 @@ def helmholtz2d_sequence(nside, nsys, kbar, ell, sigma=1.0, spread=0.2, seed=0):
     return out
 
 
+def chebyshev_poisson_sequence(nside, nsys, ncoef=8, decay=0.6, seed=0):
+    """N Poisson problems lap u = f with Dirichlet data from truncated Chebyshev series.
+
+    The four boundary functions are 1D series sum_j c_j T_j(2t - 1) and f is
+    the 2D series sum_ij a_ij T_i(2x - 1) T_j(2y - 1), j, i < ncoef, with
+    independent normal coefficients of standard deviation decay^j
+    (decay^(i+j) for f).  Returns (keys, f, g): keys (nsys, 4 ncoef + ncoef^2)
+    are the coefficients (the sort keys), f (nsys, nside, nside) at the
+    interior nodes, g (nsys, 4, nside) = u on x = 0, x = 1, y = 0, y = 1 at
+    the interior node coordinates of that line.
+    """
+    from numpy.polynomial import chebyshev as C
+
+    rng = np.random.default_rng(seed)
+    t = np.arange(1, nside + 1) / (nside + 1.0)
+    s = 2.0 * t - 1.0
+    w1 = decay ** np.arange(ncoef)
+    w2 = np.outer(w1, w1)
+    keys = np.empty((nsys, 4 * ncoef + ncoef * ncoef))
+    f = np.empty((nsys, nside, nside))
+    g = np.empty((nsys, 4, nside))
+    for q in range(nsys):
+        cb = rng.standard_normal((4, ncoef)) * w1
+        a = rng.standard_normal((ncoef, ncoef)) * w2
+        keys[q] = np.concatenate([cb.ravel(), a.ravel()])
+        for e in range(4):
+            g[q, e] = C.chebval(s, cb[e])
+        f[q] = C.chebgrid2d(s, s, a)
+    return keys, f, g
+
+
 def batched_chains(nchains, chain_len, sides=(64, 128, 192, 256, 384),
                    ell_range=(0.05, 0.3), sigma=1.0, seed=0):
     """Independent Darcy chains of mixed grid sides.
@@ -113,7 +144,7 @@ def serving_stream(nreq, rate, seed=0, sides2d=(128, 256, 512, 1024),
 
 
 # Named workloads: grid side, number of systems, GRF length scale, solver
-# settings.  Seeds 1..6 in table order.
+# settings.  Seeds 1..7.
 CONFIGS = {
     "darcy32_fp64": dict(kind="darcy2d", nside=32, nsys=20, ell=0.2, sigma=1.0, seed=1,
                           m=30, k=10, precond="none", precision="fp64", tol=1e-8),
@@ -125,6 +156,9 @@ CONFIGS = {
                           m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8),
     "serving": dict(kind="serving", nreq=2000, rate=200.0, seed=5,
                      m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8),
+    # Poisson with Chebyshev boundary data and forcing; sort keys = the coefficients
+    "poisson_cheb256": dict(kind="poisson2d", nside=256, nsys=200, ncoef=8, decay=0.6, seed=7,
+                             m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8),
     # the paper's Helmholtz set has 10,000 unknowns (100^2)
     "helmholtz100": dict(kind="helmholtz2d", nside=100, nsys=200, kbar=10.0, ell=0.1, sigma=1.0,
                           spread=0.2, seed=6, m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8),

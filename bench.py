@@ -34,6 +34,11 @@ WORKLOADS = {
                      precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5,
                      desc="darcy2d 256x256 (n=65536), %d systems, a=exp(GRF ell=0.1 sigma=1), f=1, "
                           "Jacobi, GCRO-DR m=40 k=20, mixed precision, tol 1e-8"),
+    # Darcy at the ablation's matrix size (10^4 unknowns, 100^2)
+    "darcy100": dict(kind="darcy2d", nside=100, nsys=200, ell=0.1, sigma=1.0, seed=8, m=40, k=20,
+                     precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5,
+                     desc="darcy2d 100x100 (n=10000), %d systems, a=exp(GRF ell=0.1 sigma=1), f=1, "
+                          "Jacobi, GCRO-DR m=40 k=20, mixed precision, tol 1e-8"),
     # Poisson with Dirichlet data and forcing from truncated Chebyshev series (App. E);
     # one fixed matrix, the right-hand sides differ; sort keys = the 96 coefficients
     "poisson_cheb256": dict(kind="poisson2d", nside=256, nsys=200, ncoef=8, decay=0.6, seed=7, m=40, k=20,
@@ -215,11 +220,13 @@ def run_gpu(args):
         return skr.skr_options_default(m=W["m"], k=k, tol=W["tol"], inner_tol=W["inner_tol"],
                                        precond=W["precond"], precision=W["precision"],
                                        cluster_size=args.cluster_size, stream=stream,
-                                       warm_start=int(args.warm_start))
+                                       warm_start=int(args.warm_start), diagnostics=int(args.diagnostics))
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(k, order=None):
+        if order is None:
+            order = np.arange(N, dtype=np.int32) if args.no_sort else None
         perm = skr.skr_sort(P_dev, stream=stream) if order is None else order
         permh = perm.cpu().numpy() if hasattr(perm, "cpu") else perm
         _, res = skr.skr_solve_sequence(systems, order=permh, nchains=nchains, options=opts(k),
@@ -298,7 +305,7 @@ def run_gpu(args):
         xh_np = [x.numpy() for x in xh]
 
         def e2e_step():
-            perm = skr.skr_sort(Ph.numpy(), stream=stream)
+            perm = np.arange(N, dtype=np.int32) if args.no_sort else skr.skr_sort(Ph.numpy(), stream=stream)
             skr.skr_solve_sequence(sys_h, order=perm, nchains=nchains, options=opts(W["k"]),
                                    x_out=xh_np)
 
@@ -337,6 +344,7 @@ def run_gpu(args):
         "config": {
             "workload": W["desc"] % N,
             "chains": nchains, "cluster_size": st_skr[-1]["cluster_size"], "warm_start": bool(args.warm_start),
+            "sorted": not args.no_sort,
             "slots": st_skr[-1]["slots"], "l2": "flushed between steps (256 MB write)",
             "parallelism": "replicas" if ws > 1 else "single GPU",
         },
@@ -354,9 +362,13 @@ def run_gpu(args):
                      "kernel": "chain_kernel<float>", "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": int(kbytes), "kernel_ms": round(kms, 3)},
         "e2e": e2e,
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": (1 if args.no_sort else 3) * args.steps,
         "clocks": clocks,
     }
+    if args.diagnostics:
+        ds = [r["delta"] for r in res_skr[-1] if r["delta"] >= 0.0]
+        line["delta_mean"] = round(sum(ds) / len(ds), 4) if ds else None
+        line["delta_systems"] = len(ds)
     if args.cpu_baseline and rank == 0:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, W, args.warm_start)
     if rank == 0:
@@ -461,8 +473,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="skr", choices=["skr", "reference"])
     ap.add_argument("--workload", default="darcy256", choices=sorted(WORKLOADS),
-                    help="darcy256 (the headline workload), helmholtz100 or poisson_cheb256")
+                    help="darcy256 (the headline workload), darcy100, helmholtz100 or poisson_cheb256")
     ap.add_argument("--warm-start", action="store_true", help="x_0 = previous solution of the chain")
+    ap.add_argument("--no-sort", action="store_true", help="solve in input order (ablation)")
+    ap.add_argument("--diagnostics", action="store_true", help="report the mean one-sided distance delta")
     ap.add_argument("--chains", type=int, default=76, help="independent chains the sorted order is cut into")
     ap.add_argument("--cluster-size", type=int, default=2, help="CTAs per chain (thread-block cluster)")
     ap.add_argument("--nsys", type=int, default=200, help="systems per batch (200 = the full workload)")

@@ -121,7 +121,7 @@ typedef struct skr_options {
     int32_t warm_start;     /* nonzero: x_0 of a system is the solution of the previous system of
                                its chain (Algorithm 2 leaves x_0 free); the first system of a chain,
                                and every system when zero (default), starts from x_0 = 0 */
-    int32_t reserved;       /* must be 0 */
+    int32_t diagnostics;    /* nonzero: report skr_result.delta (one extra Gram pass per system) */
 } skr_options;
 
 typedef struct skr_result {
@@ -133,6 +133,11 @@ typedef struct skr_result {
     int32_t k_final;        /* recycle dimension carried out of this system */
     double  relres;         /* true ||b - A x||_2 / ||b||_2, computed in FP64 on the device */
     double  seconds;        /* device time spent on this system (globaltimer) */
+    double  delta;          /* with diagnostics: the one-sided distance (Sec. 5.1, Eq. 5)
+                               delta(Q, C) = ||(I - Pi_C) Pi_Q||_2 from C = range(C_k) entering the
+                               system (after the App. B.1 refresh) to Q = range(C_k) leaving it,
+                               i.e. the sine of the largest principal angle; -1 when either space
+                               is empty or diagnostics are off */
 } skr_result;
 
 /* Fill *opt with the defaults named above. */

@@ -161,6 +161,17 @@ def harmonic_ritz_general(G, What, Vhat, k):
     return select_smallest(theta, Z, k), theta
 
 
+def one_sided_distance(Q, C):
+    """Eq. 5 (Sec. 5.1): delta(Q, C) = ||(I - Pi_C) Pi_Q||_2 for orthonormal bases Q, C.
+
+    With G = C^T Q, (I - Pi_C) Pi_Q restricted to range(Q) has Gram matrix
+    I - G^T G, so delta is the square root of its largest eigenvalue.
+    """
+    G = C.T @ Q
+    lam = np.linalg.eigvalsh(np.eye(Q.shape[1]) - G.T @ G)
+    return float(np.sqrt(min(max(lam[-1], 0.0), 1.0)))
+
+
 class RecycleState:
     """What one system hands to the next: U_k (as Y_tilde) and C_k."""
 

@@ -19,7 +19,7 @@ import numpy as np
 
 from . import assembly
 from .precond import RightPreconditioner
-from .krylov import RecycleState, refresh, gcrodr_solve
+from .krylov import RecycleState, refresh, gcrodr_solve, one_sided_distance
 
 
 def grid_of(system):
@@ -70,8 +70,9 @@ def solve_system(A, b, precond, m, k, tol, state, precision="fp64", inner_tol=1e
     def op(v):
         return A @ M.apply(v)
 
-    stats = dict(steps=0, cycles=0, matvecs=0, refinements=0)
+    stats = dict(steps=0, cycles=0, matvecs=0, refinements=0, delta=-1.0)
     stats["matvecs"] += refresh(op, state)
+    C_in = None if state.C is None else state.C.copy()
     bnorm = np.linalg.norm(b)
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
     if bnorm == 0.0:
@@ -91,6 +92,9 @@ def solve_system(A, b, precond, m, k, tol, state, precision="fp64", inner_tol=1e
         stats["refinements"] += 1
     relres = np.linalg.norm(b - A @ x) / bnorm
     stats.update(relres=relres, converged=bool(relres <= tol))
+    if C_in is not None and state.C is not None and state.C.shape[1] > 0:
+        # how far this system moved the recycle space it was handed (Eq. 5)
+        stats["delta"] = one_sided_distance(state.C, C_in)
     return x, stats
 
 

@@ -61,14 +61,14 @@ class SkrOptions(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
                 ("max_slots", ctypes.c_int32), ("mem", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("warm_start", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("warm_start", ctypes.c_int32), ("diagnostics", ctypes.c_int32)]
 
 
 class SkrResult(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int32), ("cycles", ctypes.c_int32), ("matvecs", ctypes.c_int32),
                 ("refinements", ctypes.c_int32), ("flag", ctypes.c_int32),
                 ("k_final", ctypes.c_int32), ("relres", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("delta", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

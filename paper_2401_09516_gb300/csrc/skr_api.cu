@@ -394,7 +394,7 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     if (opt.mem != SKR_MEM_DEVICE && opt.mem != SKR_MEM_HOST) return fail(SKR_ERR_INVALID_ARG, "bad mem");
     if (opt.cluster_size < 0 || opt.cluster_size > 16) return fail(SKR_ERR_INVALID_ARG, "cluster_size in [0, 16]");
     if (opt.warm_start != 0 && opt.warm_start != 1) return fail(SKR_ERR_INVALID_ARG, "warm_start must be 0 or 1");
-    if (opt.reserved != 0) return fail(SKR_ERR_INVALID_ARG, "reserved must be 0");
+    if (opt.diagnostics != 0 && opt.diagnostics != 1) return fail(SKR_ERR_INVALID_ARG, "diagnostics must be 0 or 1");
     cudaStream_t st = (cudaStream_t)opt.stream;
 
     // order and chains
@@ -505,6 +505,7 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     a.prof = opt.profile ? reinterpret_cast<unsigned long long *>(dctr.as<char>() + 64) : nullptr;
     a.chain_kc = nullptr;
     a.warm_start = opt.warm_start;
+    a.diagnostics = opt.diagnostics;
     a.chain_xok = nullptr;   // every chain of the call starts from x_0 = 0
     if (encode_basis_maps(a.ws.basis, ld, nslots, (int)esz, a.tmap) != cudaSuccess)
         return fail(SKR_ERR_CUDA, "TMA descriptors of the basis could not be encoded");
@@ -549,6 +550,7 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
         r.k_final = d.k_final;
         r.relres = d.relres;
         r.seconds = (d.t_end >= d.t_begin) ? (double)(d.t_end - d.t_begin) * 1e-9 : 0.0;
+        r.delta = d.delta;
     }
     g_last.bytes = hbytes;
     for (int i = 0; i < SKR_NPHASE; i++) g_last.prof[i] = hprof[i];

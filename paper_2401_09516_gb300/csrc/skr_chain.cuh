@@ -1394,6 +1394,35 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
 
 // ------------------------------------------------------------------ one system
 
+// The one-sided distance of Eq. 5, delta(Q, C) = ||(I - Pi_C) Pi_Q||_2, from
+// C = the kc_in columns saved at COL_CIN when the system started to Q = the
+// current C_k: with orthonormal bases and G = C^T Q, delta^2 is the largest
+// eigenvalue of I - G^T G (FP64, Hessenberg + Francis QR on every CTA).
+template <typename T>
+__device__ __noinline__ double recycle_delta(Ctx<T> &c, int kc_in) {
+    const int kq = c.kc;
+    T *red = c.template red<T>();
+    staged_gram(c, COL_CIN, kc_in, COL_C_END - kq, kq, red);
+    allreduce<T, T>(c, kc_in * kq + kq);
+    const T *gv = c.template vals<T>();   // gv[a * kq + b] = C_a . Q_b
+    double *S = c.D(c.P.o_F);
+    const int lds = c.P.ldh;
+    for (int e = threadIdx.x; e < kq * kq; e += blockDim.x) {
+        const int i = e % kq, j = e / kq;
+        double acc = (i == j) ? 1.0 : 0.0;
+        for (int a = 0; a < kc_in; a++) acc -= (double)gv[a * kq + i] * (double)gv[a * kq + j];
+        M_(S, lds, i, j) = acc;
+    }
+    __syncthreads();
+    double *Z = c.D(c.P.o_Z), *wr = c.D(c.P.o_wr), *wi = c.D(c.P.o_wi);
+    hessenberg_reduce<double>(S, lds, Z, kq, kq, c.D(c.P.o_vscr), c.D(c.P.o_sc));
+    const int fail = francis_schur<double>(S, lds, Z, kq, kq, wr, wi, c.ints() + 8);
+    double lmax = 0.0;
+    for (int i = 0; i < kq; i++) lmax = fmax(lmax, wr[i]);   // symmetric: real eigenvalues
+    __syncthreads();
+    return fail ? -1.0 : sqrt(fmin(fmax(lmax, 0.0), 1.0));
+}
+
 // Mixed form: recycle updates between two recomputations of C = A M^-1 U.
 constexpr int RECYCLE_REFRESH = 8;
 
@@ -1413,6 +1442,17 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx, bool war
     // refresh the carried recycle space against the new operator (App. B.1)
     if (c.kc > 0) refresh_recycle(c);
     c.tick(PH_REFRESH);
+    // diagnostics: keep the refreshed C_k to measure how far the system moves it
+    int kc_in = 0;
+    if (a.diagnostics && c.kc > 0) {
+        kc_in = c.kc;
+        for (int b = 0; b < kc_in; b++) {
+            const T *src = c.col(COL_C_END - kc_in + b);
+            T *dst = c.col(COL_CIN + b);
+            for (long long p = c.lo + threadIdx.x; p < c.lo + c.cnt; p += blockDim.x) dst[p] = src[p];
+        }
+        __syncthreads();
+    }
     const long long hi = c.lo + c.cnt;
     // ||b||; x_0 = 0, or the previous solution of the chain (warm start)
     double bacc[1] = {0.0};
@@ -1491,6 +1531,7 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx, bool war
         c.refinements += 1;
         c.bytes += (unsigned long long)c.g.n * (8 * 3 + sizeof(T));
     }
+    const double delta = (kc_in > 0 && c.kc > 0) ? recycle_delta(c, kc_in) : -1.0;
     // write the solution
     for (long long p = c.lo + threadIdx.x; p < min(hi, c.g.n); p += blockDim.x) sys.x_out[p] = c.x[p];
     c.bytes += (unsigned long long)c.g.n * 16;
@@ -1509,6 +1550,7 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx, bool war
         res.relres = (bnorm > 0.0) ? rnorm / bnorm : 0.0;
         res.t_begin = t0;
         res.t_end = global_ns();
+        res.delta = delta;
         a.results[sysidx] = res;
         if (a.bytes) atomicAdd(a.bytes, c.bytes);
     }

@@ -21,6 +21,7 @@ constexpr int LDH = MMAX + 1;     // leading dimension of the small FP64 matrice
 //   RW                        inner residual (working precision)
 //   DH                        inner correction d (working precision)
 //   Z                         ILU(0) sweep scratch
+//   CIN, CIN+KMAX             copy of C_k at the start of a system (delta diagnostic)
 // C directly precedes V, so [C_k, V_1..V_j] is one contiguous column range.
 constexpr int COL_C_END = KMAX;
 constexpr int COL_V0 = KMAX;
@@ -30,7 +31,8 @@ constexpr int COL_Y1 = COL_Y0 + 1;
 constexpr int COL_RW = COL_Y0 + 2;
 constexpr int COL_DH = COL_Y0 + 3;
 constexpr int COL_Z = COL_Y0 + 4;
-constexpr int NCOLS = COL_Y0 + 5;
+constexpr int COL_CIN = COL_Y0 + 5;
+constexpr int NCOLS = COL_CIN + KMAX;
 // Operator slots per slot: NST coefficient arrays, plus (ILU) the inverse pivots in slot 7.
 constexpr int AW_SLOTS = 8;
 
@@ -55,6 +57,7 @@ struct DevResult {
     int steps, cycles, matvecs, refinements, flag, k_final;
     double relres;
     unsigned long long t_begin, t_end;
+    double delta;   // one-sided distance of the recycle space, or -1
 };
 
 // Device workspace: one region per slot (cluster in flight).
@@ -83,6 +86,7 @@ struct ChainArgs {
     unsigned long long *bytes;    // algorithmic bytes counter (optional)
     unsigned long long *prof;     // SKR_NPHASE per-phase ns accumulators (optional)
     int warm_start;               // x_0 = previous solution of the chain
+    int diagnostics;              // nonzero: compute delta per system
     int *chain_xok;               // per chain, optional: nonzero when the slot's x holds the
                                   // previous solution (read at chain start, set at chain end)
     int *chain_kc;                // per-chain recycle dimension carried between launches

@@ -252,6 +252,7 @@ bool launch(skr_server *S, Chain *c, Request *r) {
     a.prof = nullptr;
     a.chain_kc = c->dkc;
     a.warm_start = S->opt.warm_start;
+    a.diagnostics = S->opt.diagnostics;
     a.chain_xok = c->dkc + 16;   // the chain's x holds its previous request's solution
     if (encode_basis_maps(a.ws.basis, a.ws.ld, a.ws.nslots, S->opt.precision == SKR_PREC_FP64 ? 8 : 4, a.tmap) !=
         cudaSuccess)
@@ -281,10 +282,12 @@ void finish(skr_server *S, Request *r, const DevResult *d, bool ok) {
         r->res.k_final = d->k_final;
         r->res.relres = d->relres;
         r->res.seconds = (d->t_end >= d->t_begin) ? (double)(d->t_end - d->t_begin) * 1e-9 : 0.0;
+        r->res.delta = d->delta;
     } else {
         r->res = skr_result{};
         r->res.flag = SKR_NUMERICAL;
         r->res.relres = NAN;
+        r->res.delta = -1.0;
     }
     r->state = 2;
     S->completed += 1;
@@ -393,8 +396,8 @@ skr_status skr_server_create(const skr_options *opt_in, size_t hbm_budget, int32
         return err(SKR_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
     if (opt.precond != SKR_PC_NONE && opt.precond != SKR_PC_JACOBI && opt.precond != SKR_PC_ILU0)
         return err(SKR_ERR_INVALID_ARG, "unknown preconditioner");
-    if ((opt.warm_start != 0 && opt.warm_start != 1) || opt.reserved != 0)
-        return err(SKR_ERR_INVALID_ARG, "warm_start must be 0 or 1, reserved 0");
+    if ((opt.warm_start != 0 && opt.warm_start != 1) || (opt.diagnostics != 0 && opt.diagnostics != 1))
+        return err(SKR_ERR_INVALID_ARG, "warm_start and diagnostics must be 0 or 1");
     if (opt.precision != SKR_PREC_FP64 && opt.precision != SKR_PREC_MIXED) return err(SKR_ERR_INVALID_ARG, "bad precision");
     if (opt.cluster_size < 0 || opt.cluster_size > 16) return err(SKR_ERR_INVALID_ARG, "cluster_size in [0, 16]");
     if (max_chains < 0) return err(SKR_ERR_INVALID_ARG, "max_chains < 0");

@@ -45,7 +45,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(skr_system, coef), offsetof(skr_system, params),
          offsetof(skr_options, tol), offsetof(skr_options, stream));
   printf("%zu %zu\n", offsetof(skr_result, relres), offsetof(skr_result, seconds));
-  printf("%zu %zu\n", offsetof(skr_options, warm_start), offsetof(skr_options, reserved));
+  printf("%zu %zu %zu\n", offsetof(skr_options, warm_start), offsetof(skr_options, diagnostics),
+         offsetof(skr_result, delta));
   return 0;
 }
 '''
@@ -61,7 +62,7 @@ int main(void) {
     assert vals[3:7] == [S.coef.offset, S.params.offset, O.tol.offset, O.stream.offset]
     assert O.profile.offset == 52
     assert vals[7:9] == [R.relres.offset, R.seconds.offset]
-    assert vals[9:11] == [O.warm_start.offset, O.reserved.offset]
+    assert vals[9:12] == [O.warm_start.offset, O.diagnostics.offset, R.delta.offset]
 
 
 def test_binding_constants_match_header(native):

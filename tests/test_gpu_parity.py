@@ -493,3 +493,23 @@ def test_warm_start_repeated_system_takes_no_steps(skr):
     bad = skr.skr_options_default(warm_start=2)
     with pytest.raises(skr.SkrError):
         skr.skr_solve_sequence([sysd], options=bad)
+
+
+# ------------------------------------------------------------------ delta diagnostic (Eq. 5)
+
+def test_delta_diagnostic_matches_oracle(skr):
+    L = darcy2d_sequence(16, 6, 0.2, seed=11)
+    order = osort.greedy_sort(L.reshape(6, -1))
+    systems = [skr.darcy2d(_dev(l)) for l in L]
+    opt = skr.skr_options_default(m=20, k=6, tol=1e-8, precond="none", precision="fp64", diagnostics=1)
+    _, res = skr.skr_solve_sequence(systems, order=order, options=opt)
+    sysd = [dict(kind="darcy2d", loga=l) for l in L]
+    _, info = oskr.solve_sequence(sysd, order, "none", 20, 6, 1e-8)
+    assert res[order[0]]["delta"] == -1.0 and info[order[0]]["delta"] == -1.0
+    for i in order[1:]:
+        assert 0.0 <= res[i]["delta"] <= 1.0
+        assert abs(res[i]["delta"] - info[i]["delta"]) <= 2e-3, (i, res[i]["delta"], info[i]["delta"])
+    opt0 = skr.skr_options_default(m=20, k=6, tol=1e-8, precond="none", precision="fp64")
+    _, res0 = skr.skr_solve_sequence(systems, order=order, options=opt0)
+    assert all(r["delta"] == -1.0 for r in res0)
+    assert [r["steps"] for r in res0] == [r["steps"] for r in res]   # diagnostics do not change the solve

@@ -328,3 +328,28 @@ def test_warm_start_on_a_sorted_chebyshev_poisson_sequence():
             assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b) * 1.01
             assert np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)
     assert iw[order[0]]["steps"] == ic[order[0]]["steps"]   # the first system starts from 0 either way
+
+
+def test_one_sided_distance_is_the_sine_of_the_largest_principal_angle():
+    import scipy.linalg as sla
+    rng = np.random.default_rng(12)
+    n = 40
+    for dq, dc in ((3, 5), (4, 4), (1, 6)):
+        Q = np.linalg.qr(rng.standard_normal((n, dq)))[0]
+        C = np.linalg.qr(rng.standard_normal((n, dc)))[0]
+        ang = sla.subspace_angles(Q, C)
+        assert abs(krylov.one_sided_distance(Q, C) - np.sin(ang.max())) < 1e-12
+    C = np.linalg.qr(rng.standard_normal((n, 5)))[0]
+    assert krylov.one_sided_distance(C[:, :3], C) < 1e-7          # Q inside C
+    P = np.eye(n)[:, :3]
+    Cp = np.eye(n)[:, 3:8]
+    assert abs(krylov.one_sided_distance(P, Cp) - 1.0) < 1e-12     # orthogonal
+    assert abs(krylov.one_sided_distance(C, C[:, :2]) - 1.0) < 1e-12  # dim Q > dim C
+
+
+def test_sequence_reports_delta_per_system():
+    L = darcy2d_sequence(14, 4, 0.2, seed=5)
+    sysd = [dict(kind="darcy2d", loga=l) for l in L]
+    _, info = skr.solve_sequence(sysd, [0, 1, 2, 3], "none", 20, 6, 1e-8)
+    assert info[0]["delta"] == -1.0                      # nothing recycled into the first system
+    assert all(0.0 <= info[i]["delta"] <= 1.0 for i in (1, 2, 3))

@@ -54,6 +54,18 @@ WORKLOADS = {
 }
 
 
+PRECOND_NAMES = {"none": "no preconditioner", "jacobi": "Jacobi", "ssor": "SSOR", "ilu0": "red-black ILU(0)"}
+
+
+def _workload(args):
+    """The named workload, with the preconditioner overridden if asked."""
+    W = dict(WORKLOADS[args.workload])
+    if args.precond and args.precond != W["precond"]:
+        W["desc"] = W["desc"].replace(PRECOND_NAMES[W["precond"]], PRECOND_NAMES[args.precond])
+        W["precond"] = args.precond
+    return W
+
+
 def _inputs(W, nsys, seed):
     """Seeded inputs of nsys systems: (sort keys [nsys, p], per-system payload)."""
     if W["kind"] == "darcy2d":
@@ -200,7 +212,7 @@ def run_gpu(args):
 
     import paper_2401_09516_gb300 as skr
     from paper_2401_09516_gb300 import _native
-    W = WORKLOADS[args.workload]
+    W = _workload(args)
     # weak scaling: every rank solves its own 200-system batch (independent chains)
     Kh, payload = _inputs(W, max(W["nsys"], args.nsys), W["seed"] + 1000 * rank)
     N = args.nsys
@@ -437,7 +449,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    W = WORKLOADS[args.workload]
+    W = _workload(args)
     ch = OracleChain(W, args.warm_start)
     budget = max(1.0, min(args.ref_seconds, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
@@ -476,6 +488,8 @@ def main():
                     help="darcy256 (the headline workload), darcy100, helmholtz100 or poisson_cheb256")
     ap.add_argument("--warm-start", action="store_true", help="x_0 = previous solution of the chain")
     ap.add_argument("--no-sort", action="store_true", help="solve in input order (ablation)")
+    ap.add_argument("--precond", default=None, choices=sorted(PRECOND_NAMES),
+                    help="override the workload's preconditioner")
     ap.add_argument("--diagnostics", action="store_true", help="report the mean one-sided distance delta")
     ap.add_argument("--chains", type=int, default=76, help="independent chains the sorted order is cut into")
     ap.add_argument("--cluster-size", type=int, default=2, help="CTAs per chain (thread-block cluster)")

@@ -79,6 +79,9 @@ typedef int32_t skr_status;
 /* right preconditioner M (App. D.3): the Krylov method solves A M^-1 y = b, x = M^-1 y */
 #define SKR_PC_NONE           0
 #define SKR_PC_JACOBI         1   /* M = diag(A) */
+#define SKR_PC_SSOR           3   /* symmetric SOR, omega = 1 (App. D.3's SOR; PETSc's default local
+                                     symmetric sweep): M = (D + L) D^-1 (D + U) of A in red-black order,
+                                     applied as the same two parallel colour sweeps as SKR_PC_ILU0 */
 #define SKR_PC_ILU0           2   /* M = L U, ILU(0) of A in red-black order (no fill; both
                                      triangular solves are two parallel colour sweeps) */
 

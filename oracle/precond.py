@@ -1,10 +1,16 @@
 """Preconditioners applied from the right (oracle).
 
-App. D.3 lists the preconditioners; this build uses three of them:
+App. D.3 lists the preconditioners; this build uses four of them:
   * none:   M = I
   * jacobi: M = diag(A) ("the inverse of the diagonal elements")
+  * ssor:   symmetric SOR with omega = 1 (App. D.3's SOR, as PETSc applies it
+            by default: one local symmetric sweep), M = (D + L) D^-1 (D + U)
+            with A = L + D + U
   * ilu0:   M = L U, the incomplete LU factorisation with no fill, i.e. L
             and U keep exactly the sparsity pattern of A (App. D.3 item 7).
+
+Reading for SSOR: omega = 1 (not stated) and the same red-black ordering
+as ILU(0) below, so that both sweeps are parallel over one colour each.
 
 Reading for ILU(0) (the paper does not fix the ordering): the unknowns of
 the 5/7-point grid are taken in red-black order (red: even i + j [+ l]),
@@ -90,10 +96,26 @@ def ilu0_redblack(A, grid):
     return perm, L, U
 
 
-class RightPreconditioner:
-    """M^-1 as an operator, for M in {none, jacobi, ilu0}.
+def ssor_redblack(A, grid):
+    """Symmetric SOR (omega = 1) of the red-black reordered matrix:
+    (perm, L', U') with M = (D + L) D^-1 (D + U) = L' U', L' = I + L D^-1 unit
+    lower, U' = D + U, where Ap = A[perm][:, perm] = L + D + U."""
+    perm = redblack_permutation(grid)
+    Ap = sp.csr_matrix(A)[perm][:, perm]
+    d = Ap.diagonal()
+    if np.any(d == 0):
+        raise ZeroDivisionError("zero diagonal entry")
+    Lo = sp.tril(Ap, k=-1, format="csr")
+    Up = sp.triu(Ap, k=0, format="csr")
+    Lp = (sp.identity(Ap.shape[0], format="csr") + Lo @ sp.diags(1.0 / d)).tocsr()
+    return perm, Lp, Up
 
-    ilu0 needs the grid shape (red-black ordering, see the module readings).
+
+class RightPreconditioner:
+    """M^-1 as an operator, for M in {none, jacobi, ssor, ilu0}.
+
+    ssor and ilu0 need the grid shape (red-black ordering, see the module
+    readings).
     """
 
     def __init__(self, A, kind, grid=None):
@@ -102,10 +124,10 @@ class RightPreconditioner:
             pass
         elif kind == "jacobi":
             self.dinv = jacobi_inv_diag(A)
-        elif kind == "ilu0":
+        elif kind in ("ilu0", "ssor"):
             if grid is None:
-                raise ValueError("ilu0 needs the grid shape")
-            self.perm, self.L, self.U = ilu0_redblack(A, grid)
+                raise ValueError(kind + " needs the grid shape")
+            self.perm, self.L, self.U = (ilu0_redblack if kind == "ilu0" else ssor_redblack)(A, grid)
         else:
             raise ValueError(kind)
 

@@ -37,6 +37,7 @@ SKR_FMT_POISSON2D = 7
 SKR_PC_NONE = 0
 SKR_PC_JACOBI = 1
 SKR_PC_ILU0 = 2
+SKR_PC_SSOR = 3
 SKR_PREC_FP64 = 0
 SKR_PREC_MIXED = 1
 SKR_MEM_DEVICE = 0
@@ -44,7 +45,7 @@ SKR_MEM_HOST = 1
 SKR_MAX_M = 48
 SKR_MAX_K = 24
 
-PRECOND = {"none": SKR_PC_NONE, "jacobi": SKR_PC_JACOBI, "ilu0": SKR_PC_ILU0}
+PRECOND = {"none": SKR_PC_NONE, "jacobi": SKR_PC_JACOBI, "ilu0": SKR_PC_ILU0, "ssor": SKR_PC_SSOR}
 PRECISION = {"fp64": SKR_PREC_FP64, "mixed": SKR_PREC_MIXED}
 
 

@@ -294,7 +294,7 @@ skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t precision, 
     if (!sys || !v || !y) return fail(SKR_ERR_INVALID_ARG, "NULL pointer");
     skr_status s0 = check_system(*sys, 0);
     if (s0 != SKR_OK) return s0;
-    if (precond != SKR_PC_NONE && precond != SKR_PC_JACOBI && precond != SKR_PC_ILU0)
+    if (precond != SKR_PC_NONE && precond != SKR_PC_JACOBI && precond != SKR_PC_ILU0 && precond != SKR_PC_SSOR)
         return fail(SKR_ERR_INVALID_ARG, "unknown preconditioner %d", precond);
     if (precision != SKR_PREC_FP64 && precision != SKR_PREC_MIXED)
         return fail(SKR_ERR_INVALID_ARG, "bad precision");
@@ -313,7 +313,7 @@ skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t precision, 
     CUDA_TRY(A.alloc((size_t)g.nst * g.n * 8));
     CUDA_TRY(dinv.alloc((size_t)g.n * 8));
     rows_kernel<<<grid_for(g.n, 256), 256, 0, st>>>(sg.dev, g, anode.as<double>(), A.as<double>(), g.n, nullptr,
-                                                     dinv.as<double>(), precond == SKR_PC_ILU0 ? SKR_PC_NONE : precond);
+                                                     dinv.as<double>(), (precond == SKR_PC_ILU0 || precond == SKR_PC_SSOR) ? SKR_PC_NONE : precond);
     CUDA_TRY(cudaGetLastError());
     const double *vin = v;
     double *yout = y;
@@ -325,10 +325,10 @@ skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t precision, 
         yout = dy.as<double>();
     }
     const int gb = grid_for(g.n, 256);
-    if (precond == SKR_PC_ILU0) {
+    if (precond == SKR_PC_ILU0 || precond == SKR_PC_SSOR) {
         DBuf inv, invw, zb;
         CUDA_TRY(inv.alloc((size_t)g.n * 8));
-        ilu_pivot_kernel<<<gb, 256, 0, st>>>(g, A.as<double>(), g.n, inv.as<double>());
+        ilu_pivot_kernel<<<gb, 256, 0, st>>>(g, A.as<double>(), g.n, inv.as<double>(), precond);
         const size_t es = (precision == SKR_PREC_MIXED) ? 4 : 8;
         CUDA_TRY(Aw.alloc((size_t)g.nst * g.n * es));
         CUDA_TRY(invw.alloc((size_t)g.n * es));
@@ -387,7 +387,8 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     if (!(opt.tol > 0.0) || !(opt.tol < 1.0)) return fail(SKR_ERR_INVALID_ARG, "tol must be in (0, 1)");
     if (opt.precision == SKR_PREC_MIXED && !(opt.inner_tol > 0.0 && opt.inner_tol < 1.0))
         return fail(SKR_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
-    if (opt.precond != SKR_PC_NONE && opt.precond != SKR_PC_JACOBI && opt.precond != SKR_PC_ILU0)
+    if (opt.precond != SKR_PC_NONE && opt.precond != SKR_PC_JACOBI && opt.precond != SKR_PC_ILU0 &&
+        opt.precond != SKR_PC_SSOR)
         return fail(SKR_ERR_INVALID_ARG, "unknown preconditioner %d", opt.precond);
     if (opt.precision != SKR_PREC_FP64 && opt.precision != SKR_PREC_MIXED)
         return fail(SKR_ERR_INVALID_ARG, "bad precision");

@@ -726,7 +726,7 @@ __device__ void ilu_spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
 
 template <typename T>
 __device__ __forceinline__ void operator_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
-    if (c.precond == SKR_PC_ILU0)
+    if (colour_sweep_pc(c.precond))
         ilu_spmv_pass(c, src, s, vout, y);
     else
         spmv_pass(c, src, s, vout, y);
@@ -808,13 +808,13 @@ __device__ __noinline__ void assemble_system(Ctx<T> &c, const DevSystem &sys) {
         }
     }
     cl_sync();
-    if (c.precond == SKR_PC_ILU0) {
-        // red-black ILU(0): inverse pivots (black ones need the neighbours'
-        // rows), and the unscaled operator in working precision
+    if (colour_sweep_pc(c.precond)) {
+        // red-black ILU(0) / SSOR: inverse pivots (ILU's black ones need the
+        // neighbours' rows), and the unscaled operator in working precision
         T *inv = c.Aw + (long long)7 * c.ld;
         for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
             if (p < c.g.n) {
-                const double ip = ilu_inv_pivot(c.g, c.A64, c.ld, p);
+                const double ip = sweep_inv_pivot(c.g, c.A64, c.ld, p, c.precond);
                 c.dinv[p] = ip;
                 inv[p] = (T)ip;
                 for (int s = 0; s < c.g.nst; s++) c.Aw[(long long)s * c.ld + p] = (T)c.A64[(long long)s * c.ld + p];
@@ -872,7 +872,7 @@ __device__ __noinline__ void refresh_recycle(Ctx<T> &c) {
     const int cC0 = COL_C_END - kc;
     // W = A M^-1 U into the C columns
     const long long hi = c.lo + c.cnt;
-    if (c.precond == SKR_PC_ILU0) {
+    if (colour_sweep_pc(c.precond)) {
         for (int b = 0; b < kc; b++) ilu_spmv_pass(c, c.col(COL_U0 + b), T(1), (T *)nullptr, c.col(cC0 + b));
     } else
     for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
@@ -1512,7 +1512,7 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx, bool war
             }
         }
         // x += M^-1 d (FP64)
-        if (c.precond == SKR_PC_ILU0) {
+        if (colour_sweep_pc(c.precond)) {
             cl_sync();   // d of the neighbours
             for (long long p = c.lo + threadIdx.x; p < hi && p < c.g.n; p += blockDim.x)
                 if (grid_color(c.g, p) == 1)

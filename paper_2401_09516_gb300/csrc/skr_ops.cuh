@@ -52,11 +52,11 @@ __global__ void apply_kernel(Geom g, const T *Aw, long long ld, const T *v, doub
         y[p] = (double)stencil_apply_row(g, Aw, ld, v, T(1), p);
 }
 
-// red-black ILU(0) for the stand-alone operator entry point
-__global__ void ilu_pivot_kernel(Geom g, const double *A, long long ld, double *inv) {
+// red-black ILU(0) / SSOR for the stand-alone operator entry point
+__global__ void ilu_pivot_kernel(Geom g, const double *A, long long ld, double *inv, int pc) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n;
          p += (long long)gridDim.x * blockDim.x)
-        inv[p] = ilu_inv_pivot(g, A, ld, p);
+        inv[p] = sweep_inv_pivot(g, A, ld, p, pc);
 }
 
 template <typename T>

@@ -394,7 +394,8 @@ skr_status skr_server_create(const skr_options *opt_in, size_t hbm_budget, int32
         return err(SKR_ERR_INVALID_ARG, "bad maxit, max_refine or tol");
     if (opt.precision == SKR_PREC_MIXED && !(opt.inner_tol > 0.0 && opt.inner_tol < 1.0))
         return err(SKR_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
-    if (opt.precond != SKR_PC_NONE && opt.precond != SKR_PC_JACOBI && opt.precond != SKR_PC_ILU0)
+    if (opt.precond != SKR_PC_NONE && opt.precond != SKR_PC_JACOBI && opt.precond != SKR_PC_ILU0 &&
+        opt.precond != SKR_PC_SSOR)
         return err(SKR_ERR_INVALID_ARG, "unknown preconditioner");
     if ((opt.warm_start != 0 && opt.warm_start != 1) || (opt.diagnostics != 0 && opt.diagnostics != 1))
         return err(SKR_ERR_INVALID_ARG, "warm_start and diagnostics must be 0 or 1");

@@ -261,6 +261,16 @@ __device__ __forceinline__ double ilu_inv_pivot(const Geom &g, const double *A, 
     return 1.0 / d;
 }
 
+// Symmetric SOR with omega = 1 in red-black order, M = (D + L) D^-1 (D + U):
+// its red rows are those of A and its black-black block is
+// D_b + A_br D_r^-1 A_rb, so it is the factorisation above with the black
+// pivots d_b = a_bb (the diagonal correction dropped): the same two sweeps.
+__device__ __forceinline__ bool colour_sweep_pc(int pc) { return pc == SKR_PC_ILU0 || pc == SKR_PC_SSOR; }
+
+__device__ __forceinline__ double sweep_inv_pivot(const Geom &g, const double *A, long long ld, long long p, int pc) {
+    return (pc == SKR_PC_SSOR) ? 1.0 / A[p] : ilu_inv_pivot(g, A, ld, p);
+}
+
 // sweep 1 (black rows): z_b = inv_b (v_b - sum_r a_br inv_r v_r), v = scale * src
 template <typename R, typename Tv>
 __device__ __forceinline__ R ilu_sweep1_row(const Geom &g, const R *Aw, long long ld, const R *inv, const Tv *src,

@@ -325,13 +325,14 @@ def test_apply_ilu0_operator(skr, kind):
         loga = rng.standard_normal((9, 8, 7))
         A, _ = assembly.darcy3d(loga)
         sysd, grid = skr.darcy3d(_dev(loga)), (7, 6, 5)
-    M = oprecond.RightPreconditioner(A, "ilu0", grid)
     v = rng.standard_normal(A.shape[0])
-    want = A @ M.apply(v)
-    y64 = skr.skr_apply(sysd, _dev(v), precond="ilu0", precision="fp64").cpu().numpy()
-    np.testing.assert_allclose(y64, want, rtol=1e-11, atol=1e-12 * np.abs(want).max())
-    y32 = skr.skr_apply(sysd, _dev(v), precond="ilu0", precision="mixed").cpu().numpy()
-    assert np.abs(y32 - want).max() <= 2e-5 * np.abs(want).max()
+    for pc in ("ilu0", "ssor"):   # the red-black colour-sweep preconditioners
+        M = oprecond.RightPreconditioner(A, pc, grid)
+        want = A @ M.apply(v)
+        y64 = skr.skr_apply(sysd, _dev(v), precond=pc, precision="fp64").cpu().numpy()
+        np.testing.assert_allclose(y64, want, rtol=1e-11, atol=1e-12 * np.abs(want).max())
+        y32 = skr.skr_apply(sysd, _dev(v), precond=pc, precision="mixed").cpu().numpy()
+        assert np.abs(y32 - want).max() <= 2e-5 * np.abs(want).max(), pc
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -513,3 +514,28 @@ def test_delta_diagnostic_matches_oracle(skr):
     _, res0 = skr.skr_solve_sequence(systems, order=order, options=opt0)
     assert all(r["delta"] == -1.0 for r in res0)
     assert [r["steps"] for r in res0] == [r["steps"] for r in res]   # diagnostics do not change the solve
+
+
+# ------------------------------------------------------------------ SSOR (App. D.3)
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_darcy_ssor_matches_oracle(skr, precision):
+    L = darcy2d_sequence(40, 6, 0.15, seed=23)
+    order = osort.greedy_sort(L.reshape(6, -1))
+    systems = [skr.darcy2d(_dev(l)) for l in L]
+    opt = skr.skr_options_default(m=30, k=10, tol=1e-8, precond="ssor", precision=precision)
+    xs, res = skr.skr_solve_sequence(systems, order=order, options=opt)
+    sysd = [dict(kind="darcy2d", loga=l) for l in L]
+    xo, info = oskr.solve_sequence(sysd, order, "ssor", 30, 10, 1e-8, precision="fp64")
+    for i in range(6):
+        A, b = assembly.darcy2d(L[i])
+        assert res[i]["flag"] == 0, res[i]
+        _check_solution(xs[i], A, b, 1e-8, spla_solve(A, b), 1e-6)
+    if precision == "fp64":
+        tot_g = sum(r["steps"] for r in res)
+        tot_o = sum(i["steps"] for i in info)
+        assert abs(tot_g - tot_o) <= 0.15 * tot_o, (tot_g, tot_o)
+    # SSOR needs fewer steps than Jacobi on the same sequence
+    optj = skr.skr_options_default(m=30, k=10, tol=1e-8, precond="jacobi", precision=precision)
+    _, resj = skr.skr_solve_sequence(systems, order=order, options=optj)
+    assert sum(r["steps"] for r in res) < sum(r["steps"] for r in resj)

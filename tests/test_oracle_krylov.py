@@ -353,3 +353,46 @@ def test_sequence_reports_delta_per_system():
     _, info = skr.solve_sequence(sysd, [0, 1, 2, 3], "none", 20, 6, 1e-8)
     assert info[0]["delta"] == -1.0                      # nothing recycled into the first system
     assert all(0.0 <= info[i]["delta"] <= 1.0 for i in (1, 2, 3))
+
+
+def _gauss_seidel_ssor(A, v):
+    """One forward then one backward Gauss-Seidel sweep from x = 0 (the SSOR
+    iteration with omega = 1, written as scalar loops)."""
+    A = A.toarray()
+    n = len(v)
+    x = np.zeros(n)
+    for i in range(n):
+        x[i] = (v[i] - A[i, :i] @ x[:i] - A[i, i + 1:] @ x[i + 1:]) / A[i, i]
+    for i in reversed(range(n)):
+        x[i] = (v[i] - A[i, :i] @ x[:i] - A[i, i + 1:] @ x[i + 1:]) / A[i, i]
+    return x
+
+
+def test_ssor_is_a_symmetric_gauss_seidel_sweep_in_redblack_order():
+    L = darcy2d_sequence(5, 1, 0.3, seed=6)
+    A, _ = assembly.darcy2d(L[0])
+    grid = (5, 5)
+    M = oprecond.RightPreconditioner(A, "ssor", grid)
+    perm = oprecond.redblack_permutation(grid)
+    Ap = sp.csr_matrix(A)[perm][:, perm]
+    v = np.random.default_rng(1).standard_normal(25)
+    z = M.apply(v)
+    np.testing.assert_allclose(z[perm], _gauss_seidel_ssor(Ap, v[perm]), rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("grid", [(6, 5), (4, 3, 5)])
+def test_redblack_ssor_closed_form(grid):
+    # red rows of M are those of A; the black-black block is D_b + A_br D_r^-1 A_rb
+    if len(grid) == 2:
+        A, _ = assembly.darcy2d(darcy2d_sequence(grid[0], 1, 0.3, seed=7)[0][: grid[0] + 2, : grid[1] + 2])
+    else:
+        from workloads import darcy3d_sequence
+        A, _ = assembly.darcy3d(darcy3d_sequence(max(grid), 1, 0.3, seed=7)[0][: grid[0] + 2, : grid[1] + 2, : grid[2] + 2])
+    perm, Lp, Up = oprecond.ssor_redblack(A, grid)
+    M = (Lp @ Up).toarray()
+    Ap = sp.csr_matrix(A)[perm][:, perm].toarray()
+    nr = (np.indices(grid).reshape(len(grid), -1).sum(axis=0) % 2 == 0).sum()
+    np.testing.assert_allclose(M[:nr], Ap[:nr], rtol=1e-13, atol=1e-13 * np.abs(Ap).max())
+    Dr = np.diag(Ap)[:nr]
+    want_bb = np.diag(np.diag(Ap)[nr:]) + Ap[nr:, :nr] @ np.diag(1.0 / Dr) @ Ap[:nr, nr:]
+    np.testing.assert_allclose(M[nr:, nr:], want_bb, rtol=1e-13, atol=1e-13 * np.abs(Ap).max())

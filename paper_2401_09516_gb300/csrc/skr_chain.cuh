@@ -33,14 +33,10 @@ constexpr int CHAIN_THREADS = 512;
 constexpr int CHAIN_MIN_BLOCKS = 1;
 
 template <> struct Tiles<float> {
-    static constexpr int G = 32;   // columns per multi-dot group
-    static constexpr int G2 = 16;  // columns per group of the two-target multi-dot
-    static constexpr int TA = 8;   // Gram tile rows
+    static constexpr int TA = 8;   // Gram tile rows (recycle refresh)
     static constexpr int TB = 8;   // Gram tile cols
 };
 template <> struct Tiles<double> {
-    static constexpr int G = 16;
-    static constexpr int G2 = 8;
     static constexpr int TA = 4;
     static constexpr int TB = 8;
 };
@@ -263,38 +259,10 @@ __device__ __forceinline__ void allreduce(Ctx<T> &c, int nv) {
 
 // ------------------------------------------------------------------ streaming passes
 
-// CTA partials of Q_j . y for the q columns starting at c0 (own rows), into out[0..q).
-template <typename T>
-__device__ void part_multidot(Ctx<T> &c, int c0, int q, const T *y, T *out) {
-    typedef typename Vec<T>::type VT;
-    constexpr int E = Vec<T>::N, G = Tiles<T>::G;
-    const int nvec = (int)(c.cnt / E);
-    const VT *yv = reinterpret_cast<const VT *>(y + c.lo);
-    T *wsum = reinterpret_cast<T *>(c.D(c.P.o_wsum));
-    for (int g0 = 0; g0 < q; g0 += G) {
-        const int gq = min(G, q - g0);
-        T acc[G];
-#pragma unroll
-        for (int j = 0; j < G; j++) acc[j] = T(0);
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-            const VT yy = yv[i];
-#pragma unroll
-            for (int j = 0; j < G; j++) {
-                if (j < gq) {
-                    const VT xv = reinterpret_cast<const VT *>(c.col(c0 + g0 + j) + c.lo)[i];
-                    acc[j] += vdot(xv, yy);
-                }
-            }
-        }
-        block_sum<G>(acc, gq, wsum, out + g0);
-    }
-    c.bytes += (unsigned long long)(q + 1) * c.g.n * sizeof(T);
-}
+// ------------------------------------------------------------------ staged streaming
 
 // Control int set when a staged copy did not land within RING_WAIT_NS.
 constexpr int INT_STALL = 6;
-
-// ------------------------------------------------------------------ staged streaming
 
 // A pass that streams the CTA's own rows of up to four runs of contiguous
 // basis columns through the shared-memory ring.  For every block of
@@ -946,7 +914,7 @@ __device__ __noinline__ double project_recycle(Ctx<T> &c) {
     const int kc = c.kc;
     const int cC0 = COL_C_END - kc;
     T *rw = c.col(COL_RW), *dh = c.col(COL_DH);
-    part_multidot(c, cC0, kc, rw, c.template red<T>());
+    staged_dual_dots<T, true, false>(c, cC0, kc, COL_RW, -1, c.template red<T>());
     allreduce<T, T>(c, kc);
     T *z = c.tco(c.P.t_h);
     for (int i = threadIdx.x; i < kc; i += blockDim.x) z[i] = c.template vals<T>()[i];

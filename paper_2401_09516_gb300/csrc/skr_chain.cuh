@@ -493,36 +493,39 @@ __device__ void dual_update(Ctx<T> &c, int c0, int q, const T *sv, const T *al, 
 // CTA partials of the Gram matrix of a cycle end, over own rows:
 //   out[a * nb + b] = Z_a . U_b  (a < na columns Z from a0, b < nb columns U from b0),
 //   out[na * nb + b] = U_b . U_b.
-// One staged pass per chunk of up to GB columns of U (and of up to 3 x warps
-// columns of Z).  Warp w owns the Z columns a = w (mod warps) and the lanes
-// consecutive 16-byte row vectors, so shared-memory loads are conflict free,
-// each U vector feeds up to 3 x E multiply-adds per lane, and every output
-// is one warp sum.
+// One staged pass per chunk of up to 4 BW columns of U (and of up to 4 AW
+// columns of Z).  The warps form a 4 x 4 grid: warp (ag, bg) owns the Z
+// columns a = ag (mod 4) and the U columns b = bg (mod 4) of the chunk, and
+// its lanes consecutive 16-byte row vectors, so shared-memory loads are
+// conflict free, every lane loads AW + BW vectors per row for AW x BW
+// products, and every output is one warp sum.
 template <typename T>
 __device__ __noinline__ void staged_gram(Ctx<T> &c, int a0, int na, int b0, int nb, T *out) {
     typedef typename Vec<T>::type VT;
     constexpr int E = Vec<T>::N;
     constexpr int R = RING_SEG_BYTES / (int)sizeof(T);
     constexpr int RV = R / E;   // vectors per segment
-    constexpr int NW = CHAIN_THREADS / 32;
-    constexpr int AW = 3;       // Z columns per warp and chunk
-    constexpr int GB = (sizeof(T) == 4) ? 20 : 8;   // U columns per chunk (registers)
-    static_assert(RV % 32 == 0, "ring geometry");
+    constexpr int AW = 12;      // Z columns per warp and chunk
+    constexpr int BW = (sizeof(T) == 4) ? 5 : 2;   // U columns per warp and chunk (registers)
+    static_assert(RV % 32 == 0 && CHAIN_THREADS == 512, "ring geometry");
     const int lane = lane_id(), wp = warp_id();
+    const int ag = wp & 3, bg = wp >> 2;
     const int cap_segs = (int)((long long)c.P.ring_cap * 8 / RING_SEG_BYTES);
-    for (int ac = 0; ac < na; ac += NW * AW) {
-        const int nac = min(NW * AW, na - ac);
+    for (int ac = 0; ac < na; ac += 4 * AW) {
+        const int nac = min(4 * AW, na - ac);
         // two stages of nac + nbc segments fit: the ring holds >= 2 (m + 2)
-        const int gbmax = min(GB, cap_segs / 2 - nac);
+        const int gbmax = min(4 * BW, cap_segs / 2 - nac);
         for (int bc = 0; bc < nb; bc += gbmax) {
             const int nbc = min(gbmax, nb - bc);
-            const bool norms = (ac == 0);
-            T acc[AW][GB];
-            T nrm[2] = {T(0), T(0)};
+            const bool norms = (ac == 0) && (ag == 0);
+            T acc[AW][BW];
+            T nrm[BW];
 #pragma unroll
-            for (int aa = 0; aa < AW; aa++)
+            for (int bb = 0; bb < BW; bb++) {
+                nrm[bb] = T(0);
 #pragma unroll
-                for (int bb = 0; bb < GB; bb++) acc[aa][bb] = T(0);
+                for (int aa = 0; aa < AW; aa++) acc[aa][bb] = T(0);
+            }
             const int rs[2] = {a0 + ac, b0 + bc};
             const int rl[2] = {nac, nbc};
             const RingPass rp = ring_begin_runs(c, rs, rl, 2);
@@ -533,20 +536,20 @@ __device__ __noinline__ void staged_gram(Ctx<T> &c, int a0, int na, int b0, int 
                 for (int h = 0; h < RV / 32; h++) {
                     const int vi = lane + 32 * h;
                     if (vi < nv) {
-                        VT z[AW];
+                        VT u[BW];
 #pragma unroll
-                        for (int aa = 0; aa < AW; aa++) {
-                            const int aidx = wp + NW * aa;
-                            z[aa] = (aidx < nac) ? sb[aidx * RV + vi] : vzero(T(0));
+                        for (int bb = 0; bb < BW; bb++) {
+                            const int bidx = bg + 4 * bb;
+                            u[bb] = (bidx < nbc) ? sb[(nac + bidx) * RV + vi] : vzero(T(0));
+                            if (norms) nrm[bb] += vdot(u[bb], u[bb]);
                         }
 #pragma unroll
-                        for (int bb = 0; bb < GB; bb++) {
-                            if (bb < nbc) {
-                                const VT u = sb[(nac + bb) * RV + vi];
+                        for (int aa = 0; aa < AW; aa++) {
+                            const int aidx = ag + 4 * aa;
+                            if (aidx < nac) {
+                                const VT z = sb[aidx * RV + vi];
 #pragma unroll
-                                for (int aa = 0; aa < AW; aa++) acc[aa][bb] += vdot(z[aa], u);
-                                if (norms && bb == wp) nrm[0] += vdot(u, u);
-                                if (norms && bb == wp + NW) nrm[1] += vdot(u, u);
+                                for (int bb = 0; bb < BW; bb++) acc[aa][bb] += vdot(z, u[bb]);
                             }
                         }
                     }
@@ -556,17 +559,21 @@ __device__ __noinline__ void staged_gram(Ctx<T> &c, int a0, int na, int b0, int 
             ring_end(c, rp);
 #pragma unroll
             for (int aa = 0; aa < AW; aa++) {
-                const int aidx = wp + NW * aa;
+                const int aidx = ag + 4 * aa;
 #pragma unroll
-                for (int bb = 0; bb < GB; bb++) {
+                for (int bb = 0; bb < BW; bb++) {
+                    const int bidx = bg + 4 * bb;
                     const T v = warp_sum(acc[aa][bb]);
-                    if (lane == 0 && aidx < nac && bb < nbc) out[(ac + aidx) * nb + bc + bb] = v;
+                    if (lane == 0 && aidx < nac && bidx < nbc) out[(ac + aidx) * nb + bc + bidx] = v;
                 }
             }
             if (norms) {
-                const T v0 = warp_sum(nrm[0]), v1 = warp_sum(nrm[1]);
-                if (lane == 0 && wp < nbc) out[na * nb + bc + wp] = v0;
-                if (lane == 0 && wp + NW < nbc) out[na * nb + bc + wp + NW] = v1;
+#pragma unroll
+                for (int bb = 0; bb < BW; bb++) {
+                    const int bidx = bg + 4 * bb;
+                    const T v = warp_sum(nrm[bb]);
+                    if (lane == 0 && bidx < nbc) out[na * nb + bc + bidx] = v;
+                }
             }
         }
     }

@@ -18,8 +18,22 @@ Readings (listed in DESIGN.md):
     and add, no fused multiply-add); the 256 lane sums are then added
     pairwise, lane l with lane l + half, for half = 128, 64, ..., 1.
 
+Large N (the paragraph after Algorithm 1 in Sec. 4.1): divide the systems
+into groups of bounded size by their coordinates, run Algorithm 1 inside each
+group, and concatenate the groups' orders.  Readings:
+  * "by their coordinates" is recursive coordinate bisection: a set of more
+    than G systems is split along the coordinate (entry of the flattened
+    parameter array) whose spread max - min over the set is largest (the
+    lowest coordinate on ties), at the median: with the set ordered by
+    (value of that coordinate, index), the first floor(s/2) go to the first
+    half and the rest to the second; sets of at most G systems are groups;
+  * groups are concatenated in the order of the recursion, first half first;
+  * inside a group, Algorithm 1 scans the group's systems in ascending index
+    order and starts from the group's lowest index.
+
 Pins: brute force with exact rational distances on small inputs; hand-made
-ties; permutation and start properties.
+ties; permutation and start properties; hand-derived bisections; the
+grouped order with G >= N equals Algorithm 1's.
 """
 import numpy as np
 
@@ -81,3 +95,46 @@ def greedy_sort(P, start=0):
         order.append(jmin)
         i0 = jmin
     return order
+
+
+def coordinate_groups(P, group_max):
+    """Groups of the large-N sort (Sec. 4.1): recursive coordinate bisection.
+
+    P          (N, p) float64
+    group_max  G >= 1, the largest group size
+    Returns a list of groups, each a list of indices in ascending order, in
+    concatenation order.
+    """
+    P = np.asarray(P, dtype=np.float64)
+    N = P.shape[0]
+    if group_max < 1:
+        raise ValueError("group_max < 1")
+    if not np.all(np.isfinite(P)):
+        raise ValueError("non-finite parameters")
+
+    def split(members):
+        if len(members) <= group_max:
+            return [sorted(members)]
+        X = P[members]
+        spread = X.max(axis=0) - X.min(axis=0)
+        c = int(np.argmax(spread))          # first maximum: lowest coordinate on ties
+        ordered = sorted(members, key=lambda i: (P[i, c], i))
+        h = len(members) // 2
+        return split(ordered[:h]) + split(ordered[h:])
+
+    return split(list(range(N))) if N else []
+
+
+def grouped_sort(P, group_max):
+    """The large-N order (Sec. 4.1): Algorithm 1 inside each coordinate group.
+
+    Returns (order, offsets): the concatenated order (N indices) and the
+    ngroups + 1 offsets of the groups in it.
+    """
+    P = np.asarray(P, dtype=np.float64)
+    order, offsets = [], [0]
+    for g in coordinate_groups(P, group_max):
+        local = greedy_sort(P[g], start=0)
+        order.extend(g[a] for a in local)
+        offsets.append(len(order))
+    return order, offsets

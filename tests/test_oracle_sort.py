@@ -102,3 +102,82 @@ def test_large_distances_not_stale():
     # every distance far above the paper's "e.g. 1000" initial value
     P = np.array([[0.0], [1e5], [3e5], [2e5]])
     assert sort.greedy_sort(P, 0) == [0, 1, 3, 2]
+
+
+# ------------------------------------------------------------------ large-N grouped sort (Sec. 4.1)
+
+def test_grouped_sort_hand_derived_bisection():
+    # top split on x (spread 13 > 8); each half then splits on y (spread 7 > 3)
+    P = np.array([[0, 0], [10, 1], [1, 5], [11, 6], [2, 2], [12, 3], [3, 7], [13, 8]], dtype=float)
+    assert sort.coordinate_groups(P, 2) == [[0, 4], [2, 6], [1, 5], [3, 7]]
+    order, offs = sort.grouped_sort(P, 2)
+    assert order == [0, 4, 2, 6, 1, 5, 3, 7] and offs == [0, 2, 4, 6, 8]
+
+
+def test_grouped_sort_odd_sizes_put_the_smaller_half_first():
+    # 5 = 2 + 3 by value, then 3 = 1 + 2
+    P = np.array([[5.0], [1.0], [4.0], [2.0], [3.0]])
+    assert sort.coordinate_groups(P, 2) == [[1, 3], [4], [0, 2]]
+    assert sort.grouped_sort(P, 2) == ([1, 3, 4, 0, 2], [0, 2, 3, 5])
+
+
+def test_grouped_sort_ties_lowest_coordinate_and_lowest_index():
+    # equal spreads (3 and 3): the split is along coordinate 0
+    P = np.array([[0, 3], [3, 0], [1, 2], [2, 1]], dtype=float)
+    assert sort.coordinate_groups(P, 2) == [[0, 2], [1, 3]]
+    # equal values along the split coordinate: index order decides
+    assert sort.coordinate_groups(np.full((4, 1), 7.0), 2) == [[0, 1], [2, 3]]
+    # -0.0 and +0.0 are equal values
+    Z = np.array([[0.0], [-0.0], [0.0], [-0.0]])
+    assert sort.coordinate_groups(Z, 2) == [[0, 1], [2, 3]]
+
+
+def test_grouped_sort_one_group_is_algorithm_1():
+    rng = np.random.default_rng(7)
+    P = rng.standard_normal((23, 40))
+    for G in (23, 100):
+        order, offs = sort.grouped_sort(P, G)
+        assert order == _exact_greedy(P, 0) and offs == [0, 23]
+
+
+def test_grouped_sort_one_dimensional_groups_are_value_quantiles():
+    rng = np.random.default_rng(8)
+    v = rng.permutation(64).astype(float) * 0.5 - 3.0
+    groups = sort.coordinate_groups(v[:, None], 8)
+    ranks = np.argsort(v, kind="stable")
+    assert groups == [sorted(ranks[8 * q:8 * q + 8].tolist()) for q in range(8)]
+    order, offs = sort.grouped_sort(v[:, None], 8)
+    for q, g in enumerate(groups):
+        seg = order[offs[q]:offs[q + 1]]
+        assert seg == [g[a] for a in _exact_greedy(v[g][:, None], 0)]
+
+
+def test_grouped_sort_recovers_separated_clusters():
+    rng = np.random.default_rng(9)
+    centres = np.array([[0.0, 0.0], [100.0, 0.0], [0.0, 60.0], [100.0, 60.0]])
+    lab = rng.permutation(np.repeat(np.arange(4), 8))
+    P = centres[lab] + rng.uniform(-1, 1, size=(32, 2))
+    groups = sort.coordinate_groups(P, 8)
+    assert sorted(sorted(g) for g in groups) == sorted(np.flatnonzero(lab == c).tolist() for c in range(4))
+
+
+@pytest.mark.parametrize("seed,N,p,G", [(0, 37, 6, 5), (1, 100, 3, 7), (2, 64, 50, 1), (3, 11, 2, 3), (4, 7, 4, 3)])
+def test_grouped_sort_sizes_and_permutation(seed, N, p, G):
+    rng = np.random.default_rng(seed)
+    P = rng.standard_normal((N, p))
+    groups = sort.coordinate_groups(P, G)
+    order, offs = sort.grouped_sort(P, G)
+    assert sorted(order) == list(range(N))
+    if (N, G) == (7, 3):
+        assert sorted(len(g) for g in groups) == [2, 2, 3]
+    sizes = [len(g) for g in groups]
+    assert max(sizes) <= G and sum(sizes) == N and np.diff(offs).tolist() == sizes
+    # halving at every level: sets at depth d hold floor(N / 2^d) or
+    # ceil(N / 2^d) systems, and no group is deeper than the first depth at
+    # which every set fits
+    depth = 0
+    while -(-N // 2 ** depth) > G:
+        depth += 1
+    assert min(sizes) >= N // 2 ** depth
+    for q, g in enumerate(groups):
+        assert order[offs[q]] == g[0]   # each group starts at its lowest index

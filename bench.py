@@ -518,6 +518,83 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _grouped_sort_launches(N, p, G):
+    """Kernel launches of one skr_sort_grouped call (its host loop, counted)."""
+    M = 1024
+    while M < N:
+        M <<= 1
+    bitonic, k = 1, 2048
+    while k <= M:
+        bitonic += (k.bit_length() - 1) - 10 + 1   # global steps j = k/2 .. 1024, then one local pass
+        k <<= 1
+    batch = max(1, (1 << 25) // p)
+    launches, sets = 2, [N]
+    while any(s > G for s in sets):
+        nsplit = sum(1 for s in sets if s > G)
+        launches += 3 * (-(-nsplit // batch)) + 1 + bitonic + 1
+        sets = [h for s in sets for h in ((s // 2, s - s // 2) if s > G else (s,))]
+    return launches + (1 + bitonic + 1) + 2
+
+
+def run_sort_only(args):
+    """Time the large-N grouped sort (Sec. 4.1) on N seeded coefficient keys."""
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2401_09516_gb300 as skr
+    N, p, G = args.nsys, args.keys_p, args.group_max
+    rng = np.random.default_rng(4000 + rank)
+    # coefficient keys with a decaying spectrum, like the Chebyshev data of the Poisson workload
+    Kh = rng.standard_normal((N, p)) / (1.0 + np.arange(p))[None, :]
+    P = torch.tensor(Kh, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        perm, offs = skr.skr_sort_grouped(P, G, stream=stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        perm, offs = skr.skr_sort_grouped(P, G, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    ms = sum(times) / len(times)
+    sizes = np.diff(offs)
+    line = {
+        "metric": "systems/s through the grouped greedy sort (Sec. 4.1, large N)",
+        "value": round(N / (ms / 1e3), 1), "unit": "systems/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "grouped sort, N=%d keys of p=%d decaying Gaussian coefficients, groups of at most %d"
+                               % (N, p, G),
+                   "groups": int(len(sizes)), "group_sizes": [int(sizes.min()), int(sizes.max())],
+                   "l2": "flushed between steps (256 MB write)"},
+        "gpu_launches": _grouped_sort_launches(N, p, G) * args.steps,
+        "clocks": clocks,
+    }
+    if args.cpu_baseline:
+        from oracle import sort as osort
+        ns = min(N, 20000)
+        t0 = time.perf_counter()
+        osort.grouped_sort(Kh[:ns], G)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": round(ns / dt, 1), "unit": "systems/s", "cores": 1, "kind": "oracle",
+                                "sample": "the first %d keys, grouped sort with the same G, numpy FP64, one core" % ns}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -538,12 +615,18 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--sort-only", action="store_true",
+                    help="time the large-N grouped sort instead of the solves (use with --nsys)")
+    ap.add_argument("--keys-p", type=int, default=16, help="coordinates per key for --sort-only")
+    ap.add_argument("--group-max", type=int, default=1000, help="largest group for --sort-only")
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="upper bound on one reference sample")
     args = ap.parse_args()
     for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ.setdefault(var, "1")
-    if args.impl == "reference":
+    if args.sort_only:
+        run_sort_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -194,6 +194,38 @@ skr_status skr_sort_noalloc(const double *params, int64_t N, int64_t p, int64_t 
                             void *stream, int32_t *perm_out);
 
 /*
+ * skr_sort_grouped -- the large-N order of Sec. 4.1 (the paragraph after
+ * Algorithm 1): divide the systems into groups of at most group_max by
+ * their coordinates, order each group by Algorithm 1, concatenate.
+ *
+ * params         N x p doubles, row i = P(i) flattened (memory per mem)
+ * group_max      G >= 1, the largest group
+ * perm_out       N int32 (memory per mem): the solve order
+ * group_offsets  NULL, or a HOST array of at least ngroups + 1 int64 (N + 1
+ *                always suffice): group g is perm_out[off[g] .. off[g+1])
+ * ngroups        NULL, or HOST int64: the number of groups
+ * Groups: recursive coordinate bisection.  A set of s > G systems is split
+ * along the coordinate (entry of P(i)) whose spread max - min over the set
+ * is largest, the lowest coordinate on ties: ordered by (value of that
+ * coordinate, index), its first floor(s/2) systems form the first half,
+ * the rest the second; sets of at most G systems are groups, concatenated
+ * first half first.  Every set's size, hence every group offset, depends
+ * on N and G only.  Inside a group, Algorithm 1 scans its systems in
+ * ascending index order from its lowest index, with the distances of
+ * skr_sort (bit for bit).  With G >= N the result equals skr_sort's with
+ * start = 0.
+ * Scratch (allocated and freed by the call): the working index array, the
+ * sort keys (16 bytes per system, padded to a power of two >= 1024), per
+ * split set 16 bytes per coordinate, and the groups' distance matrices
+ * (sum of size^2 doubles, at most N x G).
+ * Errors: N < 0, p < 1 (when N > 0), group_max < 1, a non-finite parameter
+ * or distance -> SKR_ERR_INVALID_ARG; allocation failure -> SKR_ERR_OOM.
+ */
+skr_status skr_sort_grouped(const double *params, int64_t N, int64_t p, int64_t group_max,
+                            int32_t mem, void *stream, int32_t *perm_out,
+                            int64_t *group_offsets, int64_t *ngroups);
+
+/*
  * skr_solve_sequence -- Algorithm 2 over a sorted sequence (Sec. 4.2,
  * App. B), with the sorted list cut into independent chains (App. E.2.2).
  *

@@ -27,5 +27,6 @@ from ._native import (  # noqa: F401
     skr_submit,
     skr_solve_sequence,
     skr_sort,
+    skr_sort_grouped,
     skr_sort_noalloc,
 )

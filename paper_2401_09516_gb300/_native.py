@@ -96,6 +96,7 @@ _i32, _i64, _vp, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.
 _lib.skr_options_default.argtypes = [ctypes.POINTER(SkrOptions)]
 _lib.skr_sort.argtypes = [_vp, _i64, _i64, _i64, _i32, _vp, _vp]
 _lib.skr_sort_noalloc.argtypes = [_vp, _i64, _i64, _i64, _vp, _vp]
+_lib.skr_sort_grouped.argtypes = [_vp, _i64, _i64, _i64, _i32, _vp, _vp, _vp, _vp]
 _lib.skr_solve_sequence.argtypes = [ctypes.POINTER(SkrSystem), _i64, _vp, _vp, _i32,
                                     ctypes.POINTER(SkrOptions), ctypes.POINTER(_vp),
                                     ctypes.POINTER(SkrResult)]
@@ -112,7 +113,7 @@ _lib.skr_server_stats.argtypes = [_vp, ctypes.POINTER(SkrServerInfo)]
 _lib.skr_server_destroy.argtypes = [_vp]
 _lib.skr_last_error.argtypes = []
 _lib.skr_last_error.restype = ctypes.c_char_p
-for _fn in ("skr_options_default", "skr_sort", "skr_sort_noalloc", "skr_solve_sequence", "skr_assemble", "skr_apply",
+for _fn in ("skr_options_default", "skr_sort", "skr_sort_noalloc", "skr_sort_grouped", "skr_solve_sequence", "skr_assemble", "skr_apply",
             "skr_last_stats", "skr_last_profile", "skr_release_workspace", "skr_server_create",
             "skr_submit", "skr_poll", "skr_server_stats", "skr_server_destroy"):
     getattr(_lib, _fn).restype = ctypes.c_int32
@@ -262,6 +263,29 @@ def skr_sort(params, start=0, stream=None):
     _check(_lib.skr_sort(_ptr(P) if N else None, N, p, int(start), mem, _stream_handle(stream),
                          _ptr(perm) if N else None))
     return perm
+
+
+def skr_sort_grouped(params, group_max, stream=None):
+    """Large-N order (Sec. 4.1): coordinate groups of at most group_max
+    systems, Algorithm 1 inside each, concatenated.
+
+    Returns (perm, offsets): perm like skr_sort's (same memory as params),
+    offsets a host int64 array of ngroups + 1 group boundaries in perm.
+    """
+    P = _f64(params)
+    N = int(P.shape[0])
+    p = int(np.prod(P.shape[1:])) if N else 1
+    mem = _mem_of(P)
+    if mem == SKR_MEM_DEVICE:
+        import torch
+        perm = torch.empty(N, dtype=torch.int32, device=P.device)
+    else:
+        perm = np.empty(N, dtype=np.int32)
+    offs = np.zeros(N + 1, dtype=np.int64)
+    ng = ctypes.c_int64(0)
+    _check(_lib.skr_sort_grouped(_ptr(P) if N else None, N, p, int(group_max), mem, _stream_handle(stream),
+                                 _ptr(perm) if N else None, offs.ctypes.data, ctypes.byref(ng)))
+    return perm, offs[:ng.value + 1].copy()
 
 
 SKR_SORT_NOALLOC_MAX_N = 512
@@ -464,7 +488,7 @@ class Server:
 
 def exported_symbols():
     """Names of the C functions this binding wraps."""
-    return ["skr_options_default", "skr_sort", "skr_sort_noalloc", "skr_solve_sequence", "skr_assemble", "skr_apply",
+    return ["skr_options_default", "skr_sort", "skr_sort_noalloc", "skr_sort_grouped", "skr_solve_sequence", "skr_assemble", "skr_apply",
             "skr_last_stats", "skr_last_profile", "skr_release_workspace", "skr_last_error",
             "skr_server_create", "skr_submit", "skr_poll", "skr_server_stats", "skr_server_destroy"]
 

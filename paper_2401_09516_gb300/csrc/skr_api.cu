@@ -193,6 +193,24 @@ thread_local LastStats g_last;
 
 }  // namespace
 
+namespace {
+
+// Sort the working positions by (set, split value, index): a bitonic
+// network over M = 2^e >= BITONIC_LOCAL keys, the steps with partner
+// distance below BITONIC_LOCAL in shared memory.
+cudaError_t bitonic_sort(GroupKey *keys, long long M, cudaStream_t st) {
+    const unsigned nb = (unsigned)(M / BITONIC_LOCAL);
+    bitonic_local_kernel<<<nb, BITONIC_LOCAL / 2, 0, st>>>(keys, 0);
+    for (long long k = 2 * BITONIC_LOCAL; k <= M; k <<= 1) {
+        for (long long j = k >> 1; j >= BITONIC_LOCAL; j >>= 1)
+            bitonic_global_kernel<<<grid_for(M / 2, 256), 256, 0, st>>>(keys, M, k, j);
+        bitonic_local_kernel<<<nb, BITONIC_LOCAL / 2, 0, st>>>(keys, k);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 extern "C" {
 
 skr_status skr_options_default(skr_options *opt) {
@@ -256,6 +274,155 @@ skr_status skr_sort(const double *params, int64_t N, int64_t p, int64_t start, i
     if (mem == SKR_MEM_HOST)
         CUDA_TRY(cudaMemcpyAsync(perm_out, perm, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    return SKR_OK;
+}
+
+skr_status skr_sort_grouped(const double *params, int64_t N, int64_t p, int64_t group_max, int32_t mem,
+                            void *stream, int32_t *perm_out, int64_t *group_offsets, int64_t *ngroups) {
+    g_err.clear();
+    if (N < 0) return fail(SKR_ERR_INVALID_ARG, "N < 0");
+    if (group_max < 1) return fail(SKR_ERR_INVALID_ARG, "group_max < 1");
+    if (mem != SKR_MEM_DEVICE && mem != SKR_MEM_HOST) return fail(SKR_ERR_INVALID_ARG, "bad mem");
+    if (N == 0) {
+        if (group_offsets) group_offsets[0] = 0;
+        if (ngroups) *ngroups = 0;
+        return SKR_OK;
+    }
+    if (!params || !perm_out) return fail(SKR_ERR_INVALID_ARG, "NULL pointer");
+    if (p < 1) return fail(SKR_ERR_INVALID_ARG, "p < 1");
+    if (N > (1LL << 30)) return fail(SKR_ERR_INVALID_ARG, "N too large");
+    if (p > 65535LL * SPREAD_THREADS) return fail(SKR_ERR_INVALID_ARG, "p too large");
+    cudaStream_t st = (cudaStream_t)stream;
+    DBuf dparams, dperm, derr, didx, dkeys;
+    const double *P = params;
+    if (mem == SKR_MEM_HOST) {
+        CUDA_TRY(dparams.alloc((size_t)N * p * 8));
+        CUDA_TRY(cudaMemcpyAsync(dparams.p, params, (size_t)N * p * 8, cudaMemcpyHostToDevice, st));
+        P = dparams.as<double>();
+    }
+    int *perm = perm_out;
+    if (mem == SKR_MEM_HOST) {
+        CUDA_TRY(dperm.alloc((size_t)N * 4));
+        perm = dperm.as<int>();
+    }
+    CUDA_TRY(derr.alloc(sizeof(int)));
+    CUDA_TRY(cudaMemsetAsync(derr.p, 0, sizeof(int), st));
+    finite_kernel<<<1024, 256, 0, st>>>(P, N * p, derr.as<int>());
+    CUDA_TRY(cudaGetLastError());
+    int herr = 0;
+    CUDA_TRY(cudaMemcpyAsync(&herr, derr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr) return fail(SKR_ERR_INVALID_ARG, "non-finite parameter");
+
+    long long M = BITONIC_LOCAL;
+    while (M < N) M <<= 1;
+    CUDA_TRY(didx.alloc((size_t)N * 4));
+    CUDA_TRY(dkeys.alloc((size_t)M * sizeof(GroupKey)));
+    iota_kernel<<<grid_for(N, 256), 256, 0, st>>>(didx.as<int>(), N);
+    CUDA_TRY(cudaGetLastError());
+    // bisection levels: the set offsets are known here, the members are not
+    std::vector<long long> off = {0, (long long)N};
+    const long long spread_cap = 1LL << 25;   // coordinates x sets per spread batch (2 x 256 MB of keys)
+    const long long batch_sets = std::max(1LL, spread_cap / p);
+    for (int final_pass = 0; final_pass < 2;) {
+        const int nn = (int)off.size() - 1;
+        std::vector<long long> soff, ssize, sslot;
+        if (!final_pass)
+            for (int q = 0; q < nn; q++)
+                if (off[q + 1] - off[q] > group_max) {
+                    soff.push_back(off[q]);
+                    ssize.push_back(off[q + 1] - off[q]);
+                    sslot.push_back(q);
+                }
+        if (!final_pass && soff.empty()) {
+            final_pass = 1;   // leaves only: one more sort puts each group in index order
+            continue;
+        }
+        DBuf dcoord, doff;
+        CUDA_TRY(dcoord.alloc((size_t)nn * 4));
+        CUDA_TRY(cudaMemsetAsync(dcoord.p, 0xff, (size_t)nn * 4, st));   // -1: not split
+        CUDA_TRY(doff.alloc((size_t)(nn + 1) * 8));
+        CUDA_TRY(cudaMemcpyAsync(doff.p, off.data(), (size_t)(nn + 1) * 8, cudaMemcpyHostToDevice, st));
+        for (size_t b0 = 0; b0 < soff.size(); b0 += (size_t)batch_sets) {
+            const long long nb = std::min((long long)(soff.size() - b0), batch_sets);
+            long long smax = 0;
+            for (long long q = 0; q < nb; q++) smax = std::max(smax, ssize[b0 + q]);
+            const long long cps = (smax + SPREAD_CHUNK - 1) / SPREAD_CHUNK;
+            if (nb * cps > 0x7fffffffLL) return fail(SKR_ERR_INVALID_ARG, "N too large");
+            DBuf dmn, dmx, dso, dss, dsl;
+            CUDA_TRY(dmn.alloc((size_t)nb * p * 8));
+            CUDA_TRY(dmx.alloc((size_t)nb * p * 8));
+            CUDA_TRY(dso.alloc((size_t)nb * 8));
+            CUDA_TRY(dss.alloc((size_t)nb * 8));
+            CUDA_TRY(dsl.alloc((size_t)nb * 8));
+            CUDA_TRY(cudaMemcpyAsync(dso.p, soff.data() + b0, (size_t)nb * 8, cudaMemcpyHostToDevice, st));
+            CUDA_TRY(cudaMemcpyAsync(dss.p, ssize.data() + b0, (size_t)nb * 8, cudaMemcpyHostToDevice, st));
+            CUDA_TRY(cudaMemcpyAsync(dsl.p, sslot.data() + b0, (size_t)nb * 8, cudaMemcpyHostToDevice, st));
+            spread_init_kernel<<<grid_for(nb * p, 256), 256, 0, st>>>(dmn.as<unsigned long long>(),
+                                                                     dmx.as<unsigned long long>(), nb * p);
+            const dim3 grid((unsigned)(nb * cps), (unsigned)((p + SPREAD_THREADS - 1) / SPREAD_THREADS));
+            spread_kernel<<<grid, SPREAD_THREADS, 0, st>>>(P, p, didx.as<int>(), dso.as<long long>(),
+                                                           dss.as<long long>(), cps, dmn.as<unsigned long long>(),
+                                                           dmx.as<unsigned long long>());
+            spread_argmax_kernel<<<(unsigned)nb, SPREAD_THREADS, 0, st>>>(
+                dmn.as<unsigned long long>(), dmx.as<unsigned long long>(), p, dsl.as<long long>(),
+                dcoord.as<int>());
+            CUDA_TRY(cudaGetLastError());
+            CUDA_TRY(cudaStreamSynchronize(st));   // the batch's buffers are freed on return
+        }
+        group_keys_kernel<<<grid_for(M, 256), 256, 0, st>>>(P, p, didx.as<int>(), N, M, doff.as<long long>(), nn,
+                                                          dcoord.as<int>(), dkeys.as<GroupKey>());
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(bitonic_sort(dkeys.as<GroupKey>(), M, st));
+        keys_to_idx_kernel<<<grid_for(N, 256), 256, 0, st>>>(dkeys.as<GroupKey>(), N, didx.as<int>());
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaStreamSynchronize(st));   // doff, dcoord are freed on return
+        if (final_pass) break;
+        std::vector<long long> next;
+        for (int q = 0; q < nn; q++) {
+            next.push_back(off[q]);
+            const long long sz = off[q + 1] - off[q];
+            if (sz > group_max) next.push_back(off[q] + sz / 2);
+        }
+        next.push_back(N);
+        off.swap(next);
+    }
+    // Algorithm 1 inside each group
+    const int ng = (int)off.size() - 1;
+    std::vector<long long> boff(ng + 1), doffs(ng + 1);
+    boff[0] = doffs[0] = 0;
+    for (int g = 0; g < ng; g++) {
+        const long long s = off[g + 1] - off[g], nt = (s + SORT_TILE - 1) / SORT_TILE;
+        boff[g + 1] = boff[g] + nt * (nt + 1) / 2;
+        doffs[g + 1] = doffs[g] + s * s;
+    }
+    if (boff[ng] > 0x7fffffffLL) return fail(SKR_ERR_INVALID_ARG, "groups too large for one launch");
+    DBuf dgoff, dboff, ddoff, ddist, dtaken;
+    CUDA_TRY(dgoff.alloc((size_t)(ng + 1) * 8));
+    CUDA_TRY(dboff.alloc((size_t)(ng + 1) * 8));
+    CUDA_TRY(ddoff.alloc((size_t)(ng + 1) * 8));
+    CUDA_TRY(ddist.alloc((size_t)doffs[ng] * 8));
+    CUDA_TRY(dtaken.alloc((size_t)N));
+    CUDA_TRY(cudaMemcpyAsync(dgoff.p, off.data(), (size_t)(ng + 1) * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(dboff.p, boff.data(), (size_t)(ng + 1) * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(ddoff.p, doffs.data(), (size_t)(ng + 1) * 8, cudaMemcpyHostToDevice, st));
+    group_dist_kernel<<<(unsigned)boff[ng], SORT_LANES, 0, st>>>(P, p, didx.as<int>(), dgoff.as<long long>(),
+                                                                 dboff.as<long long>(), ddoff.as<long long>(), ng,
+                                                                 ddist.as<double>(), derr.as<int>());
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(&herr, derr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr) return fail(SKR_ERR_INVALID_ARG, "non-finite parameter distance");
+    group_chain_kernel<<<(unsigned)ng, 256, 0, st>>>(ddist.as<double>(), ddoff.as<long long>(),
+                                                     dgoff.as<long long>(), didx.as<int>(), perm,
+                                                     dtaken.as<unsigned char>());
+    CUDA_TRY(cudaGetLastError());
+    if (mem == SKR_MEM_HOST)
+        CUDA_TRY(cudaMemcpyAsync(perm_out, perm, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (group_offsets)
+        for (int g = 0; g <= ng; g++) group_offsets[g] = off[g];
+    if (ngroups) *ngroups = ng;
     return SKR_OK;
 }
 

@@ -81,6 +81,69 @@ def test_sort_rejects_non_finite(skr):
         skr.skr_sort(_dev(P))
 
 
+# ------------------------------------------------------------------ large-N grouped sort
+
+@pytest.mark.parametrize("N,p,G,seed", [(300, 5, 16, 1), (3000, 4, 64, 2), (200, 700, 9, 3), (57, 1000, 57, 4),
+                                        (1, 10, 1, 5), (2, 3, 1, 6), (1500, 2, 1, 7), (1025, 3, 1000, 8)])
+def test_sort_grouped_bit_exact(skr, N, p, G, seed):
+    rng = np.random.default_rng(seed)
+    P = rng.standard_normal((N, p))
+    want, woffs = osort.grouped_sort(P, G)
+    perm, offs = skr.skr_sort_grouped(_dev(P), G)
+    assert perm.cpu().numpy().tolist() == want
+    assert offs.tolist() == woffs
+    perm_h, offs_h = skr.skr_sort_grouped(P, G)
+    assert perm_h.tolist() == want and offs_h.tolist() == woffs
+
+
+def test_sort_grouped_one_group_is_skr_sort(skr):
+    rng = np.random.default_rng(11)
+    P = rng.standard_normal((90, 300))
+    perm, offs = skr.skr_sort_grouped(_dev(P), 90)
+    assert perm.cpu().numpy().tolist() == skr.skr_sort(_dev(P)).cpu().numpy().tolist()
+    assert offs.tolist() == [0, 90]
+
+
+def test_sort_grouped_ties_duplicates_and_signed_zeros(skr):
+    rng = np.random.default_rng(12)
+    P = rng.integers(-2, 3, size=(400, 3)).astype(np.float64)   # equal coordinates and distances
+    P[17] = P[3]
+    P[::7, 1] = -0.0
+    P[1::7, 1] = 0.0
+    for G in (1, 5, 40):
+        want, woffs = osort.grouped_sort(P, G)
+        perm, offs = skr.skr_sort_grouped(_dev(P), G)
+        assert perm.cpu().numpy().tolist() == want and offs.tolist() == woffs
+
+
+def test_sort_grouped_darcy256_keys(skr):
+    L = darcy2d_sequence(256, 200, 0.1, seed=2)
+    P = L.reshape(200, -1)
+    want, woffs = osort.grouped_sort(P, 50)
+    perm, offs = skr.skr_sort_grouped(_dev(P), 50)
+    assert perm.cpu().numpy().tolist() == want and offs.tolist() == woffs
+
+
+def test_sort_grouped_large_n(skr):
+    # 20,000 systems with 16 smooth coordinates, groups of at most 1,000
+    rng = np.random.default_rng(13)
+    P = np.cumsum(rng.standard_normal((20000, 16)), axis=1)
+    want, woffs = osort.grouped_sort(P, 1000)
+    perm, offs = skr.skr_sort_grouped(_dev(P), 1000)
+    assert perm.cpu().numpy().tolist() == want and offs.tolist() == woffs
+
+
+def test_sort_grouped_rejects_bad_input(skr):
+    P = np.ones((6, 3))
+    with pytest.raises(skr.SkrError):
+        skr.skr_sort_grouped(_dev(P), 0)
+    P[4, 2] = np.inf
+    with pytest.raises(skr.SkrError):
+        skr.skr_sort_grouped(_dev(P), 2)
+    perm, offs = skr.skr_sort_grouped(np.zeros((0, 3)), 4)
+    assert len(perm) == 0 and offs.tolist() == [0]
+
+
 # ------------------------------------------------------------------ assembly and operator
 
 @pytest.mark.parametrize("nx,ny", [(2, 2), (13, 11), (64, 64)])

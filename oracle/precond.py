@@ -1,6 +1,6 @@
 """Preconditioners applied from the right (oracle).
 
-App. D.3 lists the preconditioners; this build uses four of them:
+App. D.3 lists the preconditioners; this build uses five of them:
   * none:   M = I
   * jacobi: M = diag(A) ("the inverse of the diagonal elements")
   * ssor:   symmetric SOR with omega = 1 (App. D.3's SOR, as PETSc applies it
@@ -8,6 +8,16 @@ App. D.3 lists the preconditioners; this build uses four of them:
             with A = L + D + U
   * ilu0:   M = L U, the incomplete LU factorisation with no fill, i.e. L
             and U keep exactly the sparsity pattern of A (App. D.3 item 7).
+  * bjacobi: block Jacobi (App. D.3 item 3): M = blockdiag(M_1, ..., M_B)
+            over B contiguous row blocks of ceil(n / B) rows (the last one
+            ragged), M_b the ILU(0) below of the diagonal block A[b, b].
+
+Reading for block Jacobi: the paper says only that each block is
+preconditioned independently from its diagonal part; its runs are PETSc's,
+whose default is one block per process of the row distribution and ILU(0)
+on each block, and its Darcy block-Jacobi table is for 72 processes.  So
+the blocks are contiguous row ranges, B is a parameter, and each block is
+factored by the red-black ILU(0) below (red and black as in the whole grid).
 
 Reading for SSOR: omega = 1 (not stated) and the same red-black ordering
 as ILU(0) below, so that both sweeps are parallel over one colour each.
@@ -111,19 +121,56 @@ def ssor_redblack(A, grid):
     return perm, Lp, Up
 
 
-class RightPreconditioner:
-    """M^-1 as an operator, for M in {none, jacobi, ssor, ilu0}.
+def block_ranges(n, blocks):
+    """The B contiguous row blocks of block Jacobi: ceil(n / B) rows each, the last ragged."""
+    bs = -(-n // blocks)
+    return [(lo, min(lo + bs, n)) for lo in range(0, n, bs)]
 
-    ssor and ilu0 need the grid shape (red-black ordering, see the module
-    readings).
+
+class BlockILU0:
+    """Block Jacobi with red-black ILU(0) on every diagonal block."""
+
+    def __init__(self, A, grid, blocks):
+        A = sp.csr_matrix(A)
+        n = A.shape[0]
+        coords = np.indices(grid).reshape(len(grid), -1)
+        color = coords.sum(axis=0) % 2
+        self.parts = []
+        for lo, hi in block_ranges(n, blocks):
+            rows = np.arange(lo, hi)
+            perm = np.concatenate([rows[color[rows] == 0], rows[color[rows] == 1]])
+            Ab = A[perm][:, perm]
+            L, U = ilu0(Ab)
+            self.parts.append((perm, L, U))
+
+    def solve(self, v):
+        v = np.asarray(v, dtype=np.float64)
+        out = np.empty_like(v)
+        for perm, L, U in self.parts:
+            y = spla.spsolve_triangular(L, v[perm], lower=True, unit_diagonal=True)
+            out[perm] = spla.spsolve_triangular(U, y, lower=False)
+        return out
+
+
+class RightPreconditioner:
+    """M^-1 as an operator, for M in {none, jacobi, ssor, ilu0, bjacobi}.
+
+    ssor, ilu0 and bjacobi need the grid shape (red-black ordering, see the
+    module readings); blocks is block Jacobi's block count.
     """
 
-    def __init__(self, A, kind, grid=None):
+    def __init__(self, A, kind, grid=None, blocks=1):
         self.kind = kind
         if kind == "none":
             pass
         elif kind == "jacobi":
             self.dinv = jacobi_inv_diag(A)
+        elif kind == "bjacobi":
+            if grid is None:
+                raise ValueError(kind + " needs the grid shape")
+            if blocks < 1:
+                raise ValueError("blocks < 1")
+            self.block = BlockILU0(A, grid, blocks)
         elif kind in ("ilu0", "ssor"):
             if grid is None:
                 raise ValueError(kind + " needs the grid shape")
@@ -136,6 +183,8 @@ class RightPreconditioner:
             return np.array(v, dtype=np.float64, copy=True)
         if self.kind == "jacobi":
             return self.dinv * v
+        if self.kind == "bjacobi":
+            return self.block.solve(v)
         vp = np.asarray(v, dtype=np.float64)[self.perm]
         y = spla.spsolve_triangular(self.L, vp, lower=True, unit_diagonal=True)
         z = spla.spsolve_triangular(self.U, y, lower=False)

@@ -56,16 +56,17 @@ def assemble(system):
 
 
 def solve_system(A, b, precond, m, k, tol, state, precision="fp64", inner_tol=1e-5,
-                 max_refine=10, max_steps=10**4, grid=None, x0=None):
+                 max_refine=10, max_steps=10**4, grid=None, x0=None, pc_blocks=1):
     """Solve one system, updating the carried recycle state in place.
 
-    x0 is Algorithm 2's initial guess (default 0).
+    x0 is Algorithm 2's initial guess (default 0); pc_blocks is block
+    Jacobi's block count.
 
     Returns (x, info) with info = dict(steps, cycles, matvecs, refinements,
     relres, converged).  `steps` counts Arnoldi steps (one operator
     application each); `matvecs` also counts the k products of the refresh.
     """
-    M = RightPreconditioner(A, precond, grid)
+    M = RightPreconditioner(A, precond, grid, blocks=pc_blocks)
 
     def op(v):
         return A @ M.apply(v)
@@ -108,7 +109,7 @@ def split_chains(order, nchains):
 
 
 def solve_sequence(systems, order, precond, m, k, tol, precision="fp64", nchains=1,
-                   inner_tol=1e-5, max_refine=10, max_steps=10**4, warm_start=False):
+                   inner_tol=1e-5, max_refine=10, max_steps=10**4, warm_start=False, pc_blocks=1):
     """Solve systems[order[0]], systems[order[1]], ... carrying U_k along each chain.
 
     warm_start: x0 of a system is the previous solution of its chain (the
@@ -124,7 +125,7 @@ def solve_sequence(systems, order, precond, m, k, tol, precision="fp64", nchains
             A, b = assemble(systems[idx])
             x, info = solve_system(A, b, precond, m, k, tol, state, precision, inner_tol,
                                    max_refine, max_steps, grid=grid_of(systems[idx]),
-                                   x0=prev if warm_start else None)
+                                   x0=prev if warm_start else None, pc_blocks=pc_blocks)
             xs[idx] = x
             infos[idx] = info
             prev = x

@@ -396,3 +396,65 @@ def test_redblack_ssor_closed_form(grid):
     Dr = np.diag(Ap)[:nr]
     want_bb = np.diag(np.diag(Ap)[nr:]) + Ap[nr:, :nr] @ np.diag(1.0 / Dr) @ Ap[:nr, nr:]
     np.testing.assert_allclose(M[nr:, nr:], want_bb, rtol=1e-13, atol=1e-13 * np.abs(Ap).max())
+
+
+# ---------------------------------------------------------------- block Jacobi (App. D.3 item 3)
+
+def _grid_matrix(grid, seed):
+    rng = np.random.default_rng(seed)
+    if len(grid) == 2:
+        return assembly.darcy2d(rng.standard_normal((grid[0] + 2, grid[1] + 2)))[0]
+    return assembly.darcy3d(rng.standard_normal(tuple(g + 2 for g in grid)))[0]
+
+
+def test_block_ranges_are_contiguous_with_a_ragged_last_block():
+    assert precond.block_ranges(30, 4) == [(0, 8), (8, 16), (16, 24), (24, 30)]
+    assert precond.block_ranges(7, 1) == [(0, 7)]
+    assert precond.block_ranges(5, 5) == [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5)]
+
+
+def test_bjacobi_one_block_is_ilu0_and_unit_blocks_are_jacobi():
+    grid = (6, 5)
+    A = _grid_matrix(grid, 1)
+    v = np.random.default_rng(2).standard_normal(30)
+    one = precond.RightPreconditioner(A, "bjacobi", grid, blocks=1).apply(v)
+    np.testing.assert_array_equal(one, precond.RightPreconditioner(A, "ilu0", grid).apply(v))
+    unit = precond.RightPreconditioner(A, "bjacobi", grid, blocks=30).apply(v)
+    np.testing.assert_allclose(unit, v / A.diagonal(), rtol=1e-15)
+
+
+@pytest.mark.parametrize("grid,blocks", [((6, 5), 4), ((7, 7), 3), ((4, 3, 5), 5)])
+def test_bjacobi_closed_form(grid, blocks):
+    # M is block diagonal over the row blocks; inside a block it is the
+    # red-black ILU(0) of the block alone: M_rr = a_rr, M_rb = a_rb and
+    # M_br = a_br for r, b in the block, and on the black rows
+    # M_bb = a_bb and, for b != b', M_bb' = sum over the block's reds r of
+    # a_br a_rb' / a_rr (the fill that ILU(0) drops from U)
+    A = _grid_matrix(grid, 3)
+    Ad = A.toarray()
+    n = Ad.shape[0]
+    Mop = precond.RightPreconditioner(A, "bjacobi", grid, blocks=blocks)
+    M = np.linalg.inv(np.stack([Mop.apply(e) for e in np.eye(n)], axis=1))
+    color = np.indices(grid).reshape(len(grid), -1).sum(axis=0) % 2
+    want = np.zeros((n, n))
+    for lo, hi in precond.block_ranges(n, blocks):
+        for i in range(lo, hi):
+            for j in range(lo, hi):
+                if color[i] == 0 or color[j] == 0:
+                    want[i, j] = Ad[i, j]
+                else:
+                    want[i, j] = Ad[i, i] if i == j else sum(
+                        Ad[i, r] * Ad[r, j] / Ad[r, r] for r in range(lo, hi) if color[r] == 0)
+    np.testing.assert_allclose(M, want, rtol=1e-10, atol=1e-10 * np.abs(Ad).max())
+    assert blocks > 1 and np.abs(want - Ad * (want != 0)).max() > 0   # not plain A
+
+
+def test_bjacobi_gcrodr_converges_on_darcy():
+    A, b = _darcy(12, seed=4)
+    st = krylov.RecycleState()
+    x, info = skr.solve_system(A, b, "bjacobi", 20, 6, 1e-10, st, grid=(12, 12), pc_blocks=5)
+    assert info["converged"] and np.linalg.norm(b - A @ x) <= 1e-10 * np.linalg.norm(b)
+    _, info1 = skr.solve_system(A, b, "ilu0", 20, 6, 1e-10, krylov.RecycleState(), grid=(12, 12))
+    _, infoj = skr.solve_system(A, b, "jacobi", 20, 6, 1e-10, krylov.RecycleState(), grid=(12, 12))
+    # between ILU(0) (one block) and Jacobi (one row per block) in strength
+    assert info1["steps"] <= info["steps"] <= infoj["steps"]

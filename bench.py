@@ -54,14 +54,20 @@ WORKLOADS = {
 }
 
 
-PRECOND_NAMES = {"none": "no preconditioner", "jacobi": "Jacobi", "ssor": "SSOR", "ilu0": "red-black ILU(0)"}
+PRECOND_NAMES = {"none": "no preconditioner", "jacobi": "Jacobi", "ssor": "SSOR", "ilu0": "red-black ILU(0)",
+                 "bjacobi": "block Jacobi"}
 
 
 def _workload(args):
     """The named workload, with the preconditioner overridden if asked."""
     W = dict(WORKLOADS[args.workload])
+    W["pc_blocks"] = 1
     if args.precond and args.precond != W["precond"]:
-        W["desc"] = W["desc"].replace(PRECOND_NAMES[W["precond"]], PRECOND_NAMES[args.precond])
+        name = PRECOND_NAMES[args.precond]
+        if args.precond == "bjacobi":
+            W["pc_blocks"] = args.pc_blocks
+            name = "block Jacobi (%d row blocks, red-black ILU(0) each)" % args.pc_blocks
+        W["desc"] = W["desc"].replace(PRECOND_NAMES[W["precond"]], name)
         W["precond"] = args.precond
     return W
 
@@ -230,7 +236,7 @@ def run_gpu(args):
 
     def opts(k):
         return skr.skr_options_default(m=W["m"], k=k, tol=W["tol"], inner_tol=W["inner_tol"],
-                                       precond=W["precond"], precision=W["precision"],
+                                       precond=W["precond"], pc_blocks=W["pc_blocks"], precision=W["precision"],
                                        cluster_size=args.cluster_size, stream=stream,
                                        warm_start=int(args.warm_start), diagnostics=int(args.diagnostics))
 
@@ -411,10 +417,12 @@ def _oracle_worker(conn, W, fields, warm):
         while True:
             if pos == len(fields):
                 state, pos, prev = RecycleState(), 0, None
-            A, b = oskr.assemble(_oracle_system(W, fields[pos]))
+            sysd = _oracle_system(W, fields[pos])
+            A, b = oskr.assemble(sysd)
             x, _ = oskr.solve_system(A, b, W["precond"], W["m"], W["k"], W["tol"], state,
                                      precision="mixed", inner_tol=W["inner_tol"],
-                                     x0=prev if warm else None)
+                                     x0=prev if warm else None, grid=oskr.grid_of(sysd),
+                                     pc_blocks=W["pc_blocks"])
             prev = x
             pos += 1
             done += 1
@@ -607,6 +615,8 @@ def main():
     ap.add_argument("--no-sort", action="store_true", help="solve in input order (ablation)")
     ap.add_argument("--precond", default=None, choices=sorted(PRECOND_NAMES),
                     help="override the workload's preconditioner")
+    ap.add_argument("--pc-blocks", type=int, default=72,
+                    help="row blocks of --precond bjacobi (72: the paper's Darcy runs, one per process)")
     ap.add_argument("--diagnostics", action="store_true", help="report the mean one-sided distance delta")
     ap.add_argument("--chains", type=int, default=76, help="independent chains the sorted order is cut into")
     ap.add_argument("--cluster-size", type=int, default=2, help="CTAs per chain (thread-block cluster)")

@@ -84,6 +84,12 @@ typedef int32_t skr_status;
                                      applied as the same two parallel colour sweeps as SKR_PC_ILU0 */
 #define SKR_PC_ILU0           2   /* M = L U, ILU(0) of A in red-black order (no fill; both
                                      triangular solves are two parallel colour sweeps) */
+#define SKR_PC_BJACOBI        4   /* block Jacobi (App. D.3): the rows are cut into pc_blocks
+                                     contiguous blocks of ceil(n / pc_blocks) rows (the last one
+                                     ragged), one per process of a row-distributed matrix, and each
+                                     diagonal block is factored by ILU(0) in red-black order, as
+                                     SKR_PC_ILU0 (PETSc's default sub-preconditioner); couplings
+                                     between blocks are left out of M.  pc_blocks = 1 is SKR_PC_ILU0 */
 
 /* precision form */
 #define SKR_PREC_FP64         0   /* all vectors and reductions in FP64 */
@@ -125,6 +131,7 @@ typedef struct skr_options {
                                its chain (Algorithm 2 leaves x_0 free); the first system of a chain,
                                and every system when zero (default), starts from x_0 = 0 */
     int32_t diagnostics;    /* nonzero: report skr_result.delta (one extra Gram pass per system) */
+    int32_t pc_blocks;      /* SKR_PC_BJACOBI: number of row blocks, >= 1 (default 1) */
 } skr_options;
 
 typedef struct skr_result {
@@ -267,9 +274,10 @@ skr_status skr_assemble(const skr_system *sys, int32_t mem, void *stream,
  * skr_apply -- y = A M^-1 v for one system, in the working precision of
  * `precision` (SKR_PREC_MIXED: FP32 arithmetic, v rounded to FP32 on
  * input and y widened to FP64 on output), using the solver's own operator
- * code.  v, y: n doubles each, memory per mem.
+ * code.  v, y: n doubles each, memory per mem.  pc_blocks: the block count
+ * of SKR_PC_BJACOBI (>= 1; ignored by the other preconditioners).
  */
-skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t precision,
+skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t pc_blocks, int32_t precision,
                      const double *v, double *y, int32_t mem, void *stream);
 
 /* ------------------------------------------------------------------ serving

@@ -38,6 +38,7 @@ SKR_PC_NONE = 0
 SKR_PC_JACOBI = 1
 SKR_PC_ILU0 = 2
 SKR_PC_SSOR = 3
+SKR_PC_BJACOBI = 4
 SKR_PREC_FP64 = 0
 SKR_PREC_MIXED = 1
 SKR_MEM_DEVICE = 0
@@ -45,7 +46,8 @@ SKR_MEM_HOST = 1
 SKR_MAX_M = 48
 SKR_MAX_K = 24
 
-PRECOND = {"none": SKR_PC_NONE, "jacobi": SKR_PC_JACOBI, "ilu0": SKR_PC_ILU0, "ssor": SKR_PC_SSOR}
+PRECOND = {"none": SKR_PC_NONE, "jacobi": SKR_PC_JACOBI, "ilu0": SKR_PC_ILU0, "ssor": SKR_PC_SSOR,
+           "bjacobi": SKR_PC_BJACOBI}
 PRECISION = {"fp64": SKR_PREC_FP64, "mixed": SKR_PREC_MIXED}
 
 
@@ -62,7 +64,8 @@ class SkrOptions(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
                 ("max_slots", ctypes.c_int32), ("mem", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("warm_start", ctypes.c_int32), ("diagnostics", ctypes.c_int32)]
+                ("warm_start", ctypes.c_int32), ("diagnostics", ctypes.c_int32),
+                ("pc_blocks", ctypes.c_int32)]
 
 
 class SkrResult(ctypes.Structure):
@@ -101,7 +104,7 @@ _lib.skr_solve_sequence.argtypes = [ctypes.POINTER(SkrSystem), _i64, _vp, _vp, _
                                     ctypes.POINTER(SkrOptions), ctypes.POINTER(_vp),
                                     ctypes.POINTER(SkrResult)]
 _lib.skr_assemble.argtypes = [ctypes.POINTER(SkrSystem), _i32, _vp, _vp, _vp]
-_lib.skr_apply.argtypes = [ctypes.POINTER(SkrSystem), _i32, _i32, _vp, _vp, _i32, _vp]
+_lib.skr_apply.argtypes = [ctypes.POINTER(SkrSystem), _i32, _i32, _i32, _vp, _vp, _i32, _vp]
 _lib.skr_last_stats.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
 _lib.skr_last_profile.argtypes = [ctypes.POINTER(ctypes.c_double), _i32]
@@ -359,8 +362,8 @@ def skr_assemble(system, stream=None):
     return coef, rhs
 
 
-def skr_apply(system, v, precond="none", precision="fp64", stream=None):
-    """y = A M^-1 v with the solver's operator code."""
+def skr_apply(system, v, precond="none", precision="fp64", stream=None, pc_blocks=1):
+    """y = A M^-1 v with the solver's operator code (pc_blocks: block-Jacobi's block count)."""
     v = _f64(v)
     mem = _mem_of(v, *system.arrays())
     if mem == SKR_MEM_DEVICE:
@@ -369,7 +372,7 @@ def skr_apply(system, v, precond="none", precision="fp64", stream=None):
     else:
         y = np.empty_like(v)
     s = system.struct()
-    _check(_lib.skr_apply(ctypes.byref(s), PRECOND.get(precond, precond),
+    _check(_lib.skr_apply(ctypes.byref(s), PRECOND.get(precond, precond), int(pc_blocks),
                           PRECISION.get(precision, precision), _ptr(v), _ptr(y), mem,
                           _stream_handle(stream)))
     return y

@@ -228,6 +228,7 @@ skr_status skr_options_default(skr_options *opt) {
     opt->max_slots = 0;
     opt->mem = SKR_MEM_DEVICE;
     opt->stream = nullptr;
+    opt->pc_blocks = 1;
     return SKR_OK;
 }
 
@@ -455,14 +456,16 @@ skr_status skr_assemble(const skr_system *sys, int32_t mem, void *stream, double
     return SKR_OK;
 }
 
-skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t precision, const double *v, double *y,
-                     int32_t mem, void *stream) {
+skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t pc_blocks, int32_t precision,
+                     const double *v, double *y, int32_t mem, void *stream) {
     g_err.clear();
     if (!sys || !v || !y) return fail(SKR_ERR_INVALID_ARG, "NULL pointer");
     skr_status s0 = check_system(*sys, 0);
     if (s0 != SKR_OK) return s0;
-    if (precond != SKR_PC_NONE && precond != SKR_PC_JACOBI && precond != SKR_PC_ILU0 && precond != SKR_PC_SSOR)
+    if (precond != SKR_PC_NONE && precond != SKR_PC_JACOBI && precond != SKR_PC_ILU0 && precond != SKR_PC_SSOR &&
+        precond != SKR_PC_BJACOBI)
         return fail(SKR_ERR_INVALID_ARG, "unknown preconditioner %d", precond);
+    if (precond == SKR_PC_BJACOBI && pc_blocks < 1) return fail(SKR_ERR_INVALID_ARG, "pc_blocks < 1");
     if (precision != SKR_PREC_FP64 && precision != SKR_PREC_MIXED)
         return fail(SKR_ERR_INVALID_ARG, "bad precision");
     cudaStream_t st = (cudaStream_t)stream;
@@ -480,7 +483,7 @@ skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t precision, 
     CUDA_TRY(A.alloc((size_t)g.nst * g.n * 8));
     CUDA_TRY(dinv.alloc((size_t)g.n * 8));
     rows_kernel<<<grid_for(g.n, 256), 256, 0, st>>>(sg.dev, g, anode.as<double>(), A.as<double>(), g.n, nullptr,
-                                                     dinv.as<double>(), (precond == SKR_PC_ILU0 || precond == SKR_PC_SSOR) ? SKR_PC_NONE : precond);
+                                                     dinv.as<double>(), colour_sweep_pc(precond) ? SKR_PC_NONE : precond);
     CUDA_TRY(cudaGetLastError());
     const double *vin = v;
     double *yout = y;
@@ -492,10 +495,11 @@ skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t precision, 
         yout = dy.as<double>();
     }
     const int gb = grid_for(g.n, 256);
-    if (precond == SKR_PC_ILU0 || precond == SKR_PC_SSOR) {
+    if (colour_sweep_pc(precond)) {
         DBuf inv, invw, zb;
+        const long long bs = sweep_block_rows(precond, g.n, pc_blocks);
         CUDA_TRY(inv.alloc((size_t)g.n * 8));
-        ilu_pivot_kernel<<<gb, 256, 0, st>>>(g, A.as<double>(), g.n, inv.as<double>(), precond);
+        ilu_pivot_kernel<<<gb, 256, 0, st>>>(g, A.as<double>(), g.n, inv.as<double>(), precond, bs);
         const size_t es = (precision == SKR_PREC_MIXED) ? 4 : 8;
         CUDA_TRY(Aw.alloc((size_t)g.nst * g.n * es));
         CUDA_TRY(invw.alloc((size_t)g.n * es));
@@ -506,13 +510,13 @@ skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t precision, 
             to_working_kernel<float><<<gb, 256, 0, st>>>(vin, g.n, vw.as<float>());
             for (int stage = 1; stage <= 3; stage++)
                 ilu_sweep_kernel<float><<<gb, 256, 0, st>>>(g, Aw.as<float>(), g.n, invw.as<float>(), vw.as<float>(),
-                                                            zb.as<float>(), yout, stage);
+                                                            zb.as<float>(), yout, stage, bs);
         } else {
             ilu_fold_kernel<double><<<gb, 256, 0, st>>>(g, A.as<double>(), g.n, inv.as<double>(), Aw.as<double>(), invw.as<double>());
             to_working_kernel<double><<<gb, 256, 0, st>>>(vin, g.n, vw.as<double>());
             for (int stage = 1; stage <= 3; stage++)
                 ilu_sweep_kernel<double><<<gb, 256, 0, st>>>(g, Aw.as<double>(), g.n, invw.as<double>(), vw.as<double>(),
-                                                             zb.as<double>(), yout, stage);
+                                                             zb.as<double>(), yout, stage, bs);
         }
         CUDA_TRY(cudaGetLastError());
     } else if (precision == SKR_PREC_MIXED) {
@@ -555,8 +559,9 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     if (opt.precision == SKR_PREC_MIXED && !(opt.inner_tol > 0.0 && opt.inner_tol < 1.0))
         return fail(SKR_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
     if (opt.precond != SKR_PC_NONE && opt.precond != SKR_PC_JACOBI && opt.precond != SKR_PC_ILU0 &&
-        opt.precond != SKR_PC_SSOR)
+        opt.precond != SKR_PC_SSOR && opt.precond != SKR_PC_BJACOBI)
         return fail(SKR_ERR_INVALID_ARG, "unknown preconditioner %d", opt.precond);
+    if (opt.precond == SKR_PC_BJACOBI && opt.pc_blocks < 1) return fail(SKR_ERR_INVALID_ARG, "pc_blocks < 1");
     if (opt.precision != SKR_PREC_FP64 && opt.precision != SKR_PREC_MIXED)
         return fail(SKR_ERR_INVALID_ARG, "bad precision");
     if (opt.mem != SKR_MEM_DEVICE && opt.mem != SKR_MEM_HOST) return fail(SKR_ERR_INVALID_ARG, "bad mem");
@@ -667,6 +672,7 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     a.maxit = opt.maxit;
     a.max_refine = opt.max_refine;
     a.precond = opt.precond;
+    a.pc_blocks = opt.pc_blocks;
     a.tol = opt.tol;
     a.inner_tol = opt.inner_tol;
     a.bytes = reinterpret_cast<unsigned long long *>(dctr.as<char>() + 32);

@@ -199,7 +199,8 @@ struct Ctx {
     T *Aw;
     double *dinv, *x, *r, *b, *anode;
     // parameters
-    int m, k, maxit, precond;
+    int m, k, maxit, precond, pc_blocks;
+    long long pc_bs;   // rows per block of the colour sweeps (n unless block-Jacobi)
     // shared memory
     SmemPlan P;
     double *sm;
@@ -675,10 +676,15 @@ __device__ void ilu_spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
     const T *inv = c.Aw + (long long)7 * c.ld;
     T *z = c.col(COL_Z);
     const long long hi = c.lo + c.cnt;
+    const bool blocks = c.pc_bs < c.g.n;
     for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
         if (p < c.g.n) {
             if (vout) vout[p] = s * __ldcg(src + p);
-            if (grid_color(c.g, p) == 1) z[p] = ilu_sweep1_row<T, T>(c.g, c.Aw, c.ld, inv, src, s, p);
+            if (grid_color(c.g, p) == 1) {
+                long long blo, bhi;
+                pc_block(p, c.pc_bs, c.g.n, blo, bhi);
+                z[p] = ilu_sweep1_row<T, T>(c.g, c.Aw, c.ld, inv, src, s, p, blo, bhi);
+            }
         } else {
             if (vout) vout[p] = T(0);
             z[p] = T(0);
@@ -688,8 +694,13 @@ __device__ void ilu_spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
     cl_sync();
     for (long long p = c.lo + threadIdx.x; p < hi && p < c.g.n; p += blockDim.x) {
         if (grid_color(c.g, p) == 0) {
-            z[p] = ilu_sweep2_row<T, T>(c.g, c.Aw, c.ld, inv, src, s, z, p);
-            y[p] = s * __ldcg(src + p);
+            long long blo, bhi;
+            pc_block(p, c.pc_bs, c.g.n, blo, bhi);
+            z[p] = ilu_sweep2_row<T, T>(c.g, c.Aw, c.ld, inv, src, s, z, p, blo, bhi);
+            // block-Jacobi leaves the couplings to other blocks out of M, so
+            // the red rows of A M^-1 keep them
+            const T v = s * __ldcg(src + p);
+            y[p] = blocks ? v + ilu_red_cross_row(c.g, c.Aw, c.ld, z, p, blo, bhi) : v;
         }
     }
     cl_sync();
@@ -789,7 +800,7 @@ __device__ __noinline__ void assemble_system(Ctx<T> &c, const DevSystem &sys) {
         T *inv = c.Aw + (long long)7 * c.ld;
         for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
             if (p < c.g.n) {
-                const double ip = sweep_inv_pivot(c.g, c.A64, c.ld, p, c.precond);
+                const double ip = sweep_inv_pivot(c.g, c.A64, c.ld, p, c.precond, c.pc_bs);
                 c.dinv[p] = ip;
                 inv[p] = (T)ip;
                 for (int s = 0; s < c.g.nst; s++) c.Aw[(long long)s * c.ld + p] = (T)c.A64[(long long)s * c.ld + p];
@@ -1406,6 +1417,7 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx, bool war
     const DevSystem sys = a.systems[sysidx];
     const unsigned long long t0 = global_ns();
     c.g = make_geom(sys.fmt, sys.nx, sys.ny, sys.nz);
+    c.pc_bs = sweep_block_rows(c.precond, c.g.n, c.pc_blocks);
     const long long chunk = (((c.g.n + c.cs - 1) / c.cs) + 7) / 8 * 8;
     c.lo = (long long)c.rank * chunk;
     c.cnt = chunk;
@@ -1490,12 +1502,18 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx, bool war
         if (colour_sweep_pc(c.precond)) {
             cl_sync();   // d of the neighbours
             for (long long p = c.lo + threadIdx.x; p < hi && p < c.g.n; p += blockDim.x)
-                if (grid_color(c.g, p) == 1)
-                    c.r[p] = ilu_sweep1_row<double, T>(c.g, c.A64, c.ld, c.dinv, dh, 1.0, p);
+                if (grid_color(c.g, p) == 1) {
+                    long long blo, bhi;
+                    pc_block(p, c.pc_bs, c.g.n, blo, bhi);
+                    c.r[p] = ilu_sweep1_row<double, T>(c.g, c.A64, c.ld, c.dinv, dh, 1.0, p, blo, bhi);
+                }
             cl_sync();
             for (long long p = c.lo + threadIdx.x; p < hi && p < c.g.n; p += blockDim.x)
-                if (grid_color(c.g, p) == 0)
-                    c.r[p] = ilu_sweep2_row<double, T>(c.g, c.A64, c.ld, c.dinv, dh, 1.0, c.r, p);
+                if (grid_color(c.g, p) == 0) {
+                    long long blo, bhi;
+                    pc_block(p, c.pc_bs, c.g.n, blo, bhi);
+                    c.r[p] = ilu_sweep2_row<double, T>(c.g, c.A64, c.ld, c.dinv, dh, 1.0, c.r, p, blo, bhi);
+                }
             __syncthreads();
             for (long long p = c.lo + threadIdx.x; p < hi && p < c.g.n; p += blockDim.x) c.x[p] += c.r[p];
         } else {
@@ -1546,6 +1564,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS, CHAIN_MIN_BLOCKS) chain_kernel(
     c.k = a.k;
     c.maxit = a.maxit;
     c.precond = a.precond;
+    c.pc_blocks = a.pc_blocks;
     c.ld = a.ws.ld;
     c.basis = reinterpret_cast<T *>(a.ws.basis) + (long long)slot * NCOLS * c.ld;
     c.A64 = a.ws.A64 + (long long)slot * 7 * c.ld;

@@ -87,6 +87,7 @@ struct ChainArgs {
     unsigned long long *prof;     // SKR_NPHASE per-phase ns accumulators (optional)
     int warm_start;               // x_0 = previous solution of the chain
     int diagnostics;              // nonzero: compute delta per system
+    int pc_blocks;                // SKR_PC_BJACOBI: row blocks of the preconditioner
     int *chain_xok;               // per chain, optional: nonzero when the slot's x holds the
                                   // previous solution (read at chain start, set at chain end)
     int *chain_kc;                // per-chain recycle dimension carried between launches

@@ -53,10 +53,10 @@ __global__ void apply_kernel(Geom g, const T *Aw, long long ld, const T *v, doub
 }
 
 // red-black ILU(0) / SSOR for the stand-alone operator entry point
-__global__ void ilu_pivot_kernel(Geom g, const double *A, long long ld, double *inv, int pc) {
+__global__ void ilu_pivot_kernel(Geom g, const double *A, long long ld, double *inv, int pc, long long bs) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n;
          p += (long long)gridDim.x * blockDim.x)
-        inv[p] = sweep_inv_pivot(g, A, ld, p, pc);
+        inv[p] = sweep_inv_pivot(g, A, ld, p, pc, bs);
 }
 
 template <typename T>
@@ -68,18 +68,23 @@ __global__ void ilu_fold_kernel(Geom g, const double *A, long long ld, const dou
     }
 }
 
+// bs: rows per block of the sweeps (n, or ceil(n / blocks) for block-Jacobi)
 template <typename T>
 __global__ void ilu_sweep_kernel(Geom g, const T *Aw, long long ld, const T *inv, const T *v, T *z, double *y,
-                                 int stage) {
+                                 int stage, long long bs) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n;
          p += (long long)gridDim.x * blockDim.x) {
         const int col = grid_color(g, p);
-        if (stage == 1 && col == 1) z[p] = ilu_sweep1_row<T, T>(g, Aw, ld, inv, v, T(1), p);
-        if (stage == 2 && col == 0) {
-            z[p] = ilu_sweep2_row<T, T>(g, Aw, ld, inv, v, T(1), z, p);
-            y[p] = (double)v[p];
+        long long lo, hi;
+        pc_block(p, bs, g.n, lo, hi);
+        if (stage == 1 && col == 1) z[p] = ilu_sweep1_row<T, T>(g, Aw, ld, inv, v, T(1), p, lo, hi);
+        if (stage == 2 && col == 0) z[p] = ilu_sweep2_row<T, T>(g, Aw, ld, inv, v, T(1), z, p, lo, hi);
+        if (stage == 3) {
+            if (col == 1)
+                y[p] = (double)ilu_black_apply_row(g, Aw, ld, z, p);
+            else
+                y[p] = (double)(v[p] + ilu_red_cross_row(g, Aw, ld, z, p, lo, hi));
         }
-        if (stage == 3 && col == 1) y[p] = (double)ilu_black_apply_row(g, Aw, ld, z, p);
     }
 }
 

@@ -246,6 +246,7 @@ bool launch(skr_server *S, Chain *c, Request *r) {
     a.maxit = S->opt.maxit;
     a.max_refine = S->opt.max_refine;
     a.precond = S->opt.precond;
+    a.pc_blocks = S->opt.pc_blocks;
     a.tol = S->opt.tol;
     a.inner_tol = S->opt.inner_tol;
     a.bytes = c->dbytes;
@@ -395,8 +396,9 @@ skr_status skr_server_create(const skr_options *opt_in, size_t hbm_budget, int32
     if (opt.precision == SKR_PREC_MIXED && !(opt.inner_tol > 0.0 && opt.inner_tol < 1.0))
         return err(SKR_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
     if (opt.precond != SKR_PC_NONE && opt.precond != SKR_PC_JACOBI && opt.precond != SKR_PC_ILU0 &&
-        opt.precond != SKR_PC_SSOR)
+        opt.precond != SKR_PC_SSOR && opt.precond != SKR_PC_BJACOBI)
         return err(SKR_ERR_INVALID_ARG, "unknown preconditioner");
+    if (opt.precond == SKR_PC_BJACOBI && opt.pc_blocks < 1) return err(SKR_ERR_INVALID_ARG, "pc_blocks < 1");
     if ((opt.warm_start != 0 && opt.warm_start != 1) || (opt.diagnostics != 0 && opt.diagnostics != 1))
         return err(SKR_ERR_INVALID_ARG, "warm_start and diagnostics must be 0 or 1");
     if (opt.precision != SKR_PREC_FP64 && opt.precision != SKR_PREC_MIXED) return err(SKR_ERR_INVALID_ARG, "bad precision");

@@ -246,8 +246,20 @@ __device__ __forceinline__ int grid_color(const Geom &g, long long p) {
 // slot of the coefficient that couples the neighbour back to p
 __device__ __forceinline__ int opposite_slot(int s) { return (s & 1) ? s + 1 : s - 1; }
 
-// 1 / pivot of row p: 1/a_pp (red) or 1/d_p (black).  A: FP64 rows, halo through L2.
-__device__ __forceinline__ double ilu_inv_pivot(const Geom &g, const double *A, long long ld, long long p) {
+// Block-Jacobi: the rows are cut into contiguous blocks of bs rows (the
+// last one ragged), like one block per process of a row-distributed matrix,
+// and the factorisation keeps only the couplings inside a row's block, i.e.
+// it is the red-black ILU(0) of the block-diagonal part of A.  [lo, hi) is
+// the block of row p; bs >= n (ILU(0), SSOR) gives the whole matrix.
+__device__ __forceinline__ void pc_block(long long p, long long bs, long long n, long long &lo, long long &hi) {
+    lo = (bs >= n) ? 0 : (long long)((unsigned)p / (unsigned)bs) * bs;
+    hi = min(lo + bs, n);
+}
+
+// 1 / pivot of row p: 1/a_pp (red) or 1/d_p (black), the sum over the red
+// neighbours in [lo, hi).  A: FP64 rows, halo through L2.
+__device__ __forceinline__ double ilu_inv_pivot(const Geom &g, const double *A, long long ld, long long p,
+                                                long long lo, long long hi) {
     const double app = A[p];
     if (grid_color(g, p) == 0) return 1.0 / app;
     double d = app;
@@ -255,6 +267,7 @@ __device__ __forceinline__ double ilu_inv_pivot(const Geom &g, const double *A, 
         const double apq = A[(long long)s * ld + p];
         if (apq == 0.0) continue;
         const long long q = p + g.off[s];
+        if (q < lo || q >= hi) continue;
         const double aqp = __ldcg(A + (long long)opposite_slot(s) * ld + q);
         d -= apq * aqp / __ldcg(A + q);
     }
@@ -265,34 +278,63 @@ __device__ __forceinline__ double ilu_inv_pivot(const Geom &g, const double *A, 
 // its red rows are those of A and its black-black block is
 // D_b + A_br D_r^-1 A_rb, so it is the factorisation above with the black
 // pivots d_b = a_bb (the diagonal correction dropped): the same two sweeps.
-__device__ __forceinline__ bool colour_sweep_pc(int pc) { return pc == SKR_PC_ILU0 || pc == SKR_PC_SSOR; }
+__host__ __device__ __forceinline__ bool colour_sweep_pc(int pc) {
+    return pc == SKR_PC_ILU0 || pc == SKR_PC_SSOR || pc == SKR_PC_BJACOBI;
+}
 
-__device__ __forceinline__ double sweep_inv_pivot(const Geom &g, const double *A, long long ld, long long p, int pc) {
-    return (pc == SKR_PC_SSOR) ? 1.0 / A[p] : ilu_inv_pivot(g, A, ld, p);
+// Rows per block of the sweeps: ceil(n / blocks) for block-Jacobi, n otherwise.
+__host__ __device__ __forceinline__ long long sweep_block_rows(int pc, long long n, int blocks) {
+    return (pc == SKR_PC_BJACOBI && blocks > 1) ? (n + blocks - 1) / blocks : n;
+}
+
+__device__ __forceinline__ double sweep_inv_pivot(const Geom &g, const double *A, long long ld, long long p, int pc,
+                                                  long long bs) {
+    if (pc == SKR_PC_SSOR) return 1.0 / A[p];
+    long long lo, hi;
+    pc_block(p, bs, g.n, lo, hi);
+    return ilu_inv_pivot(g, A, ld, p, lo, hi);
 }
 
 // sweep 1 (black rows): z_b = inv_b (v_b - sum_r a_br inv_r v_r), v = scale * src
+// (neighbours outside [lo, hi) are skipped: block-Jacobi)
 template <typename R, typename Tv>
 __device__ __forceinline__ R ilu_sweep1_row(const Geom &g, const R *Aw, long long ld, const R *inv, const Tv *src,
-                                            R scale, long long p) {
+                                            R scale, long long p, long long lo, long long hi) {
     R acc = scale * (R)__ldcg(src + p);
     for (int s = 1; s < g.nst; s++) {
         const long long q = nb_index(g, p, s);
+        if (q < lo || q >= hi) continue;
         acc -= Aw[(long long)s * ld + p] * __ldcg(inv + q) * (scale * (R)__ldcg(src + q));
     }
     return inv[p] * acc;
 }
 
-// sweep 2 (red rows): z_r = inv_r (v_r - sum_b a_rb z_b)
+// sweep 2 (red rows): z_r = inv_r (v_r - sum_b a_rb z_b), b in [lo, hi)
 template <typename R, typename Tv>
 __device__ __forceinline__ R ilu_sweep2_row(const Geom &g, const R *Aw, long long ld, const R *inv, const Tv *src,
-                                            R scale, const R *z, long long p) {
+                                            R scale, const R *z, long long p, long long lo, long long hi) {
     R acc = scale * (R)__ldcg(src + p);
     for (int s = 1; s < g.nst; s++) {
         const long long q = nb_index(g, p, s);
+        if (q < lo || q >= hi) continue;
         acc -= Aw[(long long)s * ld + p] * __ldcg(z + q);
     }
     return inv[p] * acc;
+}
+
+// A z on a red row minus v_r: the couplings M leaves out, sum over the
+// black neighbours outside [lo, hi) of a_rb z_b (0 without blocks, where
+// the red rows of A M^-1 are unit rows)
+template <typename R>
+__device__ __forceinline__ R ilu_red_cross_row(const Geom &g, const R *Aw, long long ld, const R *z, long long p,
+                                               long long lo, long long hi) {
+    R acc = R(0);
+    for (int s = 1; s < g.nst; s++) {
+        const long long q = nb_index(g, p, s);
+        if (q >= lo && q < hi) continue;
+        acc += Aw[(long long)s * ld + p] * __ldcg(z + q);
+    }
+    return acc;
 }
 
 // A z on a black row: a_bb z_b + sum_r a_br z_r

@@ -45,8 +45,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(skr_system, coef), offsetof(skr_system, params),
          offsetof(skr_options, tol), offsetof(skr_options, stream));
   printf("%zu %zu\n", offsetof(skr_result, relres), offsetof(skr_result, seconds));
-  printf("%zu %zu %zu\n", offsetof(skr_options, warm_start), offsetof(skr_options, diagnostics),
-         offsetof(skr_result, delta));
+  printf("%zu %zu %zu %zu\n", offsetof(skr_options, warm_start), offsetof(skr_options, diagnostics),
+         offsetof(skr_result, delta), offsetof(skr_options, pc_blocks));
   return 0;
 }
 '''
@@ -62,7 +62,7 @@ int main(void) {
     assert vals[3:7] == [S.coef.offset, S.params.offset, O.tol.offset, O.stream.offset]
     assert O.profile.offset == 52
     assert vals[7:9] == [R.relres.offset, R.seconds.offset]
-    assert vals[9:12] == [O.warm_start.offset, O.diagnostics.offset, R.delta.offset]
+    assert vals[9:13] == [O.warm_start.offset, O.diagnostics.offset, R.delta.offset, O.pc_blocks.offset]
 
 
 def test_binding_constants_match_header(native):
@@ -79,13 +79,15 @@ def test_binding_constants_match_header(native):
 def test_defaults_and_host_side_validation(native):
     o = native.skr_options_default()
     assert (o.m, o.k, o.maxit, o.max_refine) == (30, 10, 10000, 10)
-    assert o.tol == 1e-8 and o.inner_tol == 1e-5
+    assert o.tol == 1e-8 and o.inner_tol == 1e-5 and o.pc_blocks == 1
     lib = native.library()
     # argument errors are reported before any device work
     assert lib.skr_sort(None, -1, 1, 0, 1, None, None) == native.SKR_ERR_INVALID_ARG
     assert "N < 0" in native.skr_last_error()
     assert lib.skr_sort(None, 0, 1, 0, 1, None, None) == native.SKR_OK
     assert lib.skr_solve_sequence(None, -2, None, None, 1, None, None, None) == native.SKR_ERR_INVALID_ARG
+    assert lib.skr_sort_grouped(None, 5, 1, 0, 0, None, None, None, None) == native.SKR_ERR_INVALID_ARG
+    assert "group_max" in native.skr_last_error()
 
 
 def test_product_path_has_no_oracle_import():

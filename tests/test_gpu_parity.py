@@ -602,3 +602,70 @@ def test_solve_darcy_ssor_matches_oracle(skr, precision):
     optj = skr.skr_options_default(m=30, k=10, tol=1e-8, precond="jacobi", precision=precision)
     _, resj = skr.skr_solve_sequence(systems, order=order, options=optj)
     assert sum(r["steps"] for r in res) < sum(r["steps"] for r in resj)
+
+
+# ------------------------------------------------------------------ block Jacobi
+
+@pytest.mark.parametrize("kind", ["darcy2d", "convdiff2d", "darcy3d"])
+def test_apply_bjacobi_operator(skr, kind):
+    rng = np.random.default_rng(29)
+    if kind == "darcy2d":
+        loga = rng.standard_normal((23, 18))
+        A, _ = assembly.darcy2d(loga)
+        sysd, grid = skr.darcy2d(_dev(loga)), (21, 16)
+    elif kind == "convdiff2d":
+        A, _ = assembly.convdiff2d(0.03, (21.0, -35.0), 20)
+        sysd, grid = skr.convdiff2d(0.03, (21.0, -35.0), 20), (20, 20)
+    else:
+        loga = rng.standard_normal((9, 8, 7))
+        A, _ = assembly.darcy3d(loga)
+        sysd, grid = skr.darcy3d(_dev(loga)), (7, 6, 5)
+    n = A.shape[0]
+    v = rng.standard_normal(n)
+    for blocks in (3, 7, 72, n):
+        M = oprecond.RightPreconditioner(A, "bjacobi", grid, blocks=blocks)
+        want = A @ M.apply(v)
+        y64 = skr.skr_apply(sysd, _dev(v), precond="bjacobi", precision="fp64", pc_blocks=blocks).cpu().numpy()
+        np.testing.assert_allclose(y64, want, rtol=1e-11, atol=1e-12 * np.abs(want).max())
+        y32 = skr.skr_apply(sysd, _dev(v), precond="bjacobi", precision="mixed", pc_blocks=blocks).cpu().numpy()
+        assert np.abs(y32 - want).max() <= 2e-5 * np.abs(want).max(), blocks
+    # one block is ILU(0), bit for bit
+    y1 = skr.skr_apply(sysd, _dev(v), precond="bjacobi", precision="fp64", pc_blocks=1).cpu().numpy()
+    yi = skr.skr_apply(sysd, _dev(v), precond="ilu0", precision="fp64").cpu().numpy()
+    np.testing.assert_array_equal(y1, yi)
+    with pytest.raises(skr.SkrError):
+        skr.skr_apply(sysd, _dev(v), precond="bjacobi", precision="fp64", pc_blocks=0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_darcy_bjacobi_matches_oracle(skr, precision):
+    # 72 blocks, as in the paper's Darcy block-Jacobi runs (one per process)
+    L = darcy2d_sequence(40, 6, 0.15, seed=31)
+    order = osort.greedy_sort(L.reshape(6, -1))
+    systems = [skr.darcy2d(_dev(l)) for l in L]
+    opt = skr.skr_options_default(m=30, k=10, tol=1e-8, precond="bjacobi", pc_blocks=72, precision=precision)
+    xs, res = skr.skr_solve_sequence(systems, order=order, options=opt)
+    sysd = [dict(kind="darcy2d", loga=l) for l in L]
+    xo, info = oskr.solve_sequence(sysd, order, "bjacobi", 30, 10, 1e-8, precision="fp64", pc_blocks=72)
+    for i in range(6):
+        A, b = assembly.darcy2d(L[i])
+        assert res[i]["flag"] == 0, res[i]
+        _check_solution(xs[i], A, b, 1e-8, spla_solve(A, b), 1e-6)
+    if precision == "fp64":
+        tot_g = sum(r["steps"] for r in res)
+        tot_o = sum(i["steps"] for i in info)
+        assert abs(tot_g - tot_o) <= 0.15 * tot_o, (tot_g, tot_o)
+    # cluster sizes cut the rows differently from the blocks: same solutions
+    opt3 = skr.skr_options_default(m=30, k=10, tol=1e-8, precond="bjacobi", pc_blocks=72, precision=precision,
+                                   cluster_size=3)
+    xs3, res3 = skr.skr_solve_sequence(systems, order=order, options=opt3)
+    for i in range(6):
+        assert res3[i]["flag"] == 0
+        x1, x3 = xs[i].cpu().numpy(), xs3[i].cpu().numpy()
+        assert np.abs(x1 - x3).max() <= 1e-6 * np.abs(x1).max()
+    # block Jacobi sits between ILU(0) (one block) and Jacobi in strength
+    st = {}
+    for pc in ("ilu0", "jacobi"):
+        o = skr.skr_options_default(m=30, k=10, tol=1e-8, precond=pc, precision=precision)
+        st[pc] = sum(r["steps"] for r in skr.skr_solve_sequence(systems, order=order, options=o)[1])
+    assert st["ilu0"] <= sum(r["steps"] for r in res) < st["jacobi"]

@@ -201,6 +201,24 @@ def _dist():
     return ws, rank, local
 
 
+def _rank_seed(W, rank):
+    """Seed of a rank's batch: ranks solve independent batches (weak scaling)."""
+    return W["seed"] + 1000 * rank
+
+
+def _agg_ms(ms_list, ws, device):
+    """Mean step time of this rank; with several ranks the maximum over the
+    ranks, since the job is as slow as its slowest rank."""
+    mean = sum(ms_list) / len(ms_list)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([mean], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+    return mean
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -220,7 +238,7 @@ def run_gpu(args):
     from paper_2401_09516_gb300 import _native
     W = _workload(args)
     # weak scaling: every rank solves its own 200-system batch (independent chains)
-    Kh, payload = _inputs(W, max(W["nsys"], args.nsys), W["seed"] + 1000 * rank)
+    Kh, payload = _inputs(W, max(W["nsys"], args.nsys), _rank_seed(W, rank))
     N = args.nsys
     Kh, payload = Kh[:N], payload[:N]
     n = W["nside"] ** 2
@@ -242,10 +260,20 @@ def run_gpu(args):
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    sort_ev = []   # (start, end) events around each sort, timed steps only
+
     def step(k, order=None):
         if order is None:
             order = np.arange(N, dtype=np.int32) if args.no_sort else None
-        perm = skr.skr_sort(P_dev, stream=stream) if order is None else order
+        if order is None:
+            es0 = torch.cuda.Event(enable_timing=True)
+            es1 = torch.cuda.Event(enable_timing=True)
+            es0.record(stream)
+            perm = skr.skr_sort(P_dev, stream=stream)
+            es1.record(stream)
+            sort_ev.append((es0, es1))
+        else:
+            perm = order
         permh = perm.cpu().numpy() if hasattr(perm, "cpu") else perm
         _, res = skr.skr_solve_sequence(systems, order=permh, nchains=nchains, options=opts(k),
                                         x_out=x_dev)
@@ -276,16 +304,13 @@ def run_gpu(args):
     sampler.start()
     t_skr, st_skr, res_skr = timed(W["k"], args.steps, args.warmup)
     clocks = sampler.stop()
+    timed_sorts = sort_ev[-args.steps:] if (sort_ev and not args.no_sort) else []
+    sort_ms = (sum(a.elapsed_time(b) for a, b in timed_sorts) / len(timed_sorts)) if timed_sorts else None
     if args.gmres_steps > 0:
         t_gm, st_gm, res_gm = timed(0, args.gmres_steps, 1)
 
     def agg(ms_list):
-        ms = max(ms_list) if ws == 1 else ms_list
-        if ws > 1:
-            tt = torch.tensor([sum(ms_list) / len(ms_list)], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            return float(tt.item())
-        return sum(ms_list) / len(ms_list)
+        return _agg_ms(ms_list, ws, dev)
 
     ms_step = agg(t_skr)
     value = N * ws / (ms_step / 1e3)
@@ -366,6 +391,7 @@ def run_gpu(args):
             "slots": st_skr[-1]["slots"], "l2": "flushed between steps (256 MB write)",
             "parallelism": "replicas" if ws > 1 else "single GPU",
         },
+        "sort_ms": None if sort_ms is None else round(sort_ms, 3),
         "gmres_value": None if gm_value is None else round(gm_value, 3),
         "gmres_ms_per_step": None if ms_gm is None else round(ms_gm, 3),
         "speedup_vs_gmres": None if gm_value is None else round(value / gm_value, 3),

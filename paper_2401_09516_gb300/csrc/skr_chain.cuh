@@ -155,7 +155,9 @@ __host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads, int es
     P.o_gc = o;    o += align2(m + 2);
     P.o_gs = o;    o += align2(m + 2);
     P.o_F = o;     o += align2(P.ldh * (m > k ? m : k));   // F / M; also the refresh Gram
-    P.o_Z = o;     o += align2(m * m > 2 * k * k ? m * m : 2 * k * k);  // Schur vectors; also R, R^-1
+    // Schur vectors (and, in the mixed form, the FP32 eigen-matrix with an
+    // odd leading dimension beside them); also R, R^-1 of the refresh
+    P.o_Z = o;     o += align2(m * m + m > 2 * k * k ? m * m + m : 2 * k * k);
     P.o_wr = o;    o += align2(m);
     P.o_wi = o;    o += align2(m);
     P.o_vscr = o;  o += align2(m + 2);
@@ -1210,9 +1212,11 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
             R *Mr, *Zr;
             int ldm;
             if (sizeof(R) == 4) {
+                // odd leading dimension: the row updates of the Hessenberg
+                // reduction and the bulge chase hit 32 distinct banks
                 Mr = reinterpret_cast<R *>(c.D(c.P.o_Z));
-                Zr = Mr + mt * mt;
-                ldm = mt;
+                ldm = mt | 1;
+                Zr = Mr + mt * ldm;
             } else {
                 Mr = reinterpret_cast<R *>(F);
                 Zr = reinterpret_cast<R *>(c.D(c.P.o_Z));

@@ -669,3 +669,33 @@ def test_solve_darcy_bjacobi_matches_oracle(skr, precision):
         o = skr.skr_options_default(m=30, k=10, tol=1e-8, precond=pc, precision=precision)
         st[pc] = sum(r["steps"] for r in skr.skr_solve_sequence(systems, order=order, options=o)[1])
     assert st["ilu0"] <= sum(r["steps"] for r in res) < st["jacobi"]
+
+
+# ------------------------------------------------------------------ full size, bench launch configuration
+
+def test_full_size_darcy256_in_the_bench_configuration(skr):
+    # Darcy 256^2, 200 systems, sorted, 76 chains of thread-block clusters of
+    # 2 CTAs, mixed precision, Jacobi, m = 40, k = 20, tol 1e-8.  The oracle
+    # cannot run 200 systems of this size in a test, so every system is
+    # checked through properties that hold at any size (its true FP64
+    # residual with the oracle's own assembly) and three sampled systems
+    # against a direct solve.
+    L = darcy2d_sequence(256, 200, 0.1, seed=2)
+    P = _dev(L.reshape(200, -1))
+    perm = skr.skr_sort(P).cpu().numpy()
+    assert perm.tolist() == osort.greedy_sort(L.reshape(200, -1), 0)
+    systems = [skr.darcy2d(P[i].view(258, 258)) for i in range(200)]
+    opt = skr.skr_options_default(m=40, k=20, tol=1e-8, inner_tol=1e-5, precond="jacobi", precision="mixed",
+                                  cluster_size=2)
+    xs, res = skr.skr_solve_sequence(systems, order=perm, nchains=76, options=opt)
+    st = skr.skr_last_stats()
+    assert st["cluster_size"] == 2 and st["slots"] == 76
+    for i in range(200):
+        assert res[i]["flag"] == 0, (i, res[i])
+        A, b = assembly.darcy2d(L[i])
+        x = xs[i].cpu().numpy()
+        assert np.linalg.norm(b - A @ x) <= 1.01e-8 * np.linalg.norm(b), i
+        assert res[i]["relres"] <= 1e-8
+    for i in (int(perm[0]), int(perm[100]), int(perm[199])):
+        A, b = assembly.darcy2d(L[i])
+        _check_solution(xs[i], A, b, 1e-8, spla_solve(A, b), 1e-6)

@@ -120,3 +120,15 @@ def test_warm_start_carries_the_previous_solution_of_a_chain(skr):
     assert r1["flag"] == 0 and r2["flag"] == 0
     assert r1["steps"] > 0 and r2["steps"] == 0, (r1, r2)
     np.testing.assert_array_equal(x2, x1)
+
+
+@pytest.mark.parametrize("pc,blocks", [("bjacobi", 12), ("ssor", 1)])
+def test_colour_sweep_preconditioners_in_the_serving_loop(skr, pc, blocks):
+    reqs = _mix()
+    with skr.Server(_opts(skr, precond=pc, pc_blocks=blocks)) as srv:
+        outs = [srv.wait(t) for t in [srv.submit(_system(skr, l)) for l in reqs]]
+    for loga, (x, res) in zip(reqs, outs):
+        A, b, xd = _direct(loga)
+        assert res["flag"] == 0, res
+        assert np.linalg.norm(b - A @ x) <= 1.01e-8 * np.linalg.norm(b)
+        assert np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)

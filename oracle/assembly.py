@@ -5,7 +5,7 @@ on a uniform grid, one matrix row per interior node, unknowns in row-major
 order with the second grid index fastest (u11, u12, u21, u22 in the 2x2
 example of Sec. 3.1), Dirichlet data folded into b (zero here).
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
   * Darcy -div(a grad u) = f is discretised in conservative (flux) form; the
     face coefficient is the arithmetic mean of the two node values of a.
   * The Poisson dataset with Chebyshev data (App. E) keeps the Sec. 3.1 sign

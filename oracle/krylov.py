@@ -9,7 +9,7 @@ exactly restarted GMRES(m).
 
 Everything is real (the paper allows complex systems; this build does not).
 
-Readings taken where Algorithm 2 is silent (the design doc lists them):
+Readings taken where Algorithm 2 is silent:
   * a cycle stops early at the first Arnoldi step whose least-squares
     residual is <= tol; such a cycle still updates x and r but does not
     recompute the recycle space (the stopping test of the while loop then

@@ -5,7 +5,7 @@ scan the systems not yet placed in ascending index order and append the one
 whose parameter matrix is nearest (Frobenius norm of the difference) to the
 last placed one, keeping the first strictly smaller distance.
 
-Readings (listed in DESIGN.md):
+Readings:
   * the running minimum starts at +inf (the paper's "e.g. 1000" would keep a
     stale index once every distance exceeds 1000);
   * the scan order is ascending index, so ties go to the lowest index;

@@ -3,9 +3,10 @@
 Each generator returns the raw parameters of N problems of one PDE family:
 coefficient fields on the node grid, scalar parameters and right-hand-side
 fields.  They stand in for the paper's generated datasets (App. D.2), which
-are not available; the shapes and distributions follow the workload table in
-the design doc (Darcy with a = exp(GRF), convection-diffusion with random nu and
-beta, batched chains of mixed grid sides, and a Poisson arrival stream).
+are not available; the shapes and distributions are those of the paper's
+workloads (Darcy with a = exp(GRF), convection-diffusion with random nu and
+beta, Helmholtz with a GRF wavenumber, Poisson with Chebyshev data), plus
+batched chains of mixed grid sides and a Poisson arrival stream.
 """
 import numpy as np
 

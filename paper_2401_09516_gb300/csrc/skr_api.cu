@@ -195,6 +195,21 @@ thread_local LastStats g_last;
 
 namespace {
 
+// Pairwise distance matrix of Algorithm 1 (full sort): short parameter
+// vectors take one thread per pair, long ones a CTA per 4 x 4 tile of pairs;
+// both follow the same summation order.
+cudaError_t launch_sort_dist(const double *P, long long N, long long p, double *dist, int *err, cudaStream_t st) {
+    if (p <= SORT_SMALL_P) {
+        launch_pair_dist_small(P, p, nullptr, nullptr, nullptr, 0, N, dist, err, st);
+    } else {
+        const long long nt = (N + SORT_TILE - 1) / SORT_TILE;
+        const long long blocks = nt * (nt + 1) / 2;
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+        sort_dist_kernel<<<(unsigned)blocks, SORT_LANES, 0, st>>>(P, N, p, dist, err);
+    }
+    return cudaGetLastError();
+}
+
 // Sort the working positions by (set, split value, index): a bitonic
 // network over M = 2^e >= BITONIC_LOCAL keys, the steps with partner
 // distance below BITONIC_LOCAL in shared memory.
@@ -261,11 +276,11 @@ skr_status skr_sort(const double *params, int64_t N, int64_t p, int64_t start, i
         CUDA_TRY(dperm.alloc((size_t)N * 4));
         perm = dperm.as<int>();
     }
-    const long long nt = (N + SORT_TILE - 1) / SORT_TILE;
-    const long long nblocks = nt * (nt + 1) / 2;
-    if (nblocks > 0x7fffffffLL) return fail(SKR_ERR_INVALID_ARG, "N too large");
-    sort_dist_kernel<<<(unsigned)nblocks, SORT_LANES, 0, st>>>(P, N, p, ddist.as<double>(), derr.as<int>());
-    CUDA_TRY(cudaGetLastError());
+    {
+        const cudaError_t e = launch_sort_dist(P, N, p, ddist.as<double>(), derr.as<int>(), st);
+        if (e == cudaErrorInvalidValue) return fail(SKR_ERR_INVALID_ARG, "N too large");
+        CUDA_TRY(e);
+    }
     int herr = 0;
     CUDA_TRY(cudaMemcpyAsync(&herr, derr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -390,6 +405,9 @@ skr_status skr_sort_grouped(const double *params, int64_t N, int64_t p, int64_t 
     }
     // Algorithm 1 inside each group
     const int ng = (int)off.size() - 1;
+    // long parameter vectors: a CTA per 4 x 4 tile of pairs; short ones: a
+    // CTA per row, a thread per pair
+    const bool small = p <= SORT_SMALL_P;
     std::vector<long long> boff(ng + 1), doffs(ng + 1);
     boff[0] = doffs[0] = 0;
     for (int g = 0; g < ng; g++) {
@@ -397,7 +415,8 @@ skr_status skr_sort_grouped(const double *params, int64_t N, int64_t p, int64_t 
         boff[g + 1] = boff[g] + nt * (nt + 1) / 2;
         doffs[g + 1] = doffs[g] + s * s;
     }
-    if (boff[ng] > 0x7fffffffLL) return fail(SKR_ERR_INVALID_ARG, "groups too large for one launch");
+    const long long nblk = small ? (long long)N : boff[ng];
+    if (nblk > 0x7fffffffLL) return fail(SKR_ERR_INVALID_ARG, "groups too large for one launch");
     DBuf dgoff, dboff, ddoff, ddist, dtaken;
     CUDA_TRY(dgoff.alloc((size_t)(ng + 1) * 8));
     CUDA_TRY(dboff.alloc((size_t)(ng + 1) * 8));
@@ -407,7 +426,11 @@ skr_status skr_sort_grouped(const double *params, int64_t N, int64_t p, int64_t 
     CUDA_TRY(cudaMemcpyAsync(dgoff.p, off.data(), (size_t)(ng + 1) * 8, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(dboff.p, boff.data(), (size_t)(ng + 1) * 8, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(ddoff.p, doffs.data(), (size_t)(ng + 1) * 8, cudaMemcpyHostToDevice, st));
-    group_dist_kernel<<<(unsigned)boff[ng], SORT_LANES, 0, st>>>(P, p, didx.as<int>(), dgoff.as<long long>(),
+    if (small)
+        launch_pair_dist_small(P, p, didx.as<int>(), dgoff.as<long long>(), ddoff.as<long long>(), ng, N,
+                               ddist.as<double>(), derr.as<int>(), st);
+    else
+        group_dist_kernel<<<(unsigned)nblk, SORT_LANES, 0, st>>>(P, p, didx.as<int>(), dgoff.as<long long>(),
                                                                  dboff.as<long long>(), ddoff.as<long long>(), ng,
                                                                  ddist.as<double>(), derr.as<int>());
     CUDA_TRY(cudaGetLastError());
@@ -840,9 +863,7 @@ extern "C" skr_status skr_sort_noalloc(const double *params, int64_t N, int64_t 
     // the array keeps the previous call's contents: reset the error word
     // (the chain kernel clears the placed flags itself)
     CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
-    const long long nt = (N + SORT_TILE - 1) / SORT_TILE;
-    sort_dist_kernel<<<(unsigned)(nt * (nt + 1) / 2), SORT_LANES, 0, st>>>(params, N, p, dist, err);
-    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(launch_sort_dist(params, N, p, dist, err, st));
     int herr = 0;
     CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));

@@ -437,6 +437,78 @@ __global__ void __launch_bounds__(SORT_LANES) group_dist_kernel(const double *__
     }
 }
 
+// Short parameter vectors (p <= SORT_SMALL_P): every lane of the fixed
+// order holds at most one term, lanes p .. 255 hold +0, and the rounds of
+// the lane tree with half >= P2 (the power of two >= p) add exact zeros.
+// One thread then reproduces the order for one pair in registers: the p
+// terms, then the rounds P2/2 .. 1.  FP64 issue, not memory, bounds this
+// work on this GPU, and a thread per pair shares each FP64 instruction among
+// 32 pairs.  One CTA per row a of a group, its threads over the rows
+// b >= a of the group; writes both (a, b) and (b, a).  Groups: rows
+// goff[g] .. goff[g + 1) of idx (system indices), matrix at dist + doff[g];
+// ng = 0: one group, rows 0 .. nrows of the identity, matrix at dist.
+constexpr int SORT_SMALL_P = 32;
+template <int P2>
+__global__ void __launch_bounds__(256) pair_dist_small_kernel(const double *__restrict__ P, long long p,
+                                                              const int *__restrict__ idx,
+                                                              const long long *__restrict__ goff,
+                                                              const long long *__restrict__ doff, int ng,
+                                                              long long nrows, double *__restrict__ dist,
+                                                              int *err) {
+    const long long row = blockIdx.x;
+    if (row >= nrows) return;
+    long long base = 0, s = nrows, dof = 0;
+    if (ng > 0) {
+        int lo = 0, hi = ng - 1;   // the group g with goff[g] <= row < goff[g + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (goff[mid] <= row) lo = mid;
+            else hi = mid - 1;
+        }
+        base = goff[lo];
+        s = goff[lo + 1] - base;
+        dof = doff[lo];
+    }
+    const long long a = row - base;
+    const long long ri = idx ? idx[row] : row;
+    double xi[P2];
+#pragma unroll
+    for (int t = 0; t < P2; t++) xi[t] = (t < p) ? P[ri * p + t] : 0.0;
+    for (long long b = a + threadIdx.x; b < s; b += blockDim.x) {
+        const long long rj = idx ? idx[base + b] : base + b;
+        double v[P2];
+#pragma unroll
+        for (int t = 0; t < P2; t++) {
+            double acc = 0.0;
+            if (t < p) {
+                const double d = __dsub_rn(xi[t], P[rj * p + t]);
+                acc = __dadd_rn(acc, __dmul_rn(d, d));
+            }
+            v[t] = acc;
+        }
+#pragma unroll
+        for (int half = P2 / 2; half >= 1; half >>= 1)
+#pragma unroll
+            for (int l = 0; l < half; l++) v[l] = __dadd_rn(v[l], v[l + half]);
+        if (!isfinite(v[0])) atomicExch(err, 1);
+        dist[dof + a * s + b] = v[0];
+        dist[dof + b * s + a] = v[0];
+    }
+}
+
+// Launch of the kernel above for p <= SORT_SMALL_P.
+inline void launch_pair_dist_small(const double *P, long long p, const int *idx, const long long *goff,
+                                   const long long *doff, int ng, long long nrows, double *dist, int *err,
+                                   cudaStream_t st) {
+    const unsigned grid = (unsigned)nrows;
+    if (p <= 1) pair_dist_small_kernel<1><<<grid, 256, 0, st>>>(P, p, idx, goff, doff, ng, nrows, dist, err);
+    else if (p <= 2) pair_dist_small_kernel<2><<<grid, 256, 0, st>>>(P, p, idx, goff, doff, ng, nrows, dist, err);
+    else if (p <= 4) pair_dist_small_kernel<4><<<grid, 256, 0, st>>>(P, p, idx, goff, doff, ng, nrows, dist, err);
+    else if (p <= 8) pair_dist_small_kernel<8><<<grid, 256, 0, st>>>(P, p, idx, goff, doff, ng, nrows, dist, err);
+    else if (p <= 16) pair_dist_small_kernel<16><<<grid, 256, 0, st>>>(P, p, idx, goff, doff, ng, nrows, dist, err);
+    else pair_dist_small_kernel<32><<<grid, 256, 0, st>>>(P, p, idx, goff, doff, ng, nrows, dist, err);
+}
+
 // Algorithm 1 inside every group (one CTA per group), from the group's
 // lowest index; writes perm[goff[g] ..) as system indices.
 __global__ void __launch_bounds__(256) group_chain_kernel(const double *__restrict__ dist,

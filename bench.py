@@ -49,6 +49,8 @@ WORKLOADS = {
     # the paper's Helmholtz set (App. E): 100^2 unknowns, k from a GRF; indefinite
     "helmholtz100": dict(kind="helmholtz2d", nside=100, nsys=200, kbar=10.0, ell=0.1, sigma=1.0, spread=0.2,
                          seed=6, m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5,
+                         # n = 10^4 needs no cluster: one CTA per chain, fewer and longer chains
+                         chains=100, cluster_size=1,
                          desc="helmholtz2d 100x100 (n=10000), %d systems, -lap u - k^2 u = 1, "
                               "k=10 exp(0.2 GRF(ell=0.1 sigma=1)), Jacobi, GCRO-DR m=40 k=20, mixed precision, tol 1e-8"),
 }
@@ -250,12 +252,13 @@ def run_gpu(args):
     systems = [_system(skr, W, p) for p in pay_dev]
     x_dev = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(N)]
     stream = torch.cuda.current_stream(dev)
-    nchains = args.chains
+    nchains = args.chains if args.chains is not None else W.get("chains", 76)
+    cluster_size = args.cluster_size if args.cluster_size is not None else W.get("cluster_size", 2)
 
     def opts(k):
         return skr.skr_options_default(m=W["m"], k=k, tol=W["tol"], inner_tol=W["inner_tol"],
                                        precond=W["precond"], pc_blocks=W["pc_blocks"], precision=W["precision"],
-                                       cluster_size=args.cluster_size, stream=stream,
+                                       cluster_size=cluster_size, stream=stream,
                                        warm_start=int(args.warm_start), diagnostics=int(args.diagnostics))
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -327,7 +330,7 @@ def run_gpu(args):
     kbytes = sum(s["bytes"] for s in st_skr) / len(st_skr)
     kms = sum(s["kernel_ms"] for s in st_skr) / len(st_skr)
     achieved = kbytes / (kms / 1e3) / 1e9
-    default_workload = (args.workload == "darcy256" and N == W["nsys"] and nchains == 76 and args.cluster_size == 2)
+    default_workload = (args.workload == "darcy256" and N == W["nsys"] and nchains == 76 and cluster_size == 2)
     traffic = None
     if default_workload and TRAFFIC["sources_sha256"] == _kernel_sources_sha256():
         traffic = TRAFFIC["bytes_per_launch"]
@@ -644,8 +647,10 @@ def main():
     ap.add_argument("--pc-blocks", type=int, default=72,
                     help="row blocks of --precond bjacobi (72: the paper's Darcy runs, one per process)")
     ap.add_argument("--diagnostics", action="store_true", help="report the mean one-sided distance delta")
-    ap.add_argument("--chains", type=int, default=76, help="independent chains the sorted order is cut into")
-    ap.add_argument("--cluster-size", type=int, default=2, help="CTAs per chain (thread-block cluster)")
+    ap.add_argument("--chains", type=int, default=None,
+                    help="independent chains the sorted order is cut into (default: the workload's, 76)")
+    ap.add_argument("--cluster-size", type=int, default=None,
+                    help="CTAs per chain, a thread-block cluster (default: the workload's, 2)")
     ap.add_argument("--nsys", type=int, default=200, help="systems per batch (200 = the full workload)")
     ap.add_argument("--gmres-steps", type=int, default=1)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")

@@ -32,9 +32,12 @@ Readings taken where Algorithm 2 is silent:
 Pins (tests/test_oracle_krylov.py): dense-LU solutions on small grids;
 orthonormality of V and C; A U = C; the projected Arnoldi relation (Eq. 4);
 k = 0 reproduces GMRES; identical consecutive systems converge in far fewer
-steps (delta = gamma = 0, Sec. 5.1); harmonic Ritz values of a repeated
-constant-coefficient Laplacian approach its smallest closed-form
-eigenvalues.  The harmonic-Ritz selection itself is parity unpinned.
+steps (delta = gamma = 0, Sec. 5.1); harmonic Ritz values on a complete
+Krylov space equal the closed-form Laplacian eigenvalues; the harmonic
+Petrov-Galerkin condition for both branches of Algorithm 2; the selection
+rule on a hand-made spectrum (order, ties, conjugate pairs, the split
+rule); and, on a complete space, the subspace selected by either branch
+spans the closed-form eigenvectors of the k smallest eigenvalues.
 """
 import numpy as np
 import scipy.linalg as sla

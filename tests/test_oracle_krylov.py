@@ -458,3 +458,65 @@ def test_bjacobi_gcrodr_converges_on_darcy():
     _, infoj = skr.solve_system(A, b, "jacobi", 20, 6, 1e-10, krylov.RecycleState(), grid=(12, 12))
     # between ILU(0) (one block) and Jacobi (one row per block) in strength
     assert info1["steps"] <= info["steps"] <= infoj["steps"]
+
+
+# ---------------------------------------------------------------- harmonic-Ritz selection on a complete space
+
+def _laplacian_3x5_and_smallest_eigvecs(k):
+    # a = 1 Darcy on a 3 x 5 grid: A = -lap_h, eigenvectors
+    # sin(p pi x_i) sin(q pi y_j), eigenvalues lx[p] + ly[q] (closed form)
+    nx, ny = 3, 5
+    A, _ = assembly.darcy2d(np.zeros((nx + 2, ny + 2)))
+    hx, hy = 1.0 / (nx + 1), 1.0 / (ny + 1)
+    pairs = [(p, q) for p in range(1, nx + 1) for q in range(1, ny + 1)]
+    lam = {pq: 4.0 / hx**2 * np.sin(pq[0] * np.pi * hx / 2) ** 2 + 4.0 / hy**2 * np.sin(pq[1] * np.pi * hy / 2) ** 2
+           for pq in pairs}
+    order = sorted(pairs, key=lambda pq: lam[pq])
+    assert lam[order[k]] - lam[order[k - 1]] > 1.0        # a gap after the k-th: the span is unique
+    i, j = np.meshgrid(np.arange(1, nx + 1), np.arange(1, ny + 1), indexing="ij")
+    E = np.stack([(np.sin(p * np.pi * i * hx) * np.sin(q * np.pi * j * hy)).ravel() for p, q in order[:k]], axis=1)
+    return A, E
+
+
+def test_first_cycle_selection_spans_the_smallest_closed_form_eigenvectors():
+    import scipy.linalg as sla
+    k = 3
+    A, E = _laplacian_3x5_and_smallest_eigvecs(k)
+    n = A.shape[0]
+    ar = krylov.arnoldi(lambda v: A @ v, np.random.default_rng(5).standard_normal(n), n, None, 0.0)
+    P, _ = krylov.harmonic_ritz_first(ar["Hbar"], k)
+    assert P.shape[1] == k
+    Y = ar["V"][:, :n] @ P
+    assert sla.subspace_angles(Y, E).max() < 1e-6
+
+
+def test_recycled_cycle_selection_spans_the_smallest_closed_form_eigenvectors():
+    # the augmented space [U, V] of a recycled cycle covers R^n: the
+    # generalized harmonic-Ritz problem of Algorithm 2 is exact, and the k
+    # smallest |theta| select the closed-form eigenvectors
+    import scipy.linalg as sla
+    k = 3
+    A, E = _laplacian_3x5_and_smallest_eigvecs(k)
+    n = A.shape[0]
+    rng = np.random.default_rng(6)
+    kc = 4
+    state = krylov.RecycleState()
+    state.U = rng.standard_normal((n, kc))
+    state.C = None
+    krylov.refresh(lambda v: A @ v, state)            # C = qr(A U).Q, U = U R^-1
+    U, C = state.U, state.C
+    r = rng.standard_normal(n)
+    r = r - C @ (C.T @ r)
+    ar = krylov.arnoldi(lambda v: A @ v, r, n - kc, C, 0.0)
+    j = ar["j"]
+    assert kc + j == n
+    Dk = 1.0 / np.linalg.norm(U, axis=0)
+    Vhat = np.concatenate([U * Dk, ar["V"][:, :j]], axis=1)
+    What = np.concatenate([C, ar["V"]], axis=1)
+    G = np.zeros((kc + j + 1, kc + j))
+    G[:kc, :kc] = np.diag(Dk)
+    G[:kc, kc:] = ar["B"]
+    G[kc:, kc:] = ar["Hbar"]
+    P, _ = krylov.harmonic_ritz_general(G, What, Vhat, k)
+    assert P.shape[1] == k
+    assert sla.subspace_angles(Vhat @ P, E).max() < 1e-6

@@ -10,7 +10,8 @@ computes, in float64, following the paper step by step:
 
   assembly.py   finite-difference discretisation (Sec. 3.1, App. A.2)
   sort.py       the greedy nearest-neighbour sort (Sec. 4.1, Algorithm 1)
-  precond.py    Jacobi and ILU(0) preconditioners (App. D.3)
+                and its large-N grouped form
+  precond.py    Jacobi, SSOR, ILU(0) and block-Jacobi preconditioners (App. D.3)
   krylov.py     Arnoldi (Eq. 2-3), restarted GMRES (Sec. 3.2) and GCRO-DR
                 with the recycle refresh (Sec. 4.2, Eq. 4, App. B.1,
                 Algorithm 2)
@@ -20,7 +21,8 @@ Library primitives used as single steps: numpy/scipy sparse products,
 np.linalg.qr, np.linalg.lstsq, np.linalg.eig, scipy.linalg.eig (QZ),
 scipy triangular solves.
 
-Parity status per function is listed in the module docstrings; the
-harmonic-Ritz selection inside GCRO-DR is "parity unpinned" beyond its
-invariants (no worked example of Algorithm 2 is printed in the paper).
+The pins of each function are listed in the module docstrings.  The paper
+prints no worked example of Algorithm 2, so GCRO-DR is pinned by closed
+forms and invariants: dense-LU solutions, the Arnoldi relations, exact
+harmonic Ritz pairs and the selected eigenvectors on a complete space.
 """

@@ -555,6 +555,57 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """Serving: a seeded Poisson arrival stream of 2D and 3D Darcy requests
+    replayed in real time against the server (skr_server_*)."""
+    import torch
+
+    _, _, local = _dist()
+    torch.cuda.set_device(local)
+    import paper_2401_09516_gb300 as skr
+    from workloads import serving_stream
+    opts = skr.skr_options_default(m=40, k=20, tol=1e-8, inner_tol=1e-5, precond="jacobi", precision="mixed")
+    sides2d, sides3d = (128, 256), (48, 64)
+    reqs = serving_stream(args.serving_requests, args.serving_rate, seed=5, sides2d=sides2d, sides3d=sides3d)
+    systems = [skr.darcy3d(r["loga"]) if r["ndim"] == 3 else skr.darcy2d(r["loga"]) for r in reqs]
+    # warm-up on a server of its own (context, module load, first chains)
+    with skr.Server(opts) as srv:
+        for t in [srv.submit(systems[i]) for i in range(min(8, len(systems)))]:
+            srv.wait(t)
+    sampler = ClockSampler(local)
+    sampler.start()
+    done = {}
+    with skr.Server(opts) as srv:
+        tickets = []
+        t0 = time.perf_counter()
+        for r, sysr in zip(reqs, systems):
+            while time.perf_counter() - t0 < r["t"]:   # arrival time of the request
+                time.sleep(0.0002)
+            tickets.append(srv.submit(sysr))
+        for t in tickets:
+            done[t] = srv.wait(t, timeout=600.0)
+        elapsed = time.perf_counter() - t0
+        st = srv.stats()
+    clocks = sampler.stop()
+    flags = sorted({res["flag"] for _, res in done.values()})
+    worst = max(res["relres"] for _, res in done.values())   # true FP64 residuals of the results
+    n3 = sum(1 for r in reqs if r["ndim"] == 3)
+    line = {
+        "metric": "serving: completed systems/s and submit-to-completion p50/p99 under Poisson arrivals",
+        "value": round(len(reqs) / elapsed, 2), "unit": "systems/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": round(elapsed * 1e3, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "%d Darcy requests, Poisson arrivals at %.0f/s (seed 5): %d 2D (sides %s), %d 3D "
+                               "(sides %s), a=exp(GRF ell=0.1 sigma=1), Jacobi, GCRO-DR m=40 k=20, mixed, tol 1e-8"
+                               % (len(reqs), args.serving_rate, len(reqs) - n3, list(sides2d), n3, list(sides3d)),
+                   "chains": st["chains"]},
+        "latency_ms": {"p50": round(st["p50_ms"], 2), "p99": round(st["p99_ms"], 2), "mean": round(st["mean_ms"], 2)},
+        "arrival_span_s": round(reqs[-1]["t"], 3), "flags": flags, "max_relres": worst,
+        "gpu_launches": len(reqs), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def _grouped_sort_launches(N, p, G):
     """Kernel launches of one skr_sort_grouped call (its host loop, counted)."""
     M = 1024
@@ -660,6 +711,10 @@ def main():
                     help="time the large-N grouped sort instead of the solves (use with --nsys)")
     ap.add_argument("--keys-p", type=int, default=16, help="coordinates per key for --sort-only")
     ap.add_argument("--group-max", type=int, default=1000, help="largest group for --sort-only")
+    ap.add_argument("--serving", action="store_true",
+                    help="replay a Poisson arrival stream against the serving loop instead of the batch")
+    ap.add_argument("--serving-requests", type=int, default=300)
+    ap.add_argument("--serving-rate", type=float, default=100.0, help="arrivals per second")
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="upper bound on one reference sample")
     args = ap.parse_args()
@@ -667,6 +722,8 @@ def main():
         os.environ.setdefault(var, "1")
     if args.sort_only:
         run_sort_only(args)
+    elif args.serving:
+        run_serving(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -574,18 +574,37 @@ def run_serving(args):
             srv.wait(t)
     sampler = ClockSampler(local)
     sampler.start()
-    done = {}
+    done, t_done = {}, {}
     with skr.Server(opts) as srv:
-        tickets = []
+        tickets, pending = [], []
         t0 = time.perf_counter()
+
+        def collect():
+            for t in list(pending):
+                out = srv.poll(t)
+                if out is not None:
+                    done[t] = out
+                    t_done[t] = time.perf_counter() - t0
+                    pending.remove(t)
+
         for r, sysr in zip(reqs, systems):
             while time.perf_counter() - t0 < r["t"]:   # arrival time of the request
+                collect()
                 time.sleep(0.0002)
-            tickets.append(srv.submit(sysr))
-        for t in tickets:
-            done[t] = srv.wait(t, timeout=600.0)
+            t = srv.submit(sysr)
+            tickets.append(t)
+            pending.append(t)
+        submit_span = time.perf_counter() - t0
+        while pending:
+            if time.perf_counter() - t0 > 600.0:
+                raise TimeoutError("serving stream not drained after 600 s")
+            collect()
+            time.sleep(0.0002)
         elapsed = time.perf_counter() - t0
         st = srv.stats()
+    # client view: from the scheduled arrival to the poll that returned the result
+    lat_client = sorted((t_done[t] - r["t"]) * 1e3 for r, t in zip(reqs, tickets))
+    pct = lambda q: lat_client[min(len(lat_client) - 1, int(round(q * (len(lat_client) - 1))))]   # noqa: E731
     clocks = sampler.stop()
     flags = sorted({res["flag"] for _, res in done.values()})
     worst = max(res["relres"] for _, res in done.values())   # true FP64 residuals of the results
@@ -599,8 +618,13 @@ def run_serving(args):
                                "(sides %s), a=exp(GRF ell=0.1 sigma=1), Jacobi, GCRO-DR m=40 k=20, mixed, tol 1e-8"
                                % (len(reqs), args.serving_rate, len(reqs) - n3, list(sides2d), n3, list(sides3d)),
                    "chains": st["chains"]},
-        "latency_ms": {"p50": round(st["p50_ms"], 2), "p99": round(st["p99_ms"], 2), "mean": round(st["mean_ms"], 2)},
-        "arrival_span_s": round(reqs[-1]["t"], 3), "flags": flags, "max_relres": worst,
+        "latency_ms": {"p50": round(pct(0.50), 2), "p99": round(pct(0.99), 2),
+                       "mean": round(sum(lat_client) / len(lat_client), 2),
+                       "measured": "scheduled arrival to the poll that returned the result"},
+        "server_latency_ms": {"p50": round(st["p50_ms"], 2), "p99": round(st["p99_ms"], 2),
+                              "measured": "skr_submit return to completion, by the server"},
+        "arrival_span_s": round(reqs[-1]["t"], 3), "submit_span_s": round(submit_span, 3),
+        "flags": flags, "max_relres": worst,
         "gpu_launches": len(reqs), "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

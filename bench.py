@@ -113,16 +113,24 @@ def _oracle_system(W, payload):
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one chain-
 # kernel launch on the default workload, from a one-pass ncu capture; valid
-# only for the kernel sources it was taken with (sha256 over csrc/ and the
-# public header, as computed by _kernel_sources_sha256).
-TRAFFIC = {"sources_sha256": "090f82f15539c97cc22c54e0a577557782f8e71ee6bc3627f21b0eff364df5ec",
+# only for the sources it was taken with (sha256 over the files that build
+# or launch the chain kernel and the public header, as computed by
+# _kernel_sources_sha256).
+TRAFFIC = {"sources_sha256": "e4f99adf54da31ed8a0398a2517ae455957ee793352754bb2fb493adc93c7385",
            "bytes_per_launch": 5.70e12 + 0.41003e12}
 
 
+# the chain kernel's translation units, their headers and the host code
+# that launches it from skr_solve_sequence (the server and the sort kernels
+# do not change a chain-kernel launch)
+CHAIN_KERNEL_SOURCES = ("skr_api.cu", "skr_chain.cuh", "skr_chain_f32.cu", "skr_chain_f64.cu",
+                        "skr_chain_launch.cuh", "skr_common.h", "skr_dense.cuh", "skr_device.cuh",
+                        "skr_launch.h", "skr_stencil.cuh", "skr_tma.h", "skr_workspace.h")
+
+
 def _kernel_sources_sha256():
-    files = [f for f in glob.glob(os.path.join(ROOT, "paper_2401_09516_gb300", "csrc", "*"))
-             if f.endswith((".cu", ".cuh", ".h"))]
-    files = sorted(files) + [os.path.join(ROOT, "include", "skr.h")]
+    files = [os.path.join(ROOT, "paper_2401_09516_gb300", "csrc", f) for f in CHAIN_KERNEL_SOURCES]
+    files = files + [os.path.join(ROOT, "include", "skr.h")]
     h = hashlib.sha256()
     for f in files:
         h.update(os.path.relpath(f, ROOT).encode())

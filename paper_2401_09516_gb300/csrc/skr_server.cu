@@ -304,10 +304,31 @@ double sqdist(const std::vector<double> &a, const std::vector<double> &b) {
     return s;
 }
 
+// The server thread.  Each round: under the lock, collect the chains whose
+// launch finished and take a snapshot of the queue; without the lock, copy
+// their results out of the pinned staging buffers and route the queued
+// requests to idle chains (the nearest key of the same shape); under the
+// lock again, publish the results, create chains and launch.  The chain list
+// and every chain's state are written by this thread only, and only under
+// the lock, so the unlocked reads race with nothing; a request that is
+// queued or running is never touched by skr_poll, and its key is immutable.
+// skr_submit and skr_poll therefore wait for the lock only while results are
+// published and requests launched, not while keys are compared.
 void loop(skr_server *S) {
     cudaSetDevice(S->device);
+    struct Done {
+        Chain *c;
+        Request *r;
+        bool ok;
+    };
+    std::vector<Done> done;
+    std::vector<Request *> queued;
+    std::vector<std::pair<Request *, Chain *>> plan;   // chain nullptr: a new chain
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
+        done.clear();
+        queued.clear();
+        plan.clear();
         bool any_busy = false;
         for (Chain *c : S->chains) {
             if (!c->busy) continue;
@@ -316,62 +337,75 @@ void loop(skr_server *S) {
                 any_busy = true;
                 continue;
             }
+            if (q != cudaSuccess) cudaGetLastError();
             auto it = S->reqs.find(c->ticket);
-            if (it != S->reqs.end()) {
-                Request *r = it->second;
-                if (q == cudaSuccess) {
-                    finish(S, r, c->hres, true);
-                    r->x.assign(c->hx, c->hx + r->n);
-                } else {
-                    cudaGetLastError();
-                    finish(S, r, nullptr, false);
+            done.push_back({c, it != S->reqs.end() ? it->second : nullptr, q == cudaSuccess});
+        }
+        if (S->stop && !any_busy && done.empty()) break;
+        if (!S->stop)
+            for (uint64_t t : S->queue) queued.push_back(S->reqs[t]);
+        const size_t nchains = S->chains.size();
+        lk.unlock();
+        for (const Done &d : done)
+            if (d.r && d.ok) d.r->x.assign(d.c->hx, d.c->hx + d.r->n);
+        {
+            std::vector<char> taken(nchains, 0);
+            int fresh = 0;
+            for (Request *r : queued) {
+                int best = -1;
+                double bd = INFINITY;
+                for (size_t ci = 0; ci < nchains; ci++) {
+                    const Chain *c = S->chains[ci];
+                    bool idle = !c->busy;
+                    for (const Done &d : done) idle = idle || d.c == c;
+                    if (!idle || taken[ci] || c->fmt != r->fmt || c->nx != r->nx || c->ny != r->ny ||
+                        c->nz != r->nz || c->p != r->key.size())
+                        continue;
+                    const double dist = c->key.empty() ? 0.0 : sqdist(c->key, r->key);
+                    if (dist < bd) {
+                        bd = dist;
+                        best = (int)ci;
+                    }
+                }
+                if (best >= 0) {
+                    taken[best] = 1;
+                    plan.push_back({r, S->chains[best]});
+                } else if ((int)nchains + fresh < S->max_chains) {
+                    fresh++;
+                    plan.push_back({r, nullptr});
                 }
             }
-            c->busy = false;
         }
-        if (S->stop && !any_busy) break;
-        if (!S->stop) {
-            for (auto it = S->queue.begin(); it != S->queue.end();) {
-                Request *r = S->reqs[*it];
-                Chain *best = nullptr;
-                double bd = INFINITY;
-                for (Chain *c : S->chains) {
-                    if (c->busy || c->fmt != r->fmt || c->nx != r->nx || c->ny != r->ny || c->nz != r->nz ||
-                        c->p != r->key.size())
-                        continue;
-                    const double d = c->key.empty() ? 0.0 : sqdist(c->key, r->key);
-                    if (d < bd) {
-                        bd = d;
-                        best = c;
-                    }
-                }
-                if (!best && (int)S->chains.size() < S->max_chains) {
-                    const size_t need = chain_bytes(S, *r, auto_cs(r->n, S->opt.cluster_size));
-                    if (S->budget == 0 || S->used + need <= S->budget) {
-                        best = create_chain(S, *r);
-                        if (best) {
-                            S->chains.push_back(best);
-                            S->used += best->bytes;
-                        } else {
-                            // device memory could not be obtained: fail the request
-                            // rather than keep it queued
-                            finish(S, r, nullptr, false);
-                            it = S->queue.erase(it);
-                            continue;
-                        }
-                    }
-                }
-                if (!best) {
-                    ++it;
+        lk.lock();
+        for (const Done &d : done) {
+            if (d.r) finish(S, d.r, d.ok ? d.c->hres : nullptr, d.ok);
+            d.c->busy = false;
+        }
+        for (auto &pr : plan) {
+            if (S->stop) break;
+            Request *r = pr.first;
+            Chain *best = pr.second;
+            if (!best) {
+                const size_t need = chain_bytes(S, *r, auto_cs(r->n, S->opt.cluster_size));
+                if (S->budget != 0 && S->used + need > S->budget) continue;   // stays queued
+                best = create_chain(S, *r);
+                if (best) {
+                    S->chains.push_back(best);
+                    S->used += best->bytes;
+                } else {
+                    // device memory could not be obtained: fail the request
+                    // rather than keep it queued
+                    finish(S, r, nullptr, false);
+                    S->queue.erase(std::find(S->queue.begin(), S->queue.end(), r->ticket));
                     continue;
                 }
-                if (!launch(S, best, r)) {
-                    cudaGetLastError();
-                    finish(S, r, nullptr, false);
-                    best->busy = false;
-                }
-                it = S->queue.erase(it);
             }
+            if (!launch(S, best, r)) {
+                cudaGetLastError();
+                finish(S, r, nullptr, false);
+                best->busy = false;
+            }
+            S->queue.erase(std::find(S->queue.begin(), S->queue.end(), r->ticket));
         }
         S->cv.wait_for(lk, std::chrono::microseconds(50));
     }

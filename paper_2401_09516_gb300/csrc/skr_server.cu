@@ -314,6 +314,11 @@ double sqdist(const std::vector<double> &a, const std::vector<double> &b) {
 // queued or running is never touched by skr_poll, and its key is immutable.
 // skr_submit and skr_poll therefore wait for the lock only while results are
 // published and requests launched, not while keys are compared.
+void dequeue(skr_server *S, uint64_t ticket) {
+    auto it = std::find(S->queue.begin(), S->queue.end(), ticket);
+    if (it != S->queue.end()) S->queue.erase(it);
+}
+
 void loop(skr_server *S) {
     cudaSetDevice(S->device);
     struct Done {
@@ -396,7 +401,7 @@ void loop(skr_server *S) {
                     // device memory could not be obtained: fail the request
                     // rather than keep it queued
                     finish(S, r, nullptr, false);
-                    S->queue.erase(std::find(S->queue.begin(), S->queue.end(), r->ticket));
+                    dequeue(S, r->ticket);
                     continue;
                 }
             }
@@ -405,7 +410,7 @@ void loop(skr_server *S) {
                 finish(S, r, nullptr, false);
                 best->busy = false;
             }
-            S->queue.erase(std::find(S->queue.begin(), S->queue.end(), r->ticket));
+            dequeue(S, r->ticket);
         }
         S->cv.wait_for(lk, std::chrono::microseconds(50));
     }

@@ -39,6 +39,13 @@ WORKLOADS = {
                      precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5,
                      desc="darcy2d 100x100 (n=10000), %d systems, a=exp(GRF ell=0.1 sigma=1), f=1, "
                           "Jacobi, GCRO-DR m=40 k=20, mixed precision, tol 1e-8"),
+    # Darcy 100^2 on a closed curve of GRF samples: close neighbours exist, so
+    # the sort's effect on the recycle spaces (Table 2's mechanism) can show
+    "darcy100_circle": dict(kind="darcy2d", family="circle", nside=100, nsys=200, ell=0.1, sigma=1.0, seed=9,
+                            m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5,
+                            desc="darcy2d 100x100 (n=10000), %d systems, a=exp(cos t G1 + sin t G2), G1, G2 "
+                                 "GRF ell=0.1 sigma=1, t ~ U[0, 2pi), f=1, Jacobi, GCRO-DR m=40 k=20, "
+                                 "mixed precision, tol 1e-8"),
     # Poisson with Dirichlet data and forcing from truncated Chebyshev series (App. E);
     # one fixed matrix, the right-hand sides differ; sort keys = the 96 coefficients
     "poisson_cheb256": dict(kind="poisson2d", nside=256, nsys=200, ncoef=8, decay=0.6, seed=7, m=40, k=20,
@@ -77,8 +84,11 @@ def _workload(args):
 def _inputs(W, nsys, seed):
     """Seeded inputs of nsys systems: (sort keys [nsys, p], per-system payload)."""
     if W["kind"] == "darcy2d":
-        from workloads import darcy2d_sequence
-        L = darcy2d_sequence(W["nside"], nsys, W["ell"], W["sigma"], seed=seed)
+        from workloads import darcy2d_sequence, darcy2d_circle_sequence
+        if W.get("family") == "circle":
+            L, _ = darcy2d_circle_sequence(W["nside"], nsys, W["ell"], W["sigma"], seed=seed)
+        else:
+            L = darcy2d_sequence(W["nside"], nsys, W["ell"], W["sigma"], seed=seed)
         return L.reshape(nsys, -1), [L[i] for i in range(nsys)]
     if W["kind"] == "helmholtz2d":
         from workloads import helmholtz2d_sequence
@@ -722,7 +732,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="skr", choices=["skr", "reference"])
     ap.add_argument("--workload", default="darcy256", choices=sorted(WORKLOADS),
-                    help="darcy256 (the headline workload), darcy100, helmholtz100 or poisson_cheb256")
+                    help="darcy256 (the headline workload), darcy100, darcy100_circle, helmholtz100 or "
+                         "poisson_cheb256")
     ap.add_argument("--warm-start", action="store_true", help="x_0 = previous solution of the chain")
     ap.add_argument("--no-sort", action="store_true", help="solve in input order (ablation)")
     ap.add_argument("--precond", default=None, choices=sorted(PRECOND_NAMES),

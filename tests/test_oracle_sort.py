@@ -181,3 +181,20 @@ def test_grouped_sort_sizes_and_permutation(seed, N, p, G):
     assert min(sizes) >= N // 2 ** depth
     for q, g in enumerate(groups):
         assert order[offs[q]] == g[0]   # each group starts at its lowest index
+
+
+def test_sort_walks_a_closed_curve_of_fields():
+    # fields cos(t) G1 + sin(t) G2: the distance between two of them grows
+    # with |t_i - t_j| (mod 2 pi), so Algorithm 1's chain walks the curve and
+    # its tour in t is short, while the input order jumps about
+    from workloads import darcy2d_circle_sequence
+    L, t = darcy2d_circle_sequence(14, 40, 0.2, seed=3)
+    assert abs(L.reshape(40, -1).var(axis=1).mean() - 1.0) < 0.6   # GRF marginal, sigma = 1
+    order = sort.greedy_sort(L.reshape(40, -1), 0)
+
+    def tour(o):
+        d = np.abs(np.diff(t[o]))
+        return float(np.minimum(d, 2 * np.pi - d).sum())
+
+    assert tour(order) <= 4 * np.pi
+    assert tour(list(range(40))) > 3 * tour(order)

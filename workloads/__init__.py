@@ -9,6 +9,7 @@ produced here.
 from .grf import grf_field
 from .sequences import (
     darcy2d_sequence,
+    darcy2d_circle_sequence,
     darcy3d_sequence,
     convdiff2d_sequence,
     helmholtz2d_sequence,
@@ -21,6 +22,7 @@ from .sequences import (
 __all__ = [
     "grf_field",
     "darcy2d_sequence",
+    "darcy2d_circle_sequence",
     "darcy3d_sequence",
     "convdiff2d_sequence",
     "helmholtz2d_sequence",

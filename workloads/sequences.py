@@ -26,6 +26,23 @@ def darcy2d_sequence(nside, nsys, ell, sigma=1.0, seed=0):
     return out
 
 
+def darcy2d_circle_sequence(nside, nsys, ell, sigma=1.0, seed=0):
+    """N Darcy problems whose fields lie on a closed curve of GRF samples.
+
+    log a(t) = cos(t) G1 + sin(t) G2 for two independent GRFs G1, G2 and
+    t_i uniform on [0, 2 pi) (seeded): every field is itself a GRF sample
+    with the same covariance, but neighbours along the curve are close, the
+    setting in which the sort's nearest neighbours share recycle spaces.
+    Returns (log a [nsys, nside+2, nside+2], t [nsys]).
+    """
+    rng = np.random.default_rng(seed)
+    g1 = grf_field(rng, nside + 2, ell, sigma, ndim=2)
+    g2 = grf_field(rng, nside + 2, ell, sigma, ndim=2)
+    t = rng.uniform(0.0, 2.0 * np.pi, size=nsys)
+    out = np.cos(t)[:, None, None] * g1[None] + np.sin(t)[:, None, None] * g2[None]
+    return out, t
+
+
 def darcy3d_sequence(nside, nsys, ell, sigma=1.0, seed=0, pad_factor=2):
     """N 3D Darcy problems on an nside^3 interior grid: log a at (nside+2)^3 nodes."""
     rng = np.random.default_rng(seed)

@@ -46,6 +46,11 @@ WORKLOADS = {
                             desc="darcy2d 100x100 (n=10000), %d systems, a=exp(cos t G1 + sin t G2), G1, G2 "
                                  "GRF ell=0.1 sigma=1, t ~ U[0, 2pi), f=1, Jacobi, GCRO-DR m=40 k=20, "
                                  "mixed precision, tol 1e-8"),
+    "darcy256_circle": dict(kind="darcy2d", family="circle", nside=256, nsys=200, ell=0.1, sigma=1.0, seed=10,
+                            m=40, k=20, precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5,
+                            desc="darcy2d 256x256 (n=65536), %d systems, a=exp(cos t G1 + sin t G2), G1, G2 "
+                                 "GRF ell=0.1 sigma=1, t ~ U[0, 2pi), f=1, Jacobi, GCRO-DR m=40 k=20, "
+                                 "mixed precision, tol 1e-8"),
     # Poisson with Dirichlet data and forcing from truncated Chebyshev series (App. E);
     # one fixed matrix, the right-hand sides differ; sort keys = the 96 coefficients
     "poisson_cheb256": dict(kind="poisson2d", nside=256, nsys=200, ncoef=8, decay=0.6, seed=7, m=40, k=20,
@@ -732,7 +737,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="skr", choices=["skr", "reference"])
     ap.add_argument("--workload", default="darcy256", choices=sorted(WORKLOADS),
-                    help="darcy256 (the headline workload), darcy100, darcy100_circle, helmholtz100 or "
+                    help="darcy256 (the headline workload), darcy100, darcy100_circle, darcy256_circle, helmholtz100 or "
                          "poisson_cheb256")
     ap.add_argument("--warm-start", action="store_true", help="x_0 = previous solution of the chain")
     ap.add_argument("--no-sort", action="store_true", help="solve in input order (ablation)")

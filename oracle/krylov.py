@@ -92,6 +92,16 @@ def select_smallest(theta, Z, k):
     return np.stack(cols, axis=1)
 
 
+def round32(a):
+    """Round to the nearest float32 and back: the FP32-emulating variant's
+    rounding after every vector-level operation."""
+    return np.asarray(a, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def _same(a):
+    return a
+
+
 def lsq_residual(Hbar, beta):
     """min_y || beta e1 - Hbar y || and its minimiser."""
     rhs = np.zeros(Hbar.shape[0])
@@ -100,40 +110,42 @@ def lsq_residual(Hbar, beta):
     return np.linalg.norm(rhs - Hbar @ y), y
 
 
-def arnoldi(op, r, steps, C, tol_abs):
+def arnoldi(op, r, steps, C, tol_abs, rnd=None):
     """Arnoldi with the operator (I - C C^T) op, v1 = r/||r|| (Eq. 2-4).
 
     Returns dict(V n x (j+1), Hbar (j+1) x j, B kc x j, j, early, matvecs).
     Stops early when the GMRES least-squares residual on Hbar is <= tol_abs
     (for GCRO-DR this equals the residual of the full LSQ problem, because
-    the D_k block of G can always cancel the C rows).
+    the D_k block of G can always cancel the C rows).  rnd (default: none)
+    rounds the result of every vector operation and reduction.
     """
+    rnd = rnd or _same
     n = r.size
-    beta = np.linalg.norm(r)
+    beta = float(rnd(np.linalg.norm(r)))
     kc = 0 if C is None else C.shape[1]
     V = np.zeros((n, steps + 1))
     H = np.zeros((steps + 1, steps))
     B = np.zeros((kc, steps))
-    V[:, 0] = r / beta
+    V[:, 0] = rnd(r / beta)
     j_done = steps
     early = False
     for j in range(steps):
-        w = op(V[:, j])
+        w = rnd(op(V[:, j]))
         nrm_in = np.linalg.norm(w)
         for _ in range(2):
             if kc:
-                c = C.T @ w
+                c = rnd(C.T @ w)
                 B[:, j] += c
-                w = w - C @ c
+                w = rnd(w - C @ c)
             for i in range(j + 1):
-                hij = V[:, i] @ w
+                hij = float(rnd(V[:, i] @ w))
                 H[i, j] += hij
-                w = w - hij * V[:, i]
-        hn = np.linalg.norm(w)
+                w = rnd(w - hij * V[:, i])
+        hn = float(rnd(np.linalg.norm(w)))
         H[j + 1, j] = hn
         breakdown = hn <= 1e-14 * max(nrm_in, 1e-300)
         if not breakdown:
-            V[:, j + 1] = w / hn
+            V[:, j + 1] = rnd(w / hn)
         res, _ = lsq_residual(H[: j + 2, : j + 1], beta)
         if res <= tol_abs or breakdown:
             j_done = j + 1
@@ -187,25 +199,29 @@ class RecycleState:
         return 0 if self.U is None else self.U.shape[1]
 
 
-def refresh(op, state):
+def refresh(op, state, rnd=None):
     """App. B.1: [Q, R] = qr(A_new U_old); C = Q; U = U_old R^-1.  Returns matvecs used."""
+    rnd = rnd or _same
     if state.U is None or state.k == 0:
         return 0
-    AY = np.stack([op(state.U[:, i]) for i in range(state.k)], axis=1)
+    AY = np.stack([rnd(op(state.U[:, i])) for i in range(state.k)], axis=1)
     Q, R = qr_pos(AY)
-    state.C = Q
-    state.U = np.linalg.solve(R.T, state.U.T).T   # U_old R^-1
+    state.C = rnd(Q)
+    state.U = rnd(np.linalg.solve(R.T, state.U.T).T)   # U_old R^-1
     return state.k
 
 
-def gcrodr_solve(op, r0, m, k, tol_abs, state, max_steps=10**4, stats=None):
+def gcrodr_solve(op, r0, m, k, tol_abs, state, max_steps=10**4, stats=None, rnd=None):
     """Solve op(d) = r0 from d = 0 by GCRO-DR(m, k) (Algorithm 2).
 
     op        callable v -> A_hat v (the right-preconditioned operator)
     state     RecycleState, updated in place (U, C valid for op on return)
     tol_abs   stop when ||r|| <= tol_abs
+    rnd       rounding after every vector operation (default: none); the
+              small dense step (least squares, eigenproblem, QR) stays FP64
     Returns (d, r); `stats` (dict) accumulates steps, cycles, matvecs.
     """
+    rnd = rnd or _same
     if stats is None:
         stats = {}
     for key in ("steps", "cycles", "matvecs"):
@@ -213,42 +229,42 @@ def gcrodr_solve(op, r0, m, k, tol_abs, state, max_steps=10**4, stats=None):
     history = stats.setdefault("history", [])
     n = r0.size
     d = np.zeros(n)
-    r = np.array(r0, dtype=np.float64, copy=True)
+    r = rnd(np.array(r0, dtype=np.float64, copy=True))
     if state.U is not None and state.k > 0:
-        z = state.C.T @ r                       # x1 = x0 + U C^T r0
-        d = d + state.U @ z
-        r = r - state.C @ z                     # r1 = r0 - C C^T r0
+        z = rnd(state.C.T @ r)                  # x1 = x0 + U C^T r0
+        d = rnd(d + state.U @ z)
+        r = rnd(r - state.C @ z)                # r1 = r0 - C C^T r0
     while np.linalg.norm(r) > tol_abs and stats["steps"] < max_steps:
         kc = state.k
         budget = max_steps - stats["steps"]
         if kc == 0:
             # GMRES cycle of m steps (the "else" branch of Algorithm 2)
-            ar = arnoldi(op, r, min(m, budget), None, tol_abs)
+            ar = arnoldi(op, r, min(m, budget), None, tol_abs, rnd)
             j = ar["j"]
             stats["steps"] += j
             stats["matvecs"] += j
             stats["cycles"] += 1
             Hbar, V = ar["Hbar"], ar["V"]
             _, y = lsq_residual(Hbar, ar["beta"])
-            d = d + V[:, :j] @ y
-            r = r - V @ (Hbar @ y)
+            d = rnd(d + V[:, :j] @ y)
+            r = rnd(r - V @ (Hbar @ y))
             if k > 0 and not ar["early"] and j == m:
                 P, _ = harmonic_ritz_first(Hbar, k)
                 if P.shape[1] > 0:
                     Yt = V[:, :m] @ P
                     Q, R = qr_pos(Hbar @ P)
-                    state.C = V @ Q
-                    state.U = np.linalg.solve(R.T, Yt.T).T
+                    state.C = rnd(V @ Q)
+                    state.U = rnd(np.linalg.solve(R.T, Yt.T).T)
         else:
             # re-apply the projection of Algorithm 2's first step (x += U C^T r,
             # r -= C C^T r): a no-op in exact arithmetic (r is orthogonal to C
             # after every cycle), it keeps v_1 = r/||r|| orthogonal to C in
             # floating point once ||r|| has dropped far below its earlier values
-            z = state.C.T @ r
-            d = d + state.U @ z
-            r = r - state.C @ z
+            z = rnd(state.C.T @ r)
+            d = rnd(d + state.U @ z)
+            r = rnd(r - state.C @ z)
             steps = min(m - kc, budget)
-            ar = arnoldi(op, r, steps, state.C, tol_abs)
+            ar = arnoldi(op, r, steps, state.C, tol_abs, rnd)
             j = ar["j"]
             stats["steps"] += j
             stats["matvecs"] += j
@@ -262,15 +278,15 @@ def gcrodr_solve(op, r0, m, k, tol_abs, state, max_steps=10**4, stats=None):
             G[:kc, :kc] = np.diag(Dk)
             G[:kc, kc:] = ar["B"]
             G[kc:, kc:] = ar["Hbar"]
-            y = np.linalg.lstsq(G, What.T @ r, rcond=None)[0]
-            d = d + Vhat @ y
-            r = r - What @ (G @ y)
+            y = np.linalg.lstsq(G, rnd(What.T @ r), rcond=None)[0]
+            d = rnd(d + Vhat @ y)
+            r = rnd(r - What @ (G @ y))
             if not ar["early"] and j == m - kc:
                 P, _ = harmonic_ritz_general(G, What, Vhat, k)
                 if P.shape[1] > 0:
                     Yt = Vhat @ P
                     Q, R = qr_pos(G @ P)
-                    state.C = What @ Q
-                    state.U = np.linalg.solve(R.T, Yt.T).T
+                    state.C = rnd(What @ Q)
+                    state.U = rnd(np.linalg.solve(R.T, Yt.T).T)
         history.append(np.linalg.norm(r))
     return d, r

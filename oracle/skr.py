@@ -13,13 +13,17 @@ For the "fp64" form the inner target is tol ||b|| (one pass normally
 suffices; the loop only confirms it on the true residual).  For the
 "mixed" form the inner target is max(inner_tol ||r||, tol ||b||), the
 structure the GPU path runs with single-precision inner solves; the oracle
-runs that same structure in float64.
+runs that same structure in float64.  The "fp32-emulated" form runs the
+mixed structure with every vector of the inner solves (and the carried
+U_k, C_k) rounded to float32 after each vector operation, the small dense
+step, x, the true residual and the refinement staying float64: it states
+the error the mixed form should show, without the GPU's summation orders.
 """
 import numpy as np
 
 from . import assembly
 from .precond import RightPreconditioner
-from .krylov import RecycleState, refresh, gcrodr_solve, one_sided_distance
+from .krylov import RecycleState, refresh, gcrodr_solve, one_sided_distance, round32
 
 
 def grid_of(system):
@@ -66,13 +70,16 @@ def solve_system(A, b, precond, m, k, tol, state, precision="fp64", inner_tol=1e
     relres, converged).  `steps` counts Arnoldi steps (one operator
     application each); `matvecs` also counts the k products of the refresh.
     """
+    if precision not in ("fp64", "mixed", "fp32-emulated"):
+        raise ValueError(precision)
+    rnd = round32 if precision == "fp32-emulated" else None
     M = RightPreconditioner(A, precond, grid, blocks=pc_blocks)
 
     def op(v):
         return A @ M.apply(v)
 
     stats = dict(steps=0, cycles=0, matvecs=0, refinements=0, delta=-1.0)
-    stats["matvecs"] += refresh(op, state)
+    stats["matvecs"] += refresh(op, state, rnd)
     C_in = None if state.C is None else state.C.copy()
     bnorm = np.linalg.norm(b)
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
@@ -88,7 +95,7 @@ def solve_system(A, b, precond, m, k, tol, state, precision="fp64", inner_tol=1e
             tol_abs = tol * bnorm
         else:
             tol_abs = max(inner_tol * rn, tol * bnorm)
-        d, _ = gcrodr_solve(op, r, m, k, tol_abs, state, max_steps, stats)
+        d, _ = gcrodr_solve(op, r, m, k, tol_abs, state, max_steps, stats, rnd=rnd)
         x = x + M.apply(d)
         stats["refinements"] += 1
     relres = np.linalg.norm(b - A @ x) / bnorm

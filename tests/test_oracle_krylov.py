@@ -520,3 +520,38 @@ def test_recycled_cycle_selection_spans_the_smallest_closed_form_eigenvectors():
     P, _ = krylov.harmonic_ritz_general(G, What, Vhat, k)
     assert P.shape[1] == k
     assert sla.subspace_angles(Vhat @ P, E).max() < 1e-6
+
+
+# ---------------------------------------------------------------- FP32-emulating variant (mixed-form error)
+
+def test_round32_is_float32_rounding():
+    assert krylov.round32(1.0 + 2.0 ** -30) == 1.0                     # below float32's 24-bit mantissa
+    assert krylov.round32(1.0 + 2.0 ** -20) == 1.0 + 2.0 ** -20
+    assert krylov.round32(1.0 + 3 * 2.0 ** -24) == 1.0 + 2.0 ** -22   # nearest, ties to even
+    v = np.random.default_rng(0).standard_normal(50)
+    assert np.array_equal(krylov.round32(v), v.astype(np.float32).astype(np.float64))
+
+
+def test_emulated_arnoldi_keeps_float32_vectors():
+    A, b = _darcy(8, seed=5)
+    ar = krylov.arnoldi(lambda v: A @ v, b, 10, None, 0.0, rnd=krylov.round32)
+    V = ar["V"]
+    assert np.array_equal(krylov.round32(V), V)
+    # orthonormal to float32 accuracy, not to float64's
+    err = np.abs(V.T @ V - np.eye(V.shape[1])).max()
+    assert 1e-9 < err < 1e-5
+
+
+def test_fp32_emulated_sequence_stays_within_the_mixed_form_bound():
+    L = darcy2d_sequence(24, 4, 0.15, seed=23)
+    order = list(range(4))
+    sysd = [dict(kind="darcy2d", loga=l) for l in L]
+    x64, _ = skr.solve_sequence(sysd, order, "jacobi", 30, 10, 1e-8, precision="fp64")
+    xm, _ = skr.solve_sequence(sysd, order, "jacobi", 30, 10, 1e-8, precision="mixed")
+    xe, ie = skr.solve_sequence(sysd, order, "jacobi", 30, 10, 1e-8, precision="fp32-emulated")
+    for i in range(4):
+        A, b = assembly.darcy2d(L[i])
+        assert ie[i]["converged"] and ie[i]["refinements"] >= 2       # FP32 inner solves need refinement
+        assert np.linalg.norm(b - A @ xe[i]) <= 1e-8 * np.linalg.norm(b)
+        assert np.linalg.norm(xe[i] - x64[i]) <= 1e-6 * np.linalg.norm(x64[i])
+        assert not np.array_equal(xe[i], xm[i])                        # the rounding is active

@@ -529,6 +529,26 @@ class OracleChains:
             p.join(timeout=30)
 
 
+def _cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_baseline(budget_s, W, warm=False):
     """One bounded oracle sample beside the GPU line, on every host core."""
     ch = OracleChains(W, warm)
@@ -537,6 +557,7 @@ def cpu_baseline(budget_s, W, warm=False):
     finally:
         ch.close()
     return {"value": round(v, 4), "unit": "systems/s", "cores": ch.cores, "kind": "oracle",
+            "cpu": _cpu_model(),
             "sample": "%d systems in %.0f s on %d cores, one sorted chain segment per core (the paper's "
                       "decomposition); sort of all %d amortised; numpy/scipy FP64, BLAS threads = 1 per core"
                       % (done, budget_s, ch.cores, W["nsys"])}
@@ -560,7 +581,7 @@ def run_reference(args):
     finally:
         ch.close()
     value = sum(vals) / len(vals)
-    cb = {"value": round(value, 4), "unit": "systems/s", "cores": ch.cores, "kind": "oracle",
+    cb = {"value": round(value, 4), "unit": "systems/s", "cores": ch.cores, "kind": "oracle", "cpu": _cpu_model(),
           "sample": "%d timed samples of %.0f s, one sorted chain segment per core on %d cores (the paper's "
                     "decomposition; %s systems per sample, after %d untimed samples; sort of all %d "
                     "amortised), numpy/scipy FP64, BLAS threads = 1 per core"
@@ -726,6 +747,7 @@ def run_sort_only(args):
         osort.grouped_sort(Kh[:ns], G)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": round(ns / dt, 1), "unit": "systems/s", "cores": 1, "kind": "oracle",
+                                "cpu": _cpu_model(),
                                 "sample": "the first %d keys, grouped sort with the same G, numpy FP64, one core" % ns}
     print(json.dumps(line), flush=True)
 

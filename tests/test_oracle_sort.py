@@ -198,3 +198,16 @@ def test_sort_walks_a_closed_curve_of_fields():
 
     assert tour(order) <= 4 * np.pi
     assert tour(list(range(40))) > 3 * tour(order)
+
+
+def test_convdiff_keys_are_standardised():
+    # the z-scores have mean 0 and variance 1 under the drawing distributions,
+    # so nu (range 0.09) weighs as much as beta (range 100) in the distance
+    from workloads import convdiff2d_sequence, convdiff_keys
+    nu, beta, _ = convdiff2d_sequence(4, 20000, seed=11)
+    K = convdiff_keys(nu, beta)
+    np.testing.assert_allclose(K.mean(axis=0), 0.0, atol=0.03)
+    np.testing.assert_allclose(K.std(axis=0), 1.0, atol=0.03)
+    # closed form at the ends of the nu range: +-sqrt(3)
+    K2 = convdiff_keys(np.array([0.01, 0.1]), np.zeros((2, 2)))
+    np.testing.assert_allclose(K2[:, 0], [-np.sqrt(3.0), np.sqrt(3.0)], rtol=1e-12)

@@ -12,6 +12,7 @@ from .sequences import (
     darcy2d_circle_sequence,
     darcy3d_sequence,
     convdiff2d_sequence,
+    convdiff_keys,
     helmholtz2d_sequence,
     chebyshev_poisson_sequence,
     batched_chains,
@@ -25,6 +26,7 @@ __all__ = [
     "darcy2d_circle_sequence",
     "darcy3d_sequence",
     "convdiff2d_sequence",
+    "convdiff_keys",
     "helmholtz2d_sequence",
     "chebyshev_poisson_sequence",
     "batched_chains",

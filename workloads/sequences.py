@@ -72,6 +72,21 @@ def convdiff2d_sequence(nside, nsys, seed=0, nu_range=(0.01, 0.1), beta_max=50.0
     return nu, beta, f
 
 
+def convdiff_keys(nu, beta, nu_range=(0.01, 0.1), beta_max=50.0):
+    """Sort / routing keys of convection-diffusion problems: (nu, beta_x,
+    beta_y) z-scored by the distributions convdiff2d_sequence draws them from
+    (nu uniform on nu_range; beta = U[0, beta_max] (cos phi, sin phi), whose
+    components have mean 0 and standard deviation beta_max / sqrt(6)), so
+    that no parameter dominates the distance by its units.  Returns [nsys, 3].
+    """
+    lo, hi = nu_range
+    nu_mean, nu_sd = 0.5 * (lo + hi), (hi - lo) / np.sqrt(12.0)
+    b_sd = beta_max / np.sqrt(6.0)
+    beta = np.asarray(beta, dtype=np.float64)
+    return np.stack([(np.asarray(nu, dtype=np.float64) - nu_mean) / nu_sd, beta[:, 0] / b_sd, beta[:, 1] / b_sd],
+                    axis=1)
+
+
 def helmholtz2d_sequence(nside, nsys, kbar, ell, sigma=1.0, spread=0.2, seed=0):
     """N Helmholtz problems -lap u - k^2 u = 1 on an nside x nside interior grid.
 

@@ -22,7 +22,15 @@ Readings where the paper is silent:
 Pins: the 2x2 worked example of Sec. 3.1 (Poisson, h = 1) and its Darcy
 negation for a = 1; O(h^2) convergence to a manufactured solution; the
 closed-form eigenvalues of the constant-coefficient Laplacian, shifted by
--k^2 for the Helmholtz operator.
+-k^2 for the Helmholtz operator.  Convection-diffusion: A u equals
+beta . grad u exactly on linear u and the closed-form upwind value on
+quadratic u (all four sign quadrants of beta), and first-order convergence
+to a manufactured solution.  3D Darcy: every entry of a 3 x 4 x 5 grid's
+matrix against face means computed node by node, and O(h^2) convergence
+with an axis-anisotropic coefficient.  The tests also plant plausible
+mistakes in copies of this file (upwind scale beta/(2h), halved diffusion,
+upwind side swapped, harmonic face means, swapped strides, an axis's h
+taken from another axis) and check that the pins reject each one.
 """
 import numpy as np
 import scipy.sparse as sp

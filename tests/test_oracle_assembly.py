@@ -179,3 +179,189 @@ def test_poisson_dirichlet_exact_on_a_quadratic():
     A, b = assembly.poisson2d_dirichlet(f, u(0.0, y), u(1.0, y), u(x, 0.0), u(x, 1.0))
     xs = spla.spsolve(A.tocsc(), b)
     np.testing.assert_allclose(xs, u(X, Y).ravel(), rtol=0, atol=1e-11)
+
+
+# ------------------------------------------------------------------ convection-diffusion: upwind scale and direction
+#
+# These pins hold the convection-diffusion assembly to closed forms that a
+# wrong diffusion scale, a wrong upwind scale (beta/(2h) instead of beta/h) or
+# an upwind taken from the wrong side each break.
+
+def _convdiff_interior_residual(conv, nu, beta, M, u):
+    """(A u)_p at the rows whose four neighbours are all unknowns of an M x M
+    grid, u evaluated at the nodes (i+1)h, (j+1)h with h = 1/(M+1); no
+    Dirichlet coupling is dropped on those rows, so A u is the full stencil."""
+    h = 1.0 / (M + 1)
+    x = np.arange(1, M + 1) * h
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    A, _ = conv(nu, beta, M)
+    r = (A @ u(X, Y).ravel()).reshape(M, M)
+    return r[1:-1, 1:-1], X[1:-1, 1:-1], Y[1:-1, 1:-1], h
+
+
+def _check_convdiff_closed_forms(conv):
+    """Both closed forms below, for beta in all four sign quadrants."""
+    nu, M = 0.037, 11
+    for beta in ((23.0, 7.5), (-23.0, 7.5), (23.0, -7.5), (-31.0, -4.0)):
+        # linear u: the 5-point Laplacian and one-sided differences are exact,
+        # so every full row gives beta . grad u = beta_x c1 + beta_y c2
+        c0, c1, c2 = 0.3, 1.7, -2.9
+        r, _, _, _ = _convdiff_interior_residual(conv, nu, beta, M, lambda X, Y: c0 + c1 * X + c2 * Y)
+        np.testing.assert_allclose(r, beta[0] * c1 + beta[1] * c2, rtol=0, atol=1e-9)
+        # quadratic u = a x^2 + b y^2: -nu lap_h u = -2 nu (a + b) exactly, and
+        # the upwind difference of x^2 on the side beta points from is
+        # 2x - sign(beta_x) h (similarly in y)
+        qa, qb = 1.3, -0.8
+        r, X, Y, h = _convdiff_interior_residual(conv, nu, beta, M, lambda X, Y: qa * X**2 + qb * Y**2)
+        sx, sy = np.sign(beta[0]), np.sign(beta[1])
+        want = (-2.0 * nu * (qa + qb) + beta[0] * qa * (2.0 * X - sx * h) + beta[1] * qb * (2.0 * Y - sy * h))
+        np.testing.assert_allclose(r, want, rtol=0, atol=1e-9)
+
+
+def _convdiff_manufactured_errors(conv, sizes=(15, 31)):
+    """Max nodal error against u = sin(pi x) sin(pi y) (zero on the boundary)
+    with f = -nu lap u + beta . grad u, on the given grids."""
+    nu, beta = 0.05, (20.0, -12.0)
+    errs = []
+    for N in sizes:
+        h = 1.0 / (N + 1)
+        x = np.arange(1, N + 1) * h
+        X, Y = np.meshgrid(x, x, indexing="ij")
+        u = np.sin(np.pi * X) * np.sin(np.pi * Y)
+        f = (2.0 * np.pi**2 * nu * u + beta[0] * np.pi * np.cos(np.pi * X) * np.sin(np.pi * Y)
+             + beta[1] * np.pi * np.sin(np.pi * X) * np.cos(np.pi * Y))
+        A, b = conv(nu, beta, N, rhs=f.ravel())
+        errs.append(np.abs(spla.spsolve(A.tocsc(), b) - u.ravel()).max())
+    return errs
+
+
+def _check_convdiff_first_order(conv):
+    e1, e2 = _convdiff_manufactured_errors(conv)
+    # first-order upwinding: the error halves with h (measured 0.249 -> 0.132)
+    assert e2 < 0.2 and 1.7 < e1 / e2 < 2.3, (e1, e2)
+
+
+def test_convdiff_exact_on_linear_and_quadratic_fields():
+    _check_convdiff_closed_forms(assembly.convdiff2d)
+
+
+def test_convdiff_manufactured_solution_first_order():
+    _check_convdiff_first_order(assembly.convdiff2d)
+
+
+# ------------------------------------------------------------------ 3D Darcy: face means, axis order, O(h^2)
+
+def _check_darcy3d_row_by_hand(d3):
+    """Every entry of every row of a 3 x 4 x 5 grid (three distinct sides, so
+    three distinct h and strides) against face means computed node by node."""
+    rng = np.random.default_rng(11)
+    nx, ny, nz = 3, 4, 5
+    loga = rng.standard_normal((nx + 2, ny + 2, nz + 2))
+    a = np.exp(loga)
+    hs = (1.0 / (nx + 1), 1.0 / (ny + 1), 1.0 / (nz + 1))
+    A, b = d3(loga)
+    D = A.toarray()
+    n = nx * ny * nz
+    want = np.zeros((n, n))
+    for i in range(nx):
+        for j in range(ny):
+            for l in range(nz):
+                p = (i * ny + j) * nz + l
+                c = a[i + 1, j + 1, l + 1]
+                for (di, dj, dl), hh in (((-1, 0, 0), hs[0]), ((1, 0, 0), hs[0]), ((0, -1, 0), hs[1]),
+                                         ((0, 1, 0), hs[1]), ((0, 0, -1), hs[2]), ((0, 0, 1), hs[2])):
+                    face = 0.5 * (c + a[i + 1 + di, j + 1 + dj, l + 1 + dl]) / hh**2
+                    want[p, p] += face
+                    ii, jj, ll = i + di, j + dj, l + dl
+                    if 0 <= ii < nx and 0 <= jj < ny and 0 <= ll < nz:
+                        want[p, (ii * ny + jj) * nz + ll] = -face
+    np.testing.assert_allclose(D, want, rtol=1e-14, atol=0.0)
+    np.testing.assert_array_equal(b, np.ones(n))
+
+
+def _darcy3d_manufactured_errors(d3, sizes=(7, 15)):
+    """Max nodal error for u = sin(pi x) sin(2 pi y) sin(pi z) and the smooth,
+    axis-anisotropic a = exp(0.6 x - 0.3 y + 0.9 z + 0.4 x y); f =
+    -div(a grad u) in closed form."""
+    errs = []
+    for N in sizes:
+        nx, ny, nz = N, N + 1, N + 2
+        g = [np.arange(0, s + 2) / (s + 1.0) for s in (nx, ny, nz)]
+        X, Y, Z = np.meshgrid(*g, indexing="ij")
+        la = 0.6 * X - 0.3 * Y + 0.9 * Z + 0.4 * X * Y
+        a = np.exp(la)
+        ax, ay, az = a * (0.6 + 0.4 * Y), a * (-0.3 + 0.4 * X), a * 0.9
+        sx, sy, sz = np.sin(np.pi * X), np.sin(2 * np.pi * Y), np.sin(np.pi * Z)
+        cx, cy, cz = np.cos(np.pi * X), np.cos(2 * np.pi * Y), np.cos(np.pi * Z)
+        u = sx * sy * sz
+        ux, uy, uz = np.pi * cx * sy * sz, 2 * np.pi * sx * cy * sz, np.pi * sx * sy * cz
+        lap = -(np.pi**2 + 4 * np.pi**2 + np.pi**2) * u
+        f = -(a * lap + ax * ux + ay * uy + az * uz)
+        inner = (slice(1, -1),) * 3
+        A, b = d3(la, rhs=f[inner].ravel())
+        errs.append(np.abs(spla.spsolve(A.tocsc(), b) - u[inner].ravel()).max())
+    return errs
+
+
+def _check_darcy3d_second_order(d3):
+    e1, e2 = _darcy3d_manufactured_errors(d3)
+    assert e2 < 0.05 and 3.3 < e1 / e2 < 4.7, (e1, e2)
+
+
+def test_darcy3d_rows_by_hand_on_a_non_cubic_grid():
+    _check_darcy3d_row_by_hand(assembly.darcy3d)
+
+
+def test_darcy3d_manufactured_solution_second_order():
+    _check_darcy3d_second_order(assembly.darcy3d)
+
+
+# ------------------------------------------------------------------ the pins catch planted mistakes
+#
+# Each mutant is the oracle's own source with one plausible mistake planted
+# (text substitution, then exec); the pins above must reject every one.
+
+def _mutant(func_name, old, new):
+    import inspect
+    src = inspect.getsource(assembly)
+    assert src.count(old) >= 1, old
+    ns = {}
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), ns)
+    return ns[func_name]
+
+
+def _fails(check, fn):
+    """True when the pin rejects fn: an assertion fails, or the mutant's
+    matrix cannot even be built (an index outside the grid)."""
+    try:
+        check(fn)
+    except (AssertionError, ValueError, IndexError):
+        return True
+    return False
+
+
+def test_convdiff_pins_reject_planted_mistakes():
+    mutants = [
+        _mutant("convdiff2d", "cxm = -d - max(bx, 0.0) / hh", "cxm = -d - max(bx, 0.0) / (2.0 * hh)"),
+        _mutant("convdiff2d", "cpp = 4.0 * d + abs(bx) / hh", "cpp = 4.0 * d + abs(bx) / (2.0 * hh)"),
+        _mutant("convdiff2d", "d = nu / hh**2", "d = 0.5 * nu / hh**2"),
+        # upwind from the wrong side in x: the diagonal stays |bx|/h, the
+        # coupling moves to the downstream neighbour
+        _mutant("convdiff2d", "cxm = -d - max(bx, 0.0) / hh\n    cxp = -d + min(bx, 0.0) / hh",
+                "cxm = -d + min(bx, 0.0) / hh\n    cxp = -d - max(bx, 0.0) / hh"),
+    ]
+    for mu in mutants:
+        assert _fails(_check_convdiff_closed_forms, mu) or _fails(_check_convdiff_first_order, mu)
+
+
+def test_darcy3d_pins_reject_planted_mistakes():
+    harmonic = _mutant("darcy3d", "f = 0.5 * (c + a[tuple(nb)]) / hs[ax] ** 2",
+                       "f = 2.0 * c * a[tuple(nb)] / (c + a[tuple(nb)]) / hs[ax] ** 2")
+    swapped = _mutant("darcy3d", "strides = (ny * nz, nz, 1)", "strides = (nz, ny * nz, 1)")
+    wrong_h = _mutant("darcy3d", "f = 0.5 * (c + a[tuple(nb)]) / hs[ax] ** 2",
+                      "f = 0.5 * (c + a[tuple(nb)]) / hs[2 - ax] ** 2")
+    for mu in (harmonic, swapped, wrong_h):
+        assert _fails(_check_darcy3d_row_by_hand, mu)
+    # the axis mistakes also break second-order convergence on the anisotropic field
+    for mu in (swapped, wrong_h):
+        assert _fails(_check_darcy3d_second_order, mu)

@@ -29,11 +29,33 @@ sys.path.insert(0, ROOT)
 
 METRIC = "systems/s to rel-res 1e-8, SKR vs plain GMRES on 1 GB300; HBM GB/s frac; p99"
 WORKLOADS = {
-    # the headline workload: Darcy on 256^2 (n = 65,536), 200 systems
+    # Darcy 32^2, 20 systems, no preconditioner, FP64 throughout: the small
+    # case the oracle finishes in seconds; one chain, one CTA
+    "darcy32_fp64": dict(kind="darcy2d", nside=32, nsys=20, ell=0.2, sigma=1.0, seed=1, m=30, k=10,
+                         precond="none", precision="fp64", tol=1e-8, inner_tol=1e-5, chains=1, cluster_size=1,
+                         desc="darcy2d 32x32 (n=1024), %d systems, a=exp(GRF ell=0.2 sigma=1), f=1, "
+                              "no preconditioner, GCRO-DR m=30 k=10, FP64, tol 1e-8"),
+    # Darcy on 256^2 (n = 65,536), 200 systems
     "darcy256": dict(kind="darcy2d", nside=256, nsys=200, ell=0.1, sigma=1.0, seed=2, m=40, k=20,
-                     precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5,
+                     precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5, chains=76, cluster_size=2,
                      desc="darcy2d 256x256 (n=65536), %d systems, a=exp(GRF ell=0.1 sigma=1), f=1, "
                           "Jacobi, GCRO-DR m=40 k=20, mixed precision, tol 1e-8"),
+    # convection-diffusion on 512^2 (n = 262,144), 500 systems, red-black ILU(0);
+    # sort keys (nu, beta_x, beta_y) z-scored by their drawing distributions
+    "convdiff512_ilu": dict(kind="convdiff2d", nside=512, nsys=500, seed=3, m=40, k=20,
+                            precond="ilu0", precision="mixed", tol=1e-8, inner_tol=1e-5, chains=38, cluster_size=0,
+                            desc="convdiff2d 512x512 (n=262144), %d systems, -nu lap u + beta.grad u = f "
+                                 "(first-order upwind), nu~U[0.01,0.1], beta=U[0,50](cos phi, sin phi), "
+                                 "f=GRF(ell=0.1 sigma=1), red-black ILU(0), GCRO-DR m=40 k=20, mixed precision, "
+                                 "tol 1e-8; sort keys (nu, beta) z-scored"),
+    # 64 independent chains of 50 Darcy systems, grid side per chain from
+    # {64, 128, 192, 256, 384}, ell per chain ~ U[0.05, 0.3]; each chain sorted on its own
+    "batched64x50": dict(kind="batched", nchains=64, chain_len=50, nsys=3200, seed=4, m=40, k=20,
+                         sides=(64, 128, 192, 256, 384), ell_range=(0.05, 0.3), sigma=1.0,
+                         precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5, cluster_size=0,
+                         desc="batched Darcy: %d systems in 64 independent sorted chains of 50, side per chain "
+                              "from {64,128,192,256,384}, a=exp(GRF ell~U[0.05,0.3] sigma=1), f=1, Jacobi, "
+                              "GCRO-DR m=40 k=20, mixed precision, tol 1e-8"),
     # Darcy at the ablation's matrix size (10^4 unknowns, 100^2)
     "darcy100": dict(kind="darcy2d", nside=100, nsys=200, ell=0.1, sigma=1.0, seed=8, m=40, k=20,
                      precond="jacobi", precision="mixed", tol=1e-8, inner_tol=1e-5,
@@ -66,6 +88,7 @@ WORKLOADS = {
                          desc="helmholtz2d 100x100 (n=10000), %d systems, -lap u - k^2 u = 1, "
                               "k=10 exp(0.2 GRF(ell=0.1 sigma=1)), Jacobi, GCRO-DR m=40 k=20, mixed precision, tol 1e-8"),
 }
+DEFAULT_WORKLOAD = "darcy256"
 
 
 PRECOND_NAMES = {"none": "no preconditioner", "jacobi": "Jacobi", "ssor": "SSOR", "ilu0": "red-black ILU(0)",
@@ -87,7 +110,7 @@ def _workload(args):
 
 
 def _inputs(W, nsys, seed):
-    """Seeded inputs of nsys systems: (sort keys [nsys, p], per-system payload)."""
+    """Seeded inputs of nsys systems of a one-group workload: (sort keys [nsys, p], per-system payload)."""
     if W["kind"] == "darcy2d":
         from workloads import darcy2d_sequence, darcy2d_circle_sequence
         if W.get("family") == "circle":
@@ -99,29 +122,101 @@ def _inputs(W, nsys, seed):
         from workloads import helmholtz2d_sequence
         L = helmholtz2d_sequence(W["nside"], nsys, W["kbar"], W["ell"], W["sigma"], spread=W["spread"], seed=seed)
         return L.reshape(nsys, -1), [L[i] for i in range(nsys)]
+    if W["kind"] == "convdiff2d":
+        from workloads import convdiff2d_sequence, convdiff_keys
+        nu, beta, f = convdiff2d_sequence(W["nside"], nsys, seed=seed)
+        return convdiff_keys(nu, beta), [(float(nu[i]), (float(beta[i, 0]), float(beta[i, 1])), f[i])
+                                         for i in range(nsys)]
     from workloads import chebyshev_poisson_sequence
     K, F, G = chebyshev_poisson_sequence(W["nside"], nsys, W["ncoef"], W["decay"], seed=seed)
     return K, [(F[i], G[i]) for i in range(nsys)]
+
+
+class Batch:
+    """The inputs of one bench step.
+
+    groups   list of (first system, keys [count, p]): the systems of a group
+             are sorted together (Algorithm 1) and are consecutive here
+    chains   chains per group: a group's sorted order is cut into that many
+             contiguous chains (App. E.2.2)
+    payload  per-system arrays the system is built from
+    n        unknowns per system
+    """
+
+    def __init__(self, groups, chains, payload, n):
+        self.groups, self.chains, self.payload, self.n = groups, chains, payload, n
+
+    @property
+    def nsys(self):
+        return len(self.payload)
+
+    def chain_offsets(self):
+        offs = [0]
+        for (first, keys), q in zip(self.groups, self.chains):
+            c = keys.shape[0]
+            offs += [first + (i * c) // q for i in range(1, q + 1)]
+        return offs
+
+    def order(self, perms):
+        """The solve order from one permutation per group (group-local indices)."""
+        import numpy as np
+        return np.concatenate([first + np.asarray(pm, dtype=np.int64)
+                               for (first, _), pm in zip(self.groups, perms)]).astype(np.int32)
+
+
+def _batch(W, nsys, seed, nchains=None):
+    """Seeded inputs of one bench step of workload W (nsys systems)."""
+    if W["kind"] == "batched":
+        from workloads import batched_chains
+        clen = W["chain_len"]
+        nch = max(1, nsys // clen)
+        chains = batched_chains(nch, clen, sides=W["sides"], ell_range=W["ell_range"], sigma=W["sigma"],
+                                seed=seed)
+        groups, payload, n = [], [], []
+        for side, _, sub in chains:
+            groups.append((len(payload), sub.reshape(clen, -1)))
+            for i in range(clen):
+                payload.append(sub[i])
+                n.append(side * side)
+        return Batch(groups, [1] * len(groups), payload, n)
+    K, payload = _inputs(W, nsys, seed)
+    q = nchains if nchains is not None else W.get("chains", 76)
+    n = [W["nside"] ** 2] * nsys
+    return Batch([(0, K)], [max(1, min(q, nsys))], payload, n)
 
 
 def _to(payload, conv):
     return tuple(conv(a) for a in payload) if isinstance(payload, tuple) else conv(payload)
 
 
+def _to_payload(W, payload, conv):
+    """Move a system's arrays with conv (scalars stay)."""
+    if W["kind"] == "convdiff2d":
+        nu, beta, f = payload
+        return (nu, beta, conv(f))
+    return _to(payload, conv)
+
+
 def _system(skr, W, payload):
-    if W["kind"] == "darcy2d":
+    if W["kind"] in ("darcy2d", "batched"):
         return skr.darcy2d(payload)
     if W["kind"] == "helmholtz2d":
         return skr.helmholtz2d(payload)
+    if W["kind"] == "convdiff2d":
+        nu, beta, f = payload
+        return skr.convdiff2d(nu, beta, W["nside"], rhs=f)
     f, g = payload
     return skr.poisson2d(f, tuple(g[e] for e in range(4)))
 
 
 def _oracle_system(W, payload):
-    if W["kind"] == "darcy2d":
+    if W["kind"] in ("darcy2d", "batched"):
         return dict(kind="darcy2d", loga=payload)
     if W["kind"] == "helmholtz2d":
         return dict(kind="helmholtz2d", k=payload)
+    if W["kind"] == "convdiff2d":
+        nu, beta, f = payload
+        return dict(kind="convdiff2d", nu=nu, beta=beta, nside=W["nside"], rhs=f)
     f, g = payload
     return dict(kind="poisson2d", f=f, g=tuple(g))
 
@@ -131,7 +226,7 @@ def _oracle_system(W, payload):
 # only for the sources it was taken with (sha256 over the files that build
 # or launch the chain kernel and the public header, as computed by
 # _kernel_sources_sha256).
-TRAFFIC = {"sources_sha256": "e4f99adf54da31ed8a0398a2517ae455957ee793352754bb2fb493adc93c7385",
+TRAFFIC = {"workload": "darcy256", "sources_sha256": "e4f99adf54da31ed8a0398a2517ae455957ee793352754bb2fb493adc93c7385",
            "bytes_per_launch": 5.70e12 + 0.41003e12}
 
 
@@ -260,54 +355,55 @@ def run_gpu(args):
             dist.barrier()
 
     import paper_2401_09516_gb300 as skr
-    from paper_2401_09516_gb300 import _native
     W = _workload(args)
-    # weak scaling: every rank solves its own 200-system batch (independent chains)
-    Kh, payload = _inputs(W, max(W["nsys"], args.nsys), _rank_seed(W, rank))
-    N = args.nsys
-    Kh, payload = Kh[:N], payload[:N]
-    n = W["nside"] ** 2
-    P_dev = torch.tensor(Kh, device=dev)
-    if W["kind"] == "poisson2d":
-        pay_dev = [_to(p, lambda a: torch.tensor(a, device=dev)) for p in payload]
-    else:   # the keys are the fields themselves
-        pay_dev = [P_dev[i].view(*payload[i].shape) for i in range(N)]
-    systems = [_system(skr, W, p) for p in pay_dev]
-    x_dev = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(N)]
+    # weak scaling: every rank solves its own batch (independent chains)
+    N = args.nsys if args.nsys is not None else W["nsys"]
+    B = _batch(W, N, _rank_seed(W, rank), args.chains)
+    N = B.nsys
+    P_dev = [torch.tensor(keys, device=dev) for _, keys in B.groups]
+    if W["kind"] in ("darcy2d", "helmholtz2d", "batched"):
+        # the keys are the fields themselves: the systems read them in place
+        pay_dev = []
+        for (first, keys), Pg in zip(B.groups, P_dev):
+            pay_dev += [Pg[i].view(*B.payload[first + i].shape) for i in range(keys.shape[0])]
+    else:
+        pay_dev = [_to_payload(W, pl, lambda a: torch.tensor(a, device=dev)) for pl in B.payload]
+    systems = [_system(skr, W, pl) for pl in pay_dev]
+    x_dev = [torch.empty(B.n[i], dtype=torch.float64, device=dev) for i in range(N)]
     stream = torch.cuda.current_stream(dev)
-    nchains = args.chains if args.chains is not None else W.get("chains", 76)
-    cluster_size = args.cluster_size if args.cluster_size is not None else W.get("cluster_size", 2)
+    offs = B.chain_offsets()
+    cluster_size = args.cluster_size if args.cluster_size is not None else W.get("cluster_size", 0)
 
-    def opts(k):
+    def opts(k, precision=None, profile=0):
         return skr.skr_options_default(m=W["m"], k=k, tol=W["tol"], inner_tol=W["inner_tol"],
-                                       precond=W["precond"], pc_blocks=W["pc_blocks"], precision=W["precision"],
-                                       cluster_size=cluster_size, stream=stream,
-                                       warm_start=int(args.warm_start), diagnostics=int(args.diagnostics))
+                                       maxit=args.maxit, precond=W["precond"], pc_blocks=W["pc_blocks"],
+                                       precision=precision or W["precision"], cluster_size=cluster_size,
+                                       stream=stream, warm_start=int(args.warm_start),
+                                       diagnostics=int(args.diagnostics), profile=profile)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    sort_ev = []   # (start, end) events around each sort, timed steps only
+    sort_ev = []   # (start, end) events around the sorts of each step
+    ident = [np.arange(keys.shape[0]) for _, keys in B.groups]
 
-    def step(k, order=None):
-        if order is None:
-            order = np.arange(N, dtype=np.int32) if args.no_sort else None
-        if order is None:
+    def step(k, precision=None, profile=0):
+        if args.no_sort:
+            order = B.order(ident)
+        else:
             es0 = torch.cuda.Event(enable_timing=True)
             es1 = torch.cuda.Event(enable_timing=True)
             es0.record(stream)
-            perm = skr.skr_sort(P_dev, stream=stream)
+            perms = [skr.skr_sort(Pg, stream=stream) for Pg in P_dev]
             es1.record(stream)
             sort_ev.append((es0, es1))
-        else:
-            perm = order
-        permh = perm.cpu().numpy() if hasattr(perm, "cpu") else perm
-        _, res = skr.skr_solve_sequence(systems, order=permh, nchains=nchains, options=opts(k),
-                                        x_out=x_dev)
+            order = B.order([pm.cpu().numpy() for pm in perms])
+        _, res = skr.skr_solve_sequence(systems, order=order, chain_offsets=offs, nchains=len(offs) - 1,
+                                        options=opts(k, precision, profile), x_out=x_dev)
         return res, skr.skr_last_stats()
 
-    def timed(k, steps, warmup):
+    def timed(k, steps, warmup, precision=None):
         for _ in range(warmup):
-            step(k)
+            step(k, precision)
         torch.cuda.synchronize()
         times, stats, allres = [], [], []
         for _ in range(steps):
@@ -317,7 +413,7 @@ def run_gpu(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            res, st = step(k)
+            res, st = step(k, precision)
             e1.record(stream)
             torch.cuda.synchronize()
             barrier()
@@ -332,56 +428,79 @@ def run_gpu(args):
     clocks = sampler.stop()
     timed_sorts = sort_ev[-args.steps:] if (sort_ev and not args.no_sort) else []
     sort_ms = (sum(a.elapsed_time(b) for a, b in timed_sorts) / len(timed_sorts)) if timed_sorts else None
-    if args.gmres_steps > 0:
-        t_gm, st_gm, res_gm = timed(0, args.gmres_steps, 1)
 
     def agg(ms_list):
         return _agg_ms(ms_list, ws, dev)
 
+    def arm_summary(times, allres):
+        ms = agg(times)
+        last = allres[-1]
+        flags = [r["flag"] for r in last]
+        return {"value": round(N * ws / (ms / 1e3), 3), "ms_per_step": round(ms, 3), "steps_timed": len(times),
+                "avg_arnoldi_steps": round(sum(r["steps"] for r in last) / N, 1),
+                "converged": sum(1 for f in flags if f == 0), "not_converged": sum(1 for f in flags if f != 0),
+                "flags": sorted(set(flags)), "max_relres": max(r["relres"] for r in last)}
+
     ms_step = agg(t_skr)
     value = N * ws / (ms_step / 1e3)
+    gmres = None
     if args.gmres_steps > 0:
-        ms_gm = agg(t_gm)
-        gm_value = N * ws / (ms_gm / 1e3)
-        steps_gm = sum(r["steps"] for r in res_gm[-1]) / N
-        gm_flags = sorted({r["flag"] for r in res_gm[-1]})
-    else:
-        ms_gm = gm_value = steps_gm = None
-        gm_flags = []
+        t_gm, _, res_gm = timed(0, args.gmres_steps, 1)
+        gmres = arm_summary(t_gm, res_gm)
+        gmres["maxit"] = args.maxit
+    fp64 = None
+    if args.fp64_steps > 0 and W["precision"] == "mixed":
+        t_64, _, res_64 = timed(W["k"], args.fp64_steps, 1, precision="fp64")
+        fp64 = arm_summary(t_64, res_64)
+    # per-phase device time of one more (untimed) SKR step with the phase timers on
+    phases = None
+    if args.phases:
+        step(W["k"], profile=1)
+        torch.cuda.synchronize()
+        prof = skr.skr_last_profile()
+        tot = sum(prof.values())
+        phases = {"ms_per_system": {k: round(v / N, 3) for k, v in prof.items()},
+                  "share": {k: round(v / tot, 4) for k, v in prof.items()} if tot > 0 else None,
+                  "measured": "device timers (globaltimer) of each cluster's rank-0 CTA, summed over clusters, "
+                              "divided by the systems of the step; one extra untimed step"}
     # roofline of the dominant kernel (the chain kernel), measured per launch
     peak, peak_kind = _peaks()
     kbytes = sum(s["bytes"] for s in st_skr) / len(st_skr)
     kms = sum(s["kernel_ms"] for s in st_skr) / len(st_skr)
     achieved = kbytes / (kms / 1e3) / 1e9
-    default_workload = (args.workload == "darcy256" and N == W["nsys"] and nchains == 76 and cluster_size == 2)
     traffic = None
-    if default_workload and TRAFFIC["sources_sha256"] == _kernel_sources_sha256():
+    if (args.workload == TRAFFIC.get("workload") and N == W["nsys"] and args.chains is None
+            and args.cluster_size is None and TRAFFIC["sources_sha256"] == _kernel_sources_sha256()):
         traffic = TRAFFIC["bytes_per_launch"]
     # correctness of the timed results
     relmax = max(r["relres"] for r in res_skr[-1])
     flags = sorted({r["flag"] for r in res_skr[-1]})
     lat = sorted(r["seconds"] * 1e3 for r in res_skr[-1])
     steps_skr = sum(r["steps"] for r in res_skr[-1]) / N
+    launches_per_step = (0 if args.no_sort else 2 * len(B.groups)) + st_skr[-1]["launches"]
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if args.e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()   # noqa: E731
-        Lh = [_to(p, pin) for p in payload]
-        Ph = pin(Kh)
-        xh = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(N)]
-        sys_h = [_system(skr, W, _to(Lh[i], lambda t: t.numpy())) for i in range(N)]
+        Lh = [_to_payload(W, pl, pin) for pl in B.payload]
+        Ph = [pin(keys) for _, keys in B.groups]
+        xh = [torch.empty(B.n[i], dtype=torch.float64).pin_memory() for i in range(N)]
+        sys_h = [_system(skr, W, _to_payload(W, Lh[i], lambda t: t.numpy())) for i in range(N)]
         xh_np = [x.numpy() for x in xh]
 
         def e2e_step():
-            perm = np.arange(N, dtype=np.int32) if args.no_sort else skr.skr_sort(Ph.numpy(), stream=stream)
-            skr.skr_solve_sequence(sys_h, order=perm, nchains=nchains, options=opts(W["k"]),
-                                   x_out=xh_np)
+            if args.no_sort:
+                order = B.order(ident)
+            else:
+                order = B.order([skr.skr_sort(Pg.numpy(), stream=stream) for Pg in Ph])
+            skr.skr_solve_sequence(sys_h, order=order, chain_offsets=offs, nchains=len(offs) - 1,
+                                   options=opts(W["k"]), x_out=xh_np)
 
         e2e_step()
         torch.cuda.synchronize()
         e2e_ms = []
-        for _ in range(max(1, args.steps)):
+        for _ in range(max(1, args.e2e_steps)):
             flush.zero_()
             torch.cuda.synchronize()
             barrier()
@@ -391,11 +510,16 @@ def run_gpu(args):
             barrier()
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
         e2e_val = N * ws / (agg(e2e_ms) / 1e3)
-        h2d = Ph.numel() * 8 + sum(sum(t.numel() for t in p) if isinstance(p, tuple) else p.numel()
-                                   for p in Lh) * 8
-        d2h = N * n * 8 + N * 4
+
+        def nbytes(pl):
+            if W["kind"] == "convdiff2d":
+                return pl[2].numel() * 8
+            return sum(t.numel() for t in pl) * 8 if isinstance(pl, tuple) else pl.numel() * 8
+        h2d = (0 if args.no_sort else sum(P.numel() * 8 for P in Ph))
+        h2d += sum(nbytes(pl) for pl in Lh)
+        d2h = sum(B.n) * 8 + (0 if args.no_sort else N * 4)
         e2e = {"value": round(e2e_val, 3), "unit": "systems/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+               "d2h_bytes_per_step": int(d2h), "steps_timed": len(e2e_ms)}
 
     line = {
         "metric": METRIC,
@@ -408,31 +532,32 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32+f64",
+        "dtype": "f32+f64" if W["precision"] == "mixed" else "f64",
         "data": "synthetic",
         "config": {
             "workload": W["desc"] % N,
-            "chains": nchains, "cluster_size": st_skr[-1]["cluster_size"], "warm_start": bool(args.warm_start),
-            "sorted": not args.no_sort,
-            "slots": st_skr[-1]["slots"], "l2": "flushed between steps (256 MB write)",
+            "chains": len(offs) - 1, "cluster_size": st_skr[-1]["cluster_size"],
+            "warm_start": bool(args.warm_start), "sorted": not args.no_sort,
+            "slots": st_skr[-1]["slots"], "maxit": args.maxit, "l2": "flushed between steps (256 MB write)",
             "parallelism": "replicas" if ws > 1 else "single GPU",
         },
         "sort_ms": None if sort_ms is None else round(sort_ms, 3),
-        "gmres_value": None if gm_value is None else round(gm_value, 3),
-        "gmres_ms_per_step": None if ms_gm is None else round(ms_gm, 3),
-        "speedup_vs_gmres": None if gm_value is None else round(value / gm_value, 3),
         "avg_steps_skr": round(steps_skr, 1),
-        "avg_steps_gmres": None if steps_gm is None else round(steps_gm, 1),
-        "gmres_flags": gm_flags,
         "max_relres": relmax,
         "flags": flags,
-        "latency_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3)},
+        "gmres": gmres,
+        "speedup_vs_gmres": None if gmres is None else round(value / gmres["value"], 3),
+        "fp64": fp64,
+        "latency_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
+                       "measured": "device time of each system inside the batch (first to last kernel work on it)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "chain_kernel<float>", "peak_kind": peak_kind,
+                     "kernel": "chain_kernel<%s>" % ("float" if W["precision"] == "mixed" else "double"),
+                     "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": int(kbytes), "kernel_ms": round(kms, 3)},
+        "phases": phases,
         "e2e": e2e,
-        "gpu_launches": (1 if args.no_sort else 3) * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
     if args.diagnostics:
@@ -440,93 +565,133 @@ def run_gpu(args):
         line["delta_mean"] = round(sum(ds) / len(ds), 4) if ds else None
         line["delta_systems"] = len(ds)
     if args.cpu_baseline and rank == 0:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, W, args.warm_start)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, W, args.warm_start, B)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
 
 
-def _oracle_worker(conn, W, fields, warm):
-    """One host core walking one chain segment with the FP64 oracle, as it stands.
+def _oracle_worker(conn, W, segments, warm):
+    """One host core walking its chain segments with the FP64 oracle, as it stands.
 
-    Each message is a time budget: solve consecutive systems of the segment
-    (carrying the recycle space, wrapping to a fresh start at its end) until
-    the budget is spent, at least one system; reply (systems done, seconds).
+    segments: lists of system payloads; the recycle state (and the warm
+    start) resets at the first system of each segment, and the worker wraps
+    around to its first segment after the last.  On "go" it solves systems
+    back to back; between systems it checks for "stop", then replies with
+    the (start, end) monotonic clock times of every system it finished.
     """
     for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
     from oracle import skr as oskr
     from oracle.krylov import RecycleState
 
-    state, pos, prev = RecycleState(), 0, None
-    while True:
-        budget = conn.recv()
-        if budget is None:
-            break
-        done = 0
-        t0 = time.perf_counter()
-        while True:
-            if pos == len(fields):
-                state, pos, prev = RecycleState(), 0, None
-            sysd = _oracle_system(W, fields[pos])
-            A, b = oskr.assemble(sysd)
-            x, _ = oskr.solve_system(A, b, W["precond"], W["m"], W["k"], W["tol"], state,
-                                     precision="mixed", inner_tol=W["inner_tol"],
-                                     x0=prev if warm else None, grid=oskr.grid_of(sysd),
-                                     pc_blocks=W["pc_blocks"])
-            prev = x
-            pos += 1
-            done += 1
-            if time.perf_counter() - t0 > budget:
-                break
-        conn.send((done, time.perf_counter() - t0))
+    conn.send("ready")
+    if conn.recv() != "go":
+        return
+    spans = []
+    seg, pos, state, prev = 0, 0, RecycleState(), None
+    while not conn.poll():
+        if pos == len(segments[seg]):
+            seg, pos, state, prev = (seg + 1) % len(segments), 0, RecycleState(), None
+        t0 = time.monotonic()
+        sysd = _oracle_system(W, segments[seg][pos])
+        A, b = oskr.assemble(sysd)
+        x, _ = oskr.solve_system(A, b, W["precond"], W["m"], W["k"], W["tol"], state,
+                                 precision=W["precision"], inner_tol=W["inner_tol"],
+                                 x0=prev if warm else None, grid=oskr.grid_of(sysd),
+                                 pc_blocks=W["pc_blocks"])
+        spans.append((t0, time.monotonic()))
+        prev = x
+        pos += 1
+    conn.recv()
+    conn.send(spans)
+
+
+def _progress(spans, a, b):
+    """Systems finished inside [a, b], a system that straddles an edge
+    counted by the fraction of its solve time inside."""
+    tot = 0.0
+    for t0, t1 in spans:
+        if t1 > t0:
+            tot += max(0.0, min(t1, b) - max(t0, a)) / (t1 - t0)
+    return tot
 
 
 class OracleChains:
-    """The FP64 oracle in the paper's decomposition: the sorted order cut into
-    one chain segment per host core, every core solving its segment.
+    """The FP64 oracle in the paper's decomposition: each sort group ordered
+    by the oracle's Algorithm 1 (once, on one core), the sorted order cut
+    into chain segments, the segments dealt to the host cores, every core
+    solving its segments.
 
-    The greedy sort of all systems runs once (one core) and its cost is
-    amortised over them.  Workers are spawned processes (no fork after the
-    GPU is in use) that keep their recycle state between samples.
+    Workers are spawned processes (no fork after the GPU is in use).  `run`
+    lets them solve for a number of back-to-back windows and returns, per
+    window, the systems finished inside it (fractions for systems that
+    straddle a window edge; the run waits for the systems in flight at the
+    end to finish so that their fractions are known).
     """
 
-    def __init__(self, W, warm=False, cores=None):
+    def __init__(self, W, batch, warm=False, cores=None):
         import multiprocessing as mp
         from oracle import sort as osort
         from oracle import skr as oskr
 
         self.W = W
-        keys, payload = _inputs(W, W["nsys"], W["seed"])
+        self.nsys = batch.nsys
         t0 = time.perf_counter()
-        order = osort.greedy_sort(keys)
+        perms = [osort.greedy_sort(keys) for _, keys in batch.groups]
         self.t_sort = time.perf_counter() - t0
-        self.cores = max(1, min(cores or os.cpu_count() or 1, W["nsys"]))
+        order = batch.order(perms)
+        offs = batch.chain_offsets()
+        chains = [order[offs[c]:offs[c + 1]] for c in range(len(offs) - 1)]
+        self.cores = max(1, min(cores or os.cpu_count() or 1, batch.nsys))
+        if len(chains) < self.cores:
+            # one group cut into fewer chains than cores: one segment per core instead
+            chains = [c for (first, keys), pm in zip(batch.groups, perms)
+                      for c in oskr.split_chains([first + int(i) for i in pm],
+                                                 max(1, round(self.cores * keys.shape[0] / batch.nsys)))]
+        self.cores = min(self.cores, len(chains))
+        segs = [[] for _ in range(self.cores)]
+        for c, ch in enumerate(chains):
+            segs[c % self.cores].append([batch.payload[int(i)] for i in ch])
         ctx = mp.get_context("spawn")
         self.conns, self.procs = [], []
-        for chain in oskr.split_chains(order, self.cores):
+        for sg in segs:
             a, b = ctx.Pipe()
-            p = ctx.Process(target=_oracle_worker, args=(b, W, [payload[i] for i in chain], warm), daemon=True)
+            p = ctx.Process(target=_oracle_worker, args=(b, W, sg, warm), daemon=True)
             p.start()
             self.conns.append(a)
             self.procs.append(p)
-
-    def sample(self, budget_s):
-        """All cores for about budget_s seconds: (systems/s of the whole host, systems done)."""
         for cn in self.conns:
-            cn.send(budget_s)
-        res = [cn.recv() for cn in self.conns]
-        done = sum(r[0] for r in res)
-        wall = max(r[1] for r in res)
-        per_sys = wall / done + self.t_sort / self.W["nsys"]
-        return 1.0 / per_sys, done
+            assert cn.recv() == "ready"
+
+    def run(self, windows, window_s):
+        """Solve for `windows` back-to-back windows of window_s seconds;
+        returns (systems finished per window, measured window lengths in s)."""
+        for cn in self.conns:
+            cn.send("go")
+        t0 = time.monotonic()
+        edges = [t0 + i * window_s for i in range(windows + 1)]
+        while time.monotonic() < edges[-1]:
+            time.sleep(min(0.05, max(0.0, edges[-1] - time.monotonic())))
+        for cn in self.conns:
+            cn.send("stop")
+        spans = [sp for cn in self.conns for sp in cn.recv()]
+        prog = [_progress(spans, edges[i], edges[i + 1]) for i in range(windows)]
+        return prog, [edges[i + 1] - edges[i] for i in range(windows)]
+
+    def rate(self, systems, seconds):
+        """Whole-host systems/s with the one-core sort amortised over all systems."""
+        if systems <= 0:
+            return 0.0
+        return 1.0 / (seconds / systems + self.t_sort / self.nsys)
 
     def close(self):
-        for cn in self.conns:
-            cn.send(None)
         for p in self.procs:
-            p.join(timeout=30)
+            p.join(timeout=5)
+            if p.is_alive():
+                p.terminate()
+                p.join(timeout=5)
 
 
 def _cpu_model():
@@ -549,18 +714,23 @@ def _cpu_model():
     return platform.machine()
 
 
-def cpu_baseline(budget_s, W, warm=False):
+def cpu_baseline(budget_s, W, warm=False, batch=None):
     """One bounded oracle sample beside the GPU line, on every host core."""
-    ch = OracleChains(W, warm)
+    if batch is None:
+        batch = _batch(W, W["nsys"], W["seed"])
+    ch = OracleChains(W, batch, warm)
     try:
-        v, done = ch.sample(budget_s)
+        prog, secs = ch.run(1, budget_s)
     finally:
         ch.close()
+    v = ch.rate(prog[0], secs[0])
     return {"value": round(v, 4), "unit": "systems/s", "cores": ch.cores, "kind": "oracle",
             "cpu": _cpu_model(),
-            "sample": "%d systems in %.0f s on %d cores, one sorted chain segment per core (the paper's "
-                      "decomposition); sort of all %d amortised; numpy/scipy FP64, BLAS threads = 1 per core"
-                      % (done, budget_s, ch.cores, W["nsys"])}
+            "sample": "%.1f systems finished in a %.0f s window on %d cores (a system straddling the window "
+                      "edge counts by its fraction inside), chain segments of the sorted order dealt to the "
+                      "cores (the paper's decomposition); the oracle's sort of all %d systems amortised; "
+                      "numpy/scipy FP64, BLAS threads = 1 per core"
+                      % (prog[0], secs[0], ch.cores, batch.nsys)}
 
 
 def run_reference(args):
@@ -568,31 +738,31 @@ def run_reference(args):
     if rank != 0:
         return
     W = _workload(args)
-    ch = OracleChains(W, args.warm_start)
-    budget = max(1.0, min(args.ref_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    batch = _batch(W, W["nsys"], W["seed"], getattr(args, "chains", None))
+    ch = OracleChains(W, batch, args.warm_start)
+    window = max(1.0, min(args.ref_seconds, 120.0 / max(1, args.steps + args.warmup)))
     try:
-        for _ in range(args.warmup):
-            ch.sample(budget)
-        vals, counts = [], []
-        for _ in range(args.steps):
-            v, done = ch.sample(budget)
-            vals.append(v)
-            counts.append(done)
+        prog, secs = ch.run(args.warmup + args.steps, window)
     finally:
         ch.close()
-    value = sum(vals) / len(vals)
+    prog, secs = prog[args.warmup:], secs[args.warmup:]
+    done, wall = sum(prog), sum(secs)
+    value = ch.rate(done, wall)
     cb = {"value": round(value, 4), "unit": "systems/s", "cores": ch.cores, "kind": "oracle", "cpu": _cpu_model(),
-          "sample": "%d timed samples of %.0f s, one sorted chain segment per core on %d cores (the paper's "
-                    "decomposition; %s systems per sample, after %d untimed samples; sort of all %d "
-                    "amortised), numpy/scipy FP64, BLAS threads = 1 per core"
-                    % (args.steps, budget, ch.cores, "/".join(map(str, counts)), args.warmup, W["nsys"])}
+          "sample": "%d timed windows of %.1f s after %d untimed ones, the oracle solving back to back on %d "
+                    "cores, chain segments of the sorted order dealt to the cores (the paper's decomposition); "
+                    "%.1f systems finished in the timed windows (a system straddling a window edge counts by "
+                    "its fraction inside); the oracle's sort of all %d systems amortised; numpy/scipy FP64, "
+                    "BLAS threads = 1 per core"
+                    % (args.steps, window, args.warmup, ch.cores, done, batch.nsys)}
     line = {
         "metric": METRIC, "value": cb["value"], "unit": "systems/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(W["nsys"] / value * 1e3, 3),
+        "ms_per_step": round(wall / max(1, len(secs)) * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": W["desc"].replace("mixed precision", "mixed-form refinement in FP64") % W["nsys"]},
+        "config": {"workload": W["desc"].replace("mixed precision", "mixed-form refinement in FP64")
+                   % batch.nsys},
         "cpu_baseline": cb,
         "e2e": {"value": cb["value"], "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -701,7 +871,7 @@ def run_sort_only(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     import paper_2401_09516_gb300 as skr
-    N, p, G = args.nsys, args.keys_p, args.group_max
+    N, p, G = (args.nsys or 100000), args.keys_p, args.group_max
     rng = np.random.default_rng(4000 + rank)
     # coefficient keys with a decaying spectrum, like the Chebyshev data of the Poisson workload
     Kh = rng.standard_normal((N, p)) / (1.0 + np.arange(p))[None, :]
@@ -758,9 +928,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="skr", choices=["skr", "reference"])
-    ap.add_argument("--workload", default="darcy256", choices=sorted(WORKLOADS),
-                    help="darcy256 (the headline workload), darcy100, darcy100_circle, darcy256_circle, helmholtz100 or "
-                         "poisson_cheb256")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
+                    help="named workload (default %s)" % DEFAULT_WORKLOAD)
     ap.add_argument("--warm-start", action="store_true", help="x_0 = previous solution of the chain")
     ap.add_argument("--no-sort", action="store_true", help="solve in input order (ablation)")
     ap.add_argument("--precond", default=None, choices=sorted(PRECOND_NAMES),
@@ -769,11 +938,18 @@ def main():
                     help="row blocks of --precond bjacobi (72: the paper's Darcy runs, one per process)")
     ap.add_argument("--diagnostics", action="store_true", help="report the mean one-sided distance delta")
     ap.add_argument("--chains", type=int, default=None,
-                    help="independent chains the sorted order is cut into (default: the workload's, 76)")
+                    help="chains the sorted order of a one-group workload is cut into (default: the workload's)")
     ap.add_argument("--cluster-size", type=int, default=None,
-                    help="CTAs per chain, a thread-block cluster (default: the workload's, 2)")
-    ap.add_argument("--nsys", type=int, default=200, help="systems per batch (200 = the full workload)")
-    ap.add_argument("--gmres-steps", type=int, default=1)
+                    help="CTAs per chain, a thread-block cluster (default: the workload's; 0 = the library's choice)")
+    ap.add_argument("--nsys", type=int, default=None, help="systems per batch (default: the full workload)")
+    ap.add_argument("--maxit", type=int, default=100000,
+                    help="cap on Arnoldi steps per system, both arms (high enough that plain GMRES converges)")
+    ap.add_argument("--gmres-steps", type=int, default=3, help="timed steps of the plain GMRES(m) arm (k = 0)")
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="timed steps of the same SKR solve in the FP64 form (mixed workloads only)")
+    ap.add_argument("--no-phases", dest="phases", action="store_false",
+                    help="skip the untimed profiled step that reports device time per phase")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="timed steps of the end-to-end (host buffers) arm")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

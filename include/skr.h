@@ -184,8 +184,10 @@ skr_status skr_sort(const double *params, int64_t N, int64_t p, int64_t start,
  * device memory that every GPU loading this library holds until the process
  * exits.
  *
- * params    N x p doubles in DEVICE memory, row i = P(i) flattened
- * perm_out  N int32 in DEVICE memory
+ * params    N x p doubles in DEVICE memory of the current device, row i = P(i) flattened
+ * perm_out  N int32 in DEVICE memory of the current device
+ * The call works on the current device; pointers to another device's
+ * memory are rejected with SKR_ERR_INVALID_ARG.
  * N         at most SKR_SORT_NOALLOC_MAX_N; a larger N is rejected with
  *           SKR_ERR_INVALID_ARG before any device work
  * The first call on a device looks up the device address of the array
@@ -296,8 +298,8 @@ typedef struct skr_server skr_server;
 
 typedef struct skr_server_info {
     int64_t submitted, completed, queued, running;
-    int32_t chains;           /* recycle chains created so far */
-    int32_t pad;
+    int32_t chains;           /* recycle chains resident now */
+    int32_t evicted;          /* chains evicted so far to make room for a request of a new shape */
     double  p50_ms, p99_ms, mean_ms;   /* submit-to-completion latency of completed requests */
     double  hbm_bytes;        /* device memory held by the server's chains */
 } skr_server_info;
@@ -327,8 +329,15 @@ skr_status skr_server_create(const skr_options *opt, size_t hbm_budget, int32_t 
  *        (nu, beta)); only chains of the same format, grid and p are
  *        candidates.  key may be NULL (p = 0): the system's own coefficient
  *        data is then the key
- * A request is admitted when a chain of its shape is idle (the nearest idle
- * one is taken) or when a new chain fits in the budget; otherwise it waits.
+ * Requests are admitted in arrival order, a waiting one not holding back
+ * later ones.  A request waits until its cluster's CTAs fit on the GPU
+ * beside the running requests (one request always runs).  It then goes to
+ * the nearest idle chain of its shape (format, grid and p); else to a new
+ * chain if max_chains and the budget leave room; else, when no chain of its
+ * shape exists, to a new chain that replaces the least recently used idle
+ * chains of other shapes (evicted: their recycle spaces are dropped); a
+ * request whose shape has only busy chains waits for one of them.  So every
+ * request that fits the budget on its own is eventually served.
  * A request larger than the whole budget is rejected (SKR_ERR_OOM).
  */
 skr_status skr_submit(skr_server *srv, const skr_system *sys, const double *key, int64_t p,

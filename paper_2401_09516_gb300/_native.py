@@ -81,11 +81,11 @@ class SkrResult(ctypes.Structure):
 class SkrServerInfo(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("chains", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("evicted", ctypes.c_int32), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("hbm_bytes", ctypes.c_double)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 if not os.path.exists(LIB_PATH):

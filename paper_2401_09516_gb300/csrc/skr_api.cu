@@ -830,13 +830,14 @@ skr_status noalloc_scratch(unsigned char **out) {
     return SKR_OK;
 }
 
-bool is_device_pointer(const void *p) {
+// Device memory of device `dev`, or managed memory (which any device reaches).
+bool is_device_pointer(const void *p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return (at.type == cudaMemoryTypeDevice && at.device == dev) || at.type == cudaMemoryTypeManaged;
 }
 }  // namespace
 
@@ -851,8 +852,10 @@ extern "C" skr_status skr_sort_noalloc(const double *params, int64_t N, int64_t 
     if (!params || !perm_out) return fail(SKR_ERR_INVALID_ARG, "NULL pointer");
     if (p < 1) return fail(SKR_ERR_INVALID_ARG, "p < 1");
     if (start < 0 || start >= N) return fail(SKR_ERR_INVALID_ARG, "start out of range");
-    if (!is_device_pointer(params) || !is_device_pointer(perm_out))
-        return fail(SKR_ERR_INVALID_ARG, "params and perm_out must be device memory");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (!is_device_pointer(params, dev) || !is_device_pointer(perm_out, dev))
+        return fail(SKR_ERR_INVALID_ARG, "params and perm_out must be device memory of the current device (%d)", dev);
     unsigned char *base = nullptr;
     skr_status s0 = noalloc_scratch(&base);
     if (s0 != SKR_OK) return s0;

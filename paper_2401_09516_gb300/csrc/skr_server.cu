@@ -2,12 +2,15 @@
 //
 // One host thread per server owns every CUDA call: it collects finished
 // requests (event queries), admits queued ones (nearest idle chain of the
-// same shape, or a new chain if the device-memory budget allows), and
-// launches each admitted request as a one-cluster chain-kernel launch on the
-// chain's own stream.  Requests of different chains therefore run
-// concurrently on the GPU; a request that arrives while others run starts as
-// soon as a chain of its shape is free.  skr_submit and skr_poll only touch
-// host data under the server's mutex.
+// same shape, or a new chain if the device-memory budget and the chain limit
+// allow, else a new chain in place of the least recently used idle chains
+// when the request's shape has no chain at all), and launches each admitted
+// request as a one-cluster chain-kernel launch on the chain's own stream,
+// as long as the running requests leave enough CTAs free on the GPU.
+// Requests of different chains therefore run concurrently on the GPU; a
+// request that arrives while others run starts as soon as a chain of its
+// shape (or room for one) is free.  skr_submit and skr_poll only touch host
+// data under the server's mutex.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -91,8 +94,10 @@ struct Chain {
     double *hcoef = nullptr, *hrhs = nullptr, *hx = nullptr;
     DevSystem *hsys = nullptr;
     DevResult *hres = nullptr;
+    size_t pin_bytes = 0;     // capacity of the pinned staging buffer
     bool busy = false;
     uint64_t ticket = 0;
+    uint64_t last_used = 0;   // launch counter at this chain's last launch (LRU eviction)
 };
 
 size_t al256(size_t b) { return (b + 255) / 256 * 256; }
@@ -103,6 +108,9 @@ struct skr_server {
     skr_options opt{};
     size_t budget = 0, used = 0, smem = 0;
     int max_chains = 64, device = 0, threads = 0;
+    int cap_ctas = 0;          // CTAs of the chain kernel that fit on the GPU at once
+    uint64_t launches = 0;     // launch counter (chain recency)
+    int64_t evicted = 0;
     std::mutex mu;
     std::condition_variable cv;
     std::deque<uint64_t> queue;
@@ -122,16 +130,41 @@ int auto_cs(long long n, int requested) {
     return (int)std::min<long long>(8, std::max<long long>(1, (n + 8191) / 8192));
 }
 
-size_t chain_bytes(const skr_server *S, const Request &r, int cs) {
+struct ChainPlan {
+    SlabLayout L;
+    long long ld = 0, nodecap = 1, clen = 1;
+    int cs = 1;
+    size_t o_coef = 0, o_rhs = 0, o_x = 0, o_sys = 0, o_res = 0, o_ord = 0, o_off = 0, o_ctr = 0, o_kc = 0;
+    size_t bytes = 0, pin = 0;
+};
+
+// Device and pinned-host layout of a chain shaped like request r.
+ChainPlan chain_plan(const skr_server *S, const Request &r) {
+    ChainPlan P;
     const size_t esz = S->opt.precision == SKR_PREC_FP64 ? 8 : 4;
-    const long long ld = chain_ld(r.n, cs);
-    const long long nodecap = std::max<long long>(1, (r.fmt == SKR_FMT_DARCY2D || r.fmt == SKR_FMT_DARCY3D)
-                                                         ? coef_len(r.fmt, r.nx, r.ny, r.nz)
-                                                         : 1);
-    const SlabLayout L = slab_layout(1, ld, nodecap, esz);
-    const long long clen = std::max<long long>(1, coef_len(r.fmt, r.nx, r.ny, r.nz));
-    return L.total + al256(clen * 8) + 2 * al256(r.n * 8) + 4096;
+    P.cs = auto_cs(r.n, S->opt.cluster_size);
+    P.ld = chain_ld(r.n, P.cs);
+    P.nodecap = std::max<long long>(1, (r.fmt == SKR_FMT_DARCY2D || r.fmt == SKR_FMT_DARCY3D)
+                                           ? coef_len(r.fmt, r.nx, r.ny, r.nz)
+                                           : 1);
+    P.clen = std::max<long long>(1, coef_len(r.fmt, r.nx, r.ny, r.nz));
+    P.L = slab_layout(1, P.ld, P.nodecap, esz);
+    size_t o = P.L.total;
+    P.o_coef = o;  o += al256(P.clen * 8);
+    P.o_rhs = o;   o += al256(r.n * 8);
+    P.o_x = o;     o += al256(r.n * 8);
+    P.o_sys = o;   o += 256;
+    P.o_res = o;   o += 256;
+    P.o_ord = o;   o += 256;
+    P.o_off = o;   o += 256;
+    P.o_ctr = o;   o += 256;
+    P.o_kc = o;    o += 256;
+    P.bytes = o;
+    P.pin = al256(P.clen * 8) + 2 * al256(r.n * 8) + 512;
+    return P;
 }
+
+size_t chain_bytes(const skr_server *S, const Request &r) { return chain_plan(S, r).bytes; }
 
 void destroy_chain(Chain *c) {
     if (c->st) cudaStreamSynchronize(c->st);
@@ -142,70 +175,68 @@ void destroy_chain(Chain *c) {
     delete c;
 }
 
-// New chain shaped like request r (called with the server lock held).
-Chain *create_chain(skr_server *S, const Request &r) {
-    Chain *c = new Chain();
+// Shape an idle chain (its device slab and pinned buffer already large
+// enough) like request r: bind the layout, forget any recycle space and
+// previous solution, and set the constant descriptors of a one-system chain.
+// Returns false on a CUDA error.
+bool shape_chain(skr_server *S, Chain *c, const Request &r, const ChainPlan &P) {
+    const size_t esz = S->opt.precision == SKR_PREC_FP64 ? 8 : 4;
     c->fmt = r.fmt;
     c->nx = r.nx;
     c->ny = r.ny;
     c->nz = r.nz;
     c->n = r.n;
     c->p = r.key.size();
-    c->clen = std::max<long long>(1, coef_len(r.fmt, r.nx, r.ny, r.nz));
-    c->cs = auto_cs(r.n, S->opt.cluster_size);
-    const size_t esz = S->opt.precision == SKR_PREC_FP64 ? 8 : 4;
-    c->ld = chain_ld(r.n, c->cs);
-    c->nodecap = std::max<long long>(1, (r.fmt == SKR_FMT_DARCY2D || r.fmt == SKR_FMT_DARCY3D)
-                                            ? coef_len(r.fmt, r.nx, r.ny, r.nz)
-                                            : 1);
-    const SlabLayout L = slab_layout(1, c->ld, c->nodecap, esz);
-    size_t o = L.total;
-    const size_t o_coef = o;  o += al256(c->clen * 8);
-    const size_t o_rhs = o;   o += al256(r.n * 8);
-    const size_t o_x = o;     o += al256(r.n * 8);
-    const size_t o_sys = o;   o += 256;
-    const size_t o_res = o;   o += 256;
-    const size_t o_ord = o;   o += 256;
-    const size_t o_off = o;   o += 256;
-    const size_t o_ctr = o;   o += 256;
-    const size_t o_kc = o;    o += 256;
-    c->bytes = o;
+    c->key.clear();
+    c->clen = P.clen;
+    c->cs = P.cs;
+    c->ld = P.ld;
+    c->nodecap = P.nodecap;
+    c->ws = slab_bind(c->slab, P.L, 1, c->ld, c->nodecap);
+    c->dcoef = reinterpret_cast<double *>(c->slab + P.o_coef);
+    c->drhs = reinterpret_cast<double *>(c->slab + P.o_rhs);
+    c->dx = reinterpret_cast<double *>(c->slab + P.o_x);
+    c->dsys = reinterpret_cast<DevSystem *>(c->slab + P.o_sys);
+    c->dres = reinterpret_cast<DevResult *>(c->slab + P.o_res);
+    c->dorder = reinterpret_cast<int *>(c->slab + P.o_ord);
+    c->doff = reinterpret_cast<long long *>(c->slab + P.o_off);
+    c->dctr = reinterpret_cast<int *>(c->slab + P.o_ctr);
+    c->dbytes = reinterpret_cast<unsigned long long *>(c->slab + P.o_ctr + 64);
+    c->dkc = reinterpret_cast<int *>(c->slab + P.o_kc);
+    c->hcoef = reinterpret_cast<double *>(c->pinned);
+    c->hrhs = reinterpret_cast<double *>(c->pinned + al256(c->clen * 8));
+    c->hx = reinterpret_cast<double *>(c->pinned + al256(c->clen * 8) + al256(r.n * 8));
+    c->hsys = reinterpret_cast<DevSystem *>(c->pinned + al256(c->clen * 8) + 2 * al256(r.n * 8));
+    c->hres = reinterpret_cast<DevResult *>(c->pinned + al256(c->clen * 8) + 2 * al256(r.n * 8) + 256);
+    // one chain of one system, starting with no recycle space
+    cudaMemsetAsync(c->ws.basis, 0, (size_t)NCOLS * c->ld * esz, c->st);
+    cudaMemsetAsync(c->slab + P.o_ord, 0, P.bytes - P.o_ord, c->st);
+    const long long off[2] = {0, 1};
+    cudaMemcpyAsync(c->doff, off, sizeof(off), cudaMemcpyHostToDevice, c->st);
+    cudaStreamSynchronize(c->st);
+    return cudaGetLastError() == cudaSuccess;
+}
+
+// New chain shaped like request r (called with the server lock held).
+Chain *create_chain(skr_server *S, const Request &r) {
+    const ChainPlan P = chain_plan(S, r);
+    Chain *c = new Chain();
+    c->bytes = P.bytes;
+    c->pin_bytes = P.pin;
     if (cudaMalloc(&c->slab, c->bytes) != cudaSuccess) {
         cudaGetLastError();
         c->slab = nullptr;
         destroy_chain(c);
         return nullptr;
     }
-    const size_t pin = al256(c->clen * 8) + 2 * al256(r.n * 8) + 512;
-    if (cudaMallocHost(&c->pinned, pin) != cudaSuccess || cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess ||
+    if (cudaMallocHost(&c->pinned, P.pin) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         destroy_chain(c);
         return nullptr;
     }
-    c->ws = slab_bind(c->slab, L, 1, c->ld, c->nodecap);
-    c->dcoef = reinterpret_cast<double *>(c->slab + o_coef);
-    c->drhs = reinterpret_cast<double *>(c->slab + o_rhs);
-    c->dx = reinterpret_cast<double *>(c->slab + o_x);
-    c->dsys = reinterpret_cast<DevSystem *>(c->slab + o_sys);
-    c->dres = reinterpret_cast<DevResult *>(c->slab + o_res);
-    c->dorder = reinterpret_cast<int *>(c->slab + o_ord);
-    c->doff = reinterpret_cast<long long *>(c->slab + o_off);
-    c->dctr = reinterpret_cast<int *>(c->slab + o_ctr);
-    c->dbytes = reinterpret_cast<unsigned long long *>(c->slab + o_ctr + 64);
-    c->dkc = reinterpret_cast<int *>(c->slab + o_kc);
-    c->hcoef = reinterpret_cast<double *>(c->pinned);
-    c->hrhs = reinterpret_cast<double *>(c->pinned + al256(c->clen * 8));
-    c->hx = reinterpret_cast<double *>(c->pinned + al256(c->clen * 8) + al256(r.n * 8));
-    c->hsys = reinterpret_cast<DevSystem *>(c->pinned + al256(c->clen * 8) + 2 * al256(r.n * 8));
-    c->hres = reinterpret_cast<DevResult *>(c->pinned + al256(c->clen * 8) + 2 * al256(r.n * 8) + 256);
-    // constant descriptors: one chain of one system, starting with no recycle space
-    cudaMemsetAsync(c->ws.basis, 0, (size_t)NCOLS * c->ld * esz, c->st);
-    cudaMemsetAsync(c->slab + o_ord, 0, c->bytes - o_ord, c->st);
-    const long long off[2] = {0, 1};
-    cudaMemcpyAsync(c->doff, off, sizeof(off), cudaMemcpyHostToDevice, c->st);
-    cudaStreamSynchronize(c->st);
-    if (cudaGetLastError() != cudaSuccess) {
+    if (!shape_chain(S, c, r, P)) {
         destroy_chain(c);
         return nullptr;
     }
@@ -268,6 +299,7 @@ bool launch(skr_server *S, Chain *c, Request *r) {
     c->busy = true;
     c->ticket = r->ticket;
     c->key = r->key;
+    c->last_used = ++S->launches;
     r->state = 1;
     return cudaGetLastError() == cudaSuccess;
 }
@@ -306,17 +338,42 @@ double sqdist(const std::vector<double> &a, const std::vector<double> &b) {
 
 // The server thread.  Each round: under the lock, collect the chains whose
 // launch finished and take a snapshot of the queue; without the lock, copy
-// their results out of the pinned staging buffers and route the queued
-// requests to idle chains (the nearest key of the same shape); under the
-// lock again, publish the results, create chains and launch.  The chain list
-// and every chain's state are written by this thread only, and only under
-// the lock, so the unlocked reads race with nothing; a request that is
-// queued or running is never touched by skr_poll, and its key is immutable.
-// skr_submit and skr_poll therefore wait for the lock only while results are
-// published and requests launched, not while keys are compared.
+// their results out of the pinned staging buffers and plan the admissions;
+// under the lock again, publish the results, evict, create chains and
+// launch.  The chain list and every chain's state are written by this
+// thread only, and only under the lock, so the unlocked reads race with
+// nothing; a request that is queued or running is never touched by
+// skr_poll, and its key is immutable.  skr_submit and skr_poll therefore
+// wait for the lock only while results are published and requests launched,
+// not while keys are compared.
+//
+// Admission, in arrival order (a request that must wait does not hold back
+// later ones):
+//   1. the CTAs of the request's cluster must fit beside the running and
+//      already admitted requests (at least one request always runs);
+//   2. the nearest idle chain of the request's shape (format, grid, key
+//      length) takes it;
+//   3. else a new chain, if the chain limit and the device-memory budget
+//      leave room;
+//   4. else, if no chain of its shape exists at all, the least recently used
+//      idle chains of other shapes are evicted until the new chain fits (an
+//      evicted chain's memory is reused in place when it is large enough);
+//      a request whose shape has a busy chain waits for it instead, so that
+//      chains of the shapes in use are not evicted back and forth.
+// So a request of a new shape is never starved by idle chains of others.
 void dequeue(skr_server *S, uint64_t ticket) {
     auto it = std::find(S->queue.begin(), S->queue.end(), ticket);
     if (it != S->queue.end()) S->queue.erase(it);
+}
+
+struct Admit {
+    Request *r;
+    Chain *chain;                  // an idle chain of r's shape, or nullptr: a new chain
+    std::vector<Chain *> victims;  // idle chains to evict first (new chain only)
+};
+
+bool same_shape(const Chain *c, const Request *r) {
+    return c->fmt == r->fmt && c->nx == r->nx && c->ny == r->ny && c->nz == r->nz && c->p == r->key.size();
 }
 
 void loop(skr_server *S) {
@@ -328,7 +385,7 @@ void loop(skr_server *S) {
     };
     std::vector<Done> done;
     std::vector<Request *> queued;
-    std::vector<std::pair<Request *, Chain *>> plan;   // chain nullptr: a new chain
+    std::vector<Admit> plan;
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
         done.clear();
@@ -350,22 +407,38 @@ void loop(skr_server *S) {
         if (!S->stop)
             for (uint64_t t : S->queue) queued.push_back(S->reqs[t]);
         const size_t nchains = S->chains.size();
+        const size_t used = S->used;
         lk.unlock();
         for (const Done &d : done)
             if (d.r && d.ok) d.r->x.assign(d.c->hx, d.c->hx + d.r->n);
         {
-            std::vector<char> taken(nchains, 0);
-            int fresh = 0;
+            // 0 idle, 1 busy, 2 taken this round (admitted onto or evicted)
+            std::vector<char> state(nchains, 0);
+            int free_ctas = S->cap_ctas;
+            int running = 0;
+            for (size_t ci = 0; ci < nchains; ci++) {
+                const Chain *c = S->chains[ci];
+                bool fin = false;
+                for (const Done &d : done) fin = fin || d.c == c;
+                if (c->busy && !fin) {
+                    state[ci] = 1;
+                    free_ctas -= c->cs;
+                    running++;
+                }
+            }
+            long long free_slots = (long long)S->max_chains - (long long)nchains;
+            long long free_bytes = S->budget == 0 ? (1LL << 62) : (long long)S->budget - (long long)used;
             for (Request *r : queued) {
+                const int cs = auto_cs(r->n, S->opt.cluster_size);
+                if (cs > free_ctas && running > 0) continue;      // wait for SMs
                 int best = -1;
                 double bd = INFINITY;
+                bool resident = false;
                 for (size_t ci = 0; ci < nchains; ci++) {
                     const Chain *c = S->chains[ci];
-                    bool idle = !c->busy;
-                    for (const Done &d : done) idle = idle || d.c == c;
-                    if (!idle || taken[ci] || c->fmt != r->fmt || c->nx != r->nx || c->ny != r->ny ||
-                        c->nz != r->nz || c->p != r->key.size())
-                        continue;
+                    if (!same_shape(c, r)) continue;
+                    resident = true;
+                    if (state[ci] != 0) continue;
                     const double dist = c->key.empty() ? 0.0 : sqdist(c->key, r->key);
                     if (dist < bd) {
                         bd = dist;
@@ -373,12 +446,39 @@ void loop(skr_server *S) {
                     }
                 }
                 if (best >= 0) {
-                    taken[best] = 1;
-                    plan.push_back({r, S->chains[best]});
-                } else if ((int)nchains + fresh < S->max_chains) {
-                    fresh++;
-                    plan.push_back({r, nullptr});
+                    state[best] = 2;
+                    plan.push_back({r, S->chains[best], {}});
+                } else {
+                    const long long need = (long long)chain_bytes(S, *r);
+                    std::vector<Chain *> victims;
+                    if (free_slots < 1 || need > free_bytes) {
+                        if (resident) continue;                   // wait for a chain of its own shape
+                        std::vector<size_t> idle;
+                        for (size_t ci = 0; ci < nchains; ci++)
+                            if (state[ci] == 0) idle.push_back(ci);
+                        std::sort(idle.begin(), idle.end(), [&](size_t a, size_t b) {
+                            return S->chains[a]->last_used < S->chains[b]->last_used;
+                        });
+                        long long slots = free_slots, bytes = free_bytes;
+                        size_t v = 0;
+                        for (; v < idle.size() && (slots < 1 || need > bytes); v++) {
+                            slots += 1;
+                            bytes += (long long)S->chains[idle[v]]->bytes;
+                        }
+                        if (slots < 1 || need > bytes) continue;  // not enough idle chains: wait
+                        for (size_t q = 0; q < v; q++) {
+                            state[idle[q]] = 2;
+                            victims.push_back(S->chains[idle[q]]);
+                        }
+                        free_slots = slots;
+                        free_bytes = bytes;
+                    }
+                    free_slots -= 1;
+                    free_bytes -= need;
+                    plan.push_back({r, nullptr, victims});
                 }
+                free_ctas -= cs;
+                running++;
             }
         }
         lk.lock();
@@ -386,18 +486,43 @@ void loop(skr_server *S) {
             if (d.r) finish(S, d.r, d.ok ? d.c->hres : nullptr, d.ok);
             d.c->busy = false;
         }
-        for (auto &pr : plan) {
+        for (Admit &ad : plan) {
             if (S->stop) break;
-            Request *r = pr.first;
-            Chain *best = pr.second;
-            if (!best) {
-                const size_t need = chain_bytes(S, *r, auto_cs(r->n, S->opt.cluster_size));
-                if (S->budget != 0 && S->used + need > S->budget) continue;   // stays queued
-                best = create_chain(S, *r);
-                if (best) {
-                    S->chains.push_back(best);
-                    S->used += best->bytes;
+            Request *r = ad.r;
+            Chain *c = ad.chain;
+            if (!c) {
+                const ChainPlan P = chain_plan(S, *r);
+                // reuse the last victim in place when its memory is large enough
+                Chain *reuse = nullptr;
+                if (!ad.victims.empty() && ad.victims.back()->bytes >= P.bytes &&
+                    ad.victims.back()->pin_bytes >= P.pin) {
+                    reuse = ad.victims.back();
+                    ad.victims.pop_back();
+                }
+                for (Chain *v : ad.victims) {
+                    S->chains.erase(std::find(S->chains.begin(), S->chains.end(), v));
+                    S->used -= v->bytes;
+                    destroy_chain(v);
+                    S->evicted += 1;
+                }
+                if (reuse) {
+                    S->evicted += 1;
+                    if (shape_chain(S, reuse, *r, P)) {
+                        c = reuse;
+                    } else {
+                        S->chains.erase(std::find(S->chains.begin(), S->chains.end(), reuse));
+                        S->used -= reuse->bytes;
+                        destroy_chain(reuse);
+                    }
                 } else {
+                    if (S->budget != 0 && S->used + P.bytes > S->budget) continue;   // stays queued
+                    c = create_chain(S, *r);
+                    if (c) {
+                        S->chains.push_back(c);
+                        S->used += c->bytes;
+                    }
+                }
+                if (!c) {
                     // device memory could not be obtained: fail the request
                     // rather than keep it queued
                     finish(S, r, nullptr, false);
@@ -405,10 +530,10 @@ void loop(skr_server *S) {
                     continue;
                 }
             }
-            if (!launch(S, best, r)) {
+            if (!launch(S, c, r)) {
                 cudaGetLastError();
                 finish(S, r, nullptr, false);
-                best->busy = false;
+                c->busy = false;
             }
             dequeue(S, r->ticket);
         }
@@ -457,6 +582,13 @@ skr_status skr_server_create(const skr_options *opt_in, size_t hbm_budget, int32
         delete S;
         return err(SKR_ERR_CUDA, "no CUDA device");
     }
+    // CTAs of the chain kernel resident at once (clusters of one CTA)
+    S->cap_ctas = opt.precision == SKR_PREC_FP64 ? max_active_clusters_f64(1, S->threads, S->smem)
+                                                 : max_active_clusters_f32(1, S->threads, S->smem);
+    if (S->cap_ctas < 1) {
+        delete S;
+        return err(SKR_ERR_CUDA, "the chain kernel cannot be scheduled with this shared memory");
+    }
     S->th = std::thread(loop, S);
     *out = S;
     return SKR_OK;
@@ -490,7 +622,7 @@ skr_status skr_submit(skr_server *S, const skr_system *sys, const double *key, i
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        if (S->budget > 0 && chain_bytes(S, *r, auto_cs(r->n, S->opt.cluster_size)) > S->budget) {
+        if (S->budget > 0 && chain_bytes(S, *r) > S->budget) {
             delete r;
             return err(SKR_ERR_OOM, "request does not fit in the server's device-memory budget");
         }
@@ -529,6 +661,7 @@ skr_status skr_server_stats(skr_server *S, skr_server_info *info) {
     for (Chain *c : S->chains) running += c->busy ? 1 : 0;
     info->running = running;
     info->chains = (int32_t)S->chains.size();
+    info->evicted = (int32_t)S->evicted;
     info->hbm_bytes = (double)S->used;
     if (!S->lat_ms.empty()) {
         std::vector<double> v = S->lat_ms;

@@ -132,3 +132,59 @@ def test_colour_sweep_preconditioners_in_the_serving_loop(skr, pc, blocks):
         assert res["flag"] == 0, res
         assert np.linalg.norm(b - A @ x) <= 1.01e-8 * np.linalg.norm(b)
         assert np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)
+
+
+def _interleaved_two_shapes():
+    a = darcy2d_sequence(24, 3, 0.2, seed=21)
+    b = darcy2d_sequence(32, 3, 0.2, seed=22)
+    return [a[0], b[0], a[1], b[1], a[2], b[2]]
+
+
+def _check_all_solved(reqs, outs):
+    for loga, (x, res) in zip(reqs, outs):
+        A, b, xd = _direct(loga)
+        assert res["flag"] == 0, res
+        assert np.linalg.norm(b - A @ x) <= 1.01e-8 * np.linalg.norm(b)
+        assert np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)
+
+
+def test_one_chain_serves_two_interleaved_shapes_by_eviction(skr):
+    # max_chains = 1: every request of the other shape evicts the idle chain
+    reqs = _interleaved_two_shapes()
+    with skr.Server(_opts(skr), max_chains=1) as srv:
+        tickets = [srv.submit(skr.darcy2d(l)) for l in reqs]
+        outs = [srv.wait(t, timeout=120.0) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["queued"] == 0
+    assert st["chains"] == 1 and st["evicted"] >= 1
+    _check_all_solved(reqs, outs)
+
+
+def test_budget_of_one_chain_serves_two_shapes(skr):
+    # a device-memory budget that holds one chain of the larger shape only
+    reqs = _interleaved_two_shapes()
+    with skr.Server(_opts(skr), max_chains=1) as probe:
+        probe.wait(probe.submit(skr.darcy2d(reqs[1])))
+        one = probe.stats()["hbm_bytes"]
+    with skr.Server(_opts(skr), hbm_budget=int(one * 1.5)) as srv:
+        tickets = [srv.submit(skr.darcy2d(l)) for l in reqs]
+        outs = [srv.wait(t, timeout=120.0) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["hbm_bytes"] <= one * 1.5
+    assert st["evicted"] >= 1
+    _check_all_solved(reqs, outs)
+
+
+def test_requests_beyond_the_sms_wait_and_all_complete(skr):
+    # 3D requests of 8-CTA clusters: more than fit on the GPU at once are
+    # queued by the server, not launched into the hardware queue, and all finish
+    L = darcy3d_sequence(40, 24, 0.3, seed=23)
+    with skr.Server(_opts(skr, cluster_size=8), max_chains=64) as srv:
+        tickets = [srv.submit(skr.darcy3d(l)) for l in L]
+        outs = [srv.wait(t, timeout=300.0) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(L)
+    for loga, (x, res) in zip(L[:3], outs[:3]):
+        A, b, xd = _direct(loga)
+        assert res["flag"] == 0, res
+        assert np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)

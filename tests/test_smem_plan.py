@@ -33,7 +33,22 @@ int main() {
                 ok = ok && P.ring_cap >= 2 * (m + 2) * seg;         // two stages of the widest pass
                 ok = ok && P.ring_cap % seg == 0;
                 ok = ok && P.o_ring + P.ring_cap <= P.total;
-                ok = ok && (P.o_bar * 8) % 8 == 0 && P.o_bar + RING_MAX_NS <= P.o_req;   // 8 mbarriers
+                ok = ok && P.o_bar + RING_MAX_NS <= P.o_req;        // 8 mbarriers before the request table
+                // every stage of every pass width the kernel stages (up to m + 2
+                // segments per block): its TMA destinations start 128-byte aligned
+                // (box starts are whole segments into the stage) and the stages the
+                // kernel takes for that width (min(RING_MAX_NS, capacity / width))
+                // end inside the ring
+                for (int nseg = 1; nseg <= m + 2; nseg++) {
+                    const long long stage = (long long)nseg * RING_SEG_BYTES;
+                    const int ns = std::min<long long>(RING_MAX_NS, (long long)P.ring_cap * 8 / stage);
+                    ok = ok && ns >= 2;
+                    for (int st = 0; st < ns; st++) {
+                        const long long dst = (long long)P.o_ring * 8 + st * stage;
+                        ok = ok && dst % 128 == 0 && RING_SEG_BYTES % 128 == 0;
+                        ok = ok && dst + stage <= (long long)(P.o_ring + P.ring_cap) * 8;
+                    }
+                }
                 ok = ok && P.o_Tco + (P.t_total * esz + 7) / 8 <= P.o_mon;            // coefficients fit
                 ok = ok && P.o_sc + 16 <= P.total;                                   // dense scratch fits
                 ok = ok && P.o_red + 2 * P.redsz <= P.o_vals && P.o_vals + P.redsz <= P.o_wsum;

@@ -31,11 +31,14 @@ def test_noalloc_sort_matches_allocating_sort_on_two_calls_in_a_row(skr):
     # (distances, placed flags) would change the answer if it leaked through
     P1 = torch.tensor(rng.standard_normal((300, 2048)), device="cuda:0")
     P2 = torch.tensor(rng.integers(-2, 3, size=(41, 9)).astype(np.float64), device="cuda:0")
+    from oracle import sort as osort
     for P, start in ((P1, 0), (P2, 7)):
         want = skr.skr_sort(P, start=start).cpu().numpy()
         got = skr.skr_sort_noalloc(P, start=start).cpu().numpy()
         np.testing.assert_array_equal(got, want)
         assert sorted(got.tolist()) == list(range(P.shape[0]))
+        # and directly against the oracle's Algorithm 1
+        assert got.tolist() == osort.greedy_sort(P.cpu().numpy(), start)
 
 
 def test_noalloc_sort_rejects_oversize_and_host_input(skr):

@@ -13,6 +13,8 @@ of that sampled row; a white-noise vector filtered by their square roots has
 exactly that covariance (negative eigenvalues, from truncation, are clipped
 to zero).  The field is then cropped to the (N+2)^d node block.
 """
+import functools
+
 import numpy as np
 
 
@@ -29,6 +31,25 @@ def _next_smooth(n):
         m += 1
 
 
+@functools.lru_cache(maxsize=16)
+def _sqrt_spectrum(npad, h, ell, sigma, ndim):
+    """Square roots of the circulant covariance's eigenvalues (negative ones
+    clipped to zero), for one periodic grid; a sequence of fields with the
+    same grid and covariance reuses them."""
+    idx = np.arange(npad)
+    wrapped = np.minimum(idx, npad - idx) * h
+    r2 = np.zeros((npad,) * ndim)
+    for ax in range(ndim):
+        shape = [1] * ndim
+        shape[ax] = npad
+        r2 = r2 + (wrapped ** 2).reshape(shape)
+    row = sigma * sigma * np.exp(-r2 / (2.0 * ell * ell))
+    lam = np.real(np.fft.fftn(row))
+    root = np.sqrt(np.clip(lam, 0.0, None))
+    root.setflags(write=False)
+    return root
+
+
 def grf_field(rng, nodes, ell, sigma=1.0, h=None, ndim=2, pad_factor=2):
     """Draw one GRF sample on a node grid.
 
@@ -43,17 +64,8 @@ def grf_field(rng, nodes, ell, sigma=1.0, h=None, ndim=2, pad_factor=2):
     if h is None:
         h = 1.0 / (nodes - 1)
     npad = _next_smooth(max(pad_factor * nodes, nodes + int(np.ceil(4.0 * ell / h))))
-    idx = np.arange(npad)
-    wrapped = np.minimum(idx, npad - idx) * h
-    r2 = np.zeros((npad,) * ndim)
-    for ax in range(ndim):
-        shape = [1] * ndim
-        shape[ax] = npad
-        r2 = r2 + (wrapped ** 2).reshape(shape)
-    row = sigma * sigma * np.exp(-r2 / (2.0 * ell * ell))
-    lam = np.real(np.fft.fftn(row))
-    lam = np.clip(lam, 0.0, None)
+    root = _sqrt_spectrum(npad, float(h), float(ell), float(sigma), int(ndim))
     noise = rng.standard_normal((npad,) * ndim)
-    field = np.real(np.fft.ifftn(np.sqrt(lam) * np.fft.fftn(noise)))
+    field = np.real(np.fft.ifftn(root * np.fft.fftn(noise)))
     sl = tuple(slice(0, nodes) for _ in range(ndim))
     return np.ascontiguousarray(field[sl])

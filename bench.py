@@ -99,6 +99,12 @@ def _workload(args):
     """The named workload, with the preconditioner overridden if asked."""
     W = dict(WORKLOADS[args.workload])
     W["pc_blocks"] = 1
+    for key in ("m", "k"):
+        val = getattr(args, key, None)
+        if val is not None and val != W[key]:
+            W["desc"] = W["desc"].replace("m=%d k=%d" % (W["m"], W["k"]),
+                                          "m=%d k=%d" % (val if key == "m" else W["m"], val if key == "k" else W["k"]))
+            W[key] = val
     if args.precond and args.precond != W["precond"]:
         name = PRECOND_NAMES[args.precond]
         if args.precond == "bjacobi":
@@ -399,7 +405,9 @@ def run_gpu(args):
             order = B.order([pm.cpu().numpy() for pm in perms])
         _, res = skr.skr_solve_sequence(systems, order=order, chain_offsets=offs, nchains=len(offs) - 1,
                                         options=opts(k, precision, profile), x_out=x_dev)
-        return res, skr.skr_last_stats()
+        st = skr.skr_last_stats()
+        st["plan"] = skr.skr_last_plan()
+        return res, st
 
     def timed(k, steps, warmup, precision=None):
         for _ in range(warmup):
@@ -538,7 +546,8 @@ def run_gpu(args):
             "workload": W["desc"] % N,
             "chains": len(offs) - 1, "cluster_size": st_skr[-1]["cluster_size"],
             "warm_start": bool(args.warm_start), "sorted": not args.no_sort,
-            "slots": st_skr[-1]["slots"], "maxit": args.maxit, "l2": "flushed between steps (256 MB write)",
+            "slots": st_skr[-1]["slots"], "launches": st_skr[-1]["plan"],
+            "maxit": args.maxit, "l2": "flushed between steps (256 MB write)",
             "parallelism": "replicas" if ws > 1 else "single GPU",
         },
         "sort_ms": None if sort_ms is None else round(sort_ms, 3),
@@ -942,6 +951,8 @@ def main():
     ap.add_argument("--cluster-size", type=int, default=None,
                     help="CTAs per chain, a thread-block cluster (default: the workload's; 0 = the library's choice)")
     ap.add_argument("--nsys", type=int, default=None, help="systems per batch (default: the full workload)")
+    ap.add_argument("--m", type=int, default=None, help="override the workload's restart length m")
+    ap.add_argument("--k", type=int, default=None, help="override the workload's recycle dimension k")
     ap.add_argument("--maxit", type=int, default=100000,
                     help="cap on Arnoldi steps per system, both arms (high enough that plain GMRES converges)")
     ap.add_argument("--gmres-steps", type=int, default=3, help="timed steps of the plain GMRES(m) arm (k = 0)")

@@ -122,8 +122,10 @@ typedef struct skr_options {
     double  inner_tol;      /* SKR_PREC_MIXED: relative reduction per inner solve (default 1e-5) */
     int32_t precond;        /* SKR_PC_* (default SKR_PC_NONE) */
     int32_t precision;      /* SKR_PREC_* (default SKR_PREC_FP64) */
-    int32_t cluster_size;   /* CTAs cooperating on one system, 1..16 (0 = chosen from n) */
-    int32_t max_slots;      /* chains in flight at once (0 = as many as fit on the GPU) */
+    int32_t cluster_size;   /* CTAs cooperating on one system, 1..16 (0 = planned per chain from
+                               the measured launch table, see skr_last_plan) */
+    int32_t max_slots;      /* clusters (chains in flight) at once over all launches (0 = as many
+                               as fit on the GPU) */
     int32_t mem;            /* SKR_MEM_DEVICE or SKR_MEM_HOST */
     int32_t profile;        /* nonzero: accumulate device time per phase (skr_last_profile) */
     void   *stream;         /* cudaStream_t */
@@ -132,6 +134,13 @@ typedef struct skr_options {
                                and every system when zero (default), starts from x_0 = 0 */
     int32_t diagnostics;    /* nonzero: report skr_result.delta (one extra Gram pass per system) */
     int32_t pc_blocks;      /* SKR_PC_BJACOBI: number of row blocks, >= 1 (default 1) */
+    int32_t pad0;
+    double *const *recycle_out;  /* NULL (default), or a host array of nchains pointers to DEVICE
+                               memory (skr_solve_sequence with mem = SKR_MEM_DEVICE only): chain c's
+                               final recycle space, U_k (Algorithm 2) in columns 0..k-1 and C_k in
+                               columns k..2k-1, column-major with n rows; columns past the carried
+                               dimension (k_final of the chain's last system) are zero.  For
+                               checking A M^-1 U_k = C_k, C_k^T C_k = I (Sec. 4.2, App. B.1) */
 } skr_options;
 
 typedef struct skr_result {
@@ -362,12 +371,31 @@ skr_status skr_server_destroy(skr_server *srv);
  * skr_last_stats -- figures of the last skr_solve_sequence call on the
  * calling thread: the algorithmic bytes its kernel streamed (the compulsory
  * traffic of each pass, counted by the kernel from the pass sizes, not
- * measured), the kernel's duration from CUDA events recorded around the
- * launch on the call's stream, the cluster size, the number of chains in
- * flight, and the number of kernel launches.  Any pointer may be NULL.
+ * measured), the kernels' duration from CUDA events recorded around the
+ * launches on the call's stream, the cluster size (0 when the call made
+ * launches of several sizes, see skr_last_plan), the number of clusters in
+ * flight over all launches, and the number of kernel launches.  Any
+ * pointer may be NULL.
  */
 skr_status skr_last_stats(uint64_t *bytes, double *kernel_ms, int32_t *cluster_size,
                           int32_t *slots, int32_t *launches);
+
+/*
+ * skr_last_plan -- the launches of the last skr_solve_sequence call on the
+ * calling thread.  With opt->cluster_size = 0 the library cuts the chains
+ * into launches by cluster size (App. E.2.2's independent chains, each a
+ * thread-block cluster): each chain gets the cluster size that a table
+ * measured on this GPU (the project's autotuner, paper_2401_09516_gb300/
+ * tune.py) makes cheapest in CTA time per Arnoldi step, chains longer than
+ * the batch's ideal makespan get larger clusters, the launches share the
+ * GPU's CTAs in proportion to their estimated work and run concurrently,
+ * and each launch hands out its chains longest first.  With
+ * opt->cluster_size > 0 there is one launch of that cluster size.
+ * For launch i < min(cap, *nlaunch): cluster_size[i] CTAs per cluster,
+ * clusters[i] clusters, chains[i] chains.  Any array may be NULL.
+ */
+skr_status skr_last_plan(int32_t *cluster_size, int32_t *clusters, int32_t *chains, int32_t cap,
+                         int32_t *nlaunch);
 
 /*
  * skr_last_profile -- device time per phase of the last skr_solve_sequence

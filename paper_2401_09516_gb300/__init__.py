@@ -16,6 +16,7 @@ from ._native import (  # noqa: F401
     skr_apply,
     skr_assemble,
     skr_last_error,
+    skr_last_plan,
     skr_last_profile,
     skr_last_stats,
     skr_options_default,

@@ -65,7 +65,8 @@ class SkrOptions(ctypes.Structure):
                 ("max_slots", ctypes.c_int32), ("mem", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("warm_start", ctypes.c_int32), ("diagnostics", ctypes.c_int32),
-                ("pc_blocks", ctypes.c_int32)]
+                ("pc_blocks", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("recycle_out", ctypes.c_void_p)]
 
 
 class SkrResult(ctypes.Structure):
@@ -108,6 +109,7 @@ _lib.skr_apply.argtypes = [ctypes.POINTER(SkrSystem), _i32, _i32, _i32, _vp, _vp
 _lib.skr_last_stats.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
 _lib.skr_last_profile.argtypes = [ctypes.POINTER(ctypes.c_double), _i32]
+_lib.skr_last_plan.argtypes = [_vp, _vp, _vp, _i32, ctypes.POINTER(_i32)]
 _lib.skr_release_workspace.argtypes = []
 _lib.skr_server_create.argtypes = [ctypes.POINTER(SkrOptions), ctypes.c_size_t, _i32, ctypes.POINTER(_vp)]
 _lib.skr_submit.argtypes = [_vp, ctypes.POINTER(SkrSystem), _vp, _i64, ctypes.POINTER(ctypes.c_uint64)]
@@ -117,7 +119,7 @@ _lib.skr_server_destroy.argtypes = [_vp]
 _lib.skr_last_error.argtypes = []
 _lib.skr_last_error.restype = ctypes.c_char_p
 for _fn in ("skr_options_default", "skr_sort", "skr_sort_noalloc", "skr_sort_grouped", "skr_solve_sequence", "skr_assemble", "skr_apply",
-            "skr_last_stats", "skr_last_profile", "skr_release_workspace", "skr_server_create",
+            "skr_last_stats", "skr_last_profile", "skr_last_plan", "skr_release_workspace", "skr_server_create",
             "skr_submit", "skr_poll", "skr_server_stats", "skr_server_destroy"):
     getattr(_lib, _fn).restype = ctypes.c_int32
 
@@ -314,9 +316,13 @@ def skr_sort_noalloc(params, start=0, stream=None):
     return perm
 
 
-def skr_solve_sequence(systems, order=None, chain_offsets=None, nchains=1, options=None, x_out=None):
+def skr_solve_sequence(systems, order=None, chain_offsets=None, nchains=1, options=None, x_out=None,
+                       recycle_out=None):
     """Solve the systems in `order` with recycling along each chain.
 
+    recycle_out: None, or one contiguous float64 CUDA tensor per chain of at
+    least 2 k n elements, receiving the chain's final U_k (columns 0..k-1)
+    and C_k (columns k..2k-1), column-major (skr_options.recycle_out).
     Returns (x_out, results): x_out is a list of n-vectors (numpy on the
     host path, tensors on the device path), results a list of dicts.
     """
@@ -334,14 +340,24 @@ def skr_solve_sequence(systems, order=None, chain_offsets=None, nchains=1, optio
             x_out = [torch.empty(s.n, dtype=torch.float64, device=dev) for s in systems]
         else:
             x_out = [np.empty(s.n) for s in systems]
+    rec = None
+    if recycle_out is not None:
+        if len(recycle_out) != int(nchains) or not all(_is_device(t) for t in recycle_out):
+            raise ValueError("recycle_out needs one CUDA tensor per chain")
+        rec = (_vp * len(recycle_out))(*[_f64(t).data_ptr() for t in recycle_out])
+        opt.recycle_out = ctypes.cast(rec, _vp)
     sysarr = (SkrSystem * max(N, 1))(*[s.struct() for s in systems])
     xptr = (_vp * max(N, 1))(*[_ptr(x) for x in x_out])
     res = (SkrResult * max(N, 1))()
     ordv = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
     offv = None if chain_offsets is None else np.ascontiguousarray(chain_offsets, dtype=np.int64)
-    _check(_lib.skr_solve_sequence(sysarr, N, None if ordv is None else ordv.ctypes.data,
-                                   None if offv is None else offv.ctypes.data, int(nchains),
-                                   ctypes.byref(opt), xptr, res))
+    try:
+        _check(_lib.skr_solve_sequence(sysarr, N, None if ordv is None else ordv.ctypes.data,
+                                       None if offv is None else offv.ctypes.data, int(nchains),
+                                       ctypes.byref(opt), xptr, res))
+    finally:
+        if rec is not None:
+            opt.recycle_out = None
     return x_out, [res[i].as_dict() for i in range(N)]
 
 
@@ -386,6 +402,19 @@ def skr_last_stats():
                                ctypes.byref(ln)))
     return {"bytes": b.value, "kernel_ms": ms.value, "cluster_size": cs.value, "slots": sl.value,
             "launches": ln.value}
+
+
+def skr_last_plan():
+    """Launches of the last skr_solve_sequence call: a list of
+    {"cluster_size", "clusters", "chains"} dicts."""
+    cap = 16
+    cs = (ctypes.c_int32 * cap)()
+    cl = (ctypes.c_int32 * cap)()
+    ch = (ctypes.c_int32 * cap)()
+    n = _i32()
+    _check(_lib.skr_last_plan(ctypes.addressof(cs), ctypes.addressof(cl), ctypes.addressof(ch), cap,
+                              ctypes.byref(n)))
+    return [{"cluster_size": cs[i], "clusters": cl[i], "chains": ch[i]} for i in range(min(cap, n.value))]
 
 
 PHASES = ["assembly", "refresh", "projection", "operator", "multidot", "update", "gram", "dense",
@@ -492,7 +521,7 @@ class Server:
 def exported_symbols():
     """Names of the C functions this binding wraps."""
     return ["skr_options_default", "skr_sort", "skr_sort_noalloc", "skr_sort_grouped", "skr_solve_sequence", "skr_assemble", "skr_apply",
-            "skr_last_stats", "skr_last_profile", "skr_release_workspace", "skr_last_error",
+            "skr_last_stats", "skr_last_profile", "skr_last_plan", "skr_release_workspace", "skr_last_error",
             "skr_server_create", "skr_submit", "skr_poll", "skr_server_stats", "skr_server_destroy"]
 
 

@@ -33,7 +33,7 @@ def _stale(target, sources):
 def build(verbose=False, force=False):
     """Compile (if needed) and return the path of libskr.so."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h", ".inc"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "skr.h"))
     nvcc = _nvcc()
     jobs = []

@@ -13,6 +13,7 @@
 
 #include "skr_common.h"
 #include "skr_launch.h"
+#include "skr_plan.h"
 #include "skr_tma.h"
 #include "skr_workspace.h"
 #include "skr_ops.cuh"
@@ -90,6 +91,28 @@ cudaError_t ws_get(size_t bytes, void **out) {
     w.bytes = bytes;
     g_ws.push_back(w);
     *out = w.base;
+    return cudaSuccess;
+}
+
+// Streams of the concurrent launches of one call (per device, created on
+// first use, kept until exit).
+std::vector<std::pair<int, cudaStream_t>> g_streams;
+
+cudaError_t launch_streams(int count, cudaStream_t *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    int have = 0;
+    for (auto &ps : g_streams)
+        if (ps.first == dev && have < count) out[have++] = ps.second;
+    while (have < count) {
+        cudaStream_t s2 = nullptr;
+        e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        g_streams.push_back({dev, s2});
+        out[have++] = s2;
+    }
     return cudaSuccess;
 }
 
@@ -188,6 +211,10 @@ struct LastStats {
     unsigned long long bytes = 0;
     float kernel_ms = 0.f;
     int cluster_size = 0, slots = 0, launches = 0;
+    struct Shape {
+        int cs, slots, chains;
+    };
+    std::vector<Shape> plan;   // per launch of the last call
 };
 thread_local LastStats g_last;
 
@@ -591,6 +618,11 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     if (opt.cluster_size < 0 || opt.cluster_size > 16) return fail(SKR_ERR_INVALID_ARG, "cluster_size in [0, 16]");
     if (opt.warm_start != 0 && opt.warm_start != 1) return fail(SKR_ERR_INVALID_ARG, "warm_start must be 0 or 1");
     if (opt.diagnostics != 0 && opt.diagnostics != 1) return fail(SKR_ERR_INVALID_ARG, "diagnostics must be 0 or 1");
+    if (opt.recycle_out) {
+        if (opt.mem != SKR_MEM_DEVICE) return fail(SKR_ERR_INVALID_ARG, "recycle_out needs mem = SKR_MEM_DEVICE");
+        for (int c = 0; c < nchains; c++)
+            if (!opt.recycle_out[c]) return fail(SKR_ERR_INVALID_ARG, "recycle_out[%d] is NULL", c);
+    }
     cudaStream_t st = (cudaStream_t)opt.stream;
 
     // order and chains
@@ -629,28 +661,75 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
             if (!same_shape(systems[ord[q]], systems[ord[off[c]]]))
                 return fail(SKR_ERR_INVALID_ARG, "chain %d mixes grids or formats", c);
 
-    // launch geometry
+    // launch geometry: one launch per cluster size (skr_plan.h)
     const bool fp64 = opt.precision == SKR_PREC_FP64;
     const int threads = chain_threads();
-    int cs = opt.cluster_size;
-    if (cs == 0) {
-        cs = (int)std::min<long long>(8, std::max<long long>(1, (nmax + 8191) / 8192));
-    }
     const size_t smem = chain_smem_bytes(opt.m, opt.k, threads, fp64 ? 8 : 4);
     if (smem > 227 * 1024) return fail(SKR_ERR_INVALID_ARG, "m, k too large for shared memory (%zu bytes)", smem);
-    int maxc = fp64 ? max_active_clusters_f64(cs, threads, smem) : max_active_clusters_f32(cs, threads, smem);
-    if (maxc < 1) return fail(SKR_ERR_CUDA, "cluster of %d CTAs with %zu bytes of shared memory cannot be scheduled", cs, smem);
-    int nslots = std::min(nchains, maxc);
-    if (opt.max_slots > 0) nslots = std::min(nslots, opt.max_slots);
-    const long long ld = chain_ld(nmax, cs);
+    auto maxc = [&](int cs) {
+        return fp64 ? max_active_clusters_f64(cs, threads, smem) : max_active_clusters_f32(cs, threads, smem);
+    };
+    std::vector<LaunchClass> plan;
+    if (opt.cluster_size > 0) {
+        LaunchClass k;
+        k.cs = opt.cluster_size;
+        for (int c = 0; c < nchains; c++) k.chains.push_back(c);
+        const int mc = maxc(k.cs);
+        if (mc < 1)
+            return fail(SKR_ERR_CUDA, "cluster of %d CTAs with %zu bytes of shared memory cannot be scheduled", k.cs,
+                        smem);
+        k.slots = std::min(nchains, mc);
+        if (opt.max_slots > 0) k.slots = std::min(k.slots, opt.max_slots);
+        plan.push_back(k);
+    } else {
+        std::vector<long long> cn(nchains), cl(nchains);
+        for (int c = 0; c < nchains; c++) {
+            cn[c] = sys_n(systems[ord[off[c]]]);
+            cl[c] = off[c + 1] - off[c];
+        }
+        plan = plan_launches(cn, cl, maxc(1), maxc, opt.max_slots);
+        if (plan.empty()) return fail(SKR_ERR_CUDA, "no launch shape of the chain kernel can be scheduled");
+    }
+    const int nlaunch = (int)plan.size();
     const size_t esz = fp64 ? 8 : 4;
-    const long long nodecap = std::max<long long>(nodemax, 1);
-    const SlabLayout L = slab_layout(nslots, ld, nodecap, esz);
+    // per launch: its chains' order positions, offsets and workspace
+    struct LaunchGeo {
+        long long ld = 0, nodecap = 1, ord0 = 0, off0 = 0;
+        SlabLayout L;
+        size_t ws0 = 0;
+    };
+    std::vector<LaunchGeo> geo(nlaunch);
+    std::vector<int> ordk;
+    std::vector<long long> offk;
+    size_t wtotal = 0;
+    for (int li = 0; li < nlaunch; li++) {
+        LaunchGeo &g = geo[li];
+        long long nm = 1, nodem = 0;
+        g.ord0 = (long long)ordk.size();
+        g.off0 = (long long)offk.size();
+        offk.push_back(0);
+        for (int c : plan[li].chains) {
+            for (long long q = off[c]; q < off[c + 1]; q++) {
+                const skr_system &sy = systems[ord[q]];
+                nm = std::max(nm, sys_n(sy));
+                if (sy.fmt == SKR_FMT_DARCY2D || sy.fmt == SKR_FMT_DARCY3D) nodem = std::max(nodem, sys_coef_len(sy));
+                ordk.push_back(ord[q]);
+            }
+            offk.push_back((long long)ordk.size() - g.ord0);
+        }
+        g.ld = chain_ld(nm, plan[li].cs);
+        g.nodecap = std::max<long long>(nodem, 1);
+        g.L = slab_layout(plan[li].slots, g.ld, g.nodecap, esz);
+        g.ws0 = wtotal;
+        wtotal += (g.L.total + 255) / 256 * 256;
+    }
     void *wbase = nullptr;
-    CUDA_TRY(ws_get(L.total, &wbase));
+    CUDA_TRY(ws_get(wtotal, &wbase));
     char *wb = reinterpret_cast<char *>(wbase);
     // the basis must start zeroed: padded rows are never written by the passes that read them
-    CUDA_TRY(cudaMemsetAsync(wb + L.o_basis, 0, (size_t)nslots * NCOLS * ld * esz, st));
+    for (int li = 0; li < nlaunch; li++)
+        CUDA_TRY(cudaMemsetAsync(wb + geo[li].ws0 + geo[li].L.o_basis, 0,
+                                 (size_t)plan[li].slots * NCOLS * geo[li].ld * esz, st));
 
     // per-call device arrays
     std::vector<Staged> staged(N);
@@ -670,25 +749,23 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     } else {
         for (long long i = 0; i < N; i++) hsys[i].x_out = x_out[i];
     }
+    // counters: one chain counter per launch (64 bytes apart), then the
+    // algorithmic-bytes accumulator, then the per-phase accumulators
+    const size_t ctr_bytes = 64 * (size_t)nlaunch + 64 + 8 * SKR_NPHASE;
     DBuf dsys, dord, doff, dres, dctr;
     CUDA_TRY(dsys.alloc(sizeof(DevSystem) * N));
     CUDA_TRY(dord.alloc(sizeof(int) * N));
-    CUDA_TRY(doff.alloc(sizeof(long long) * (nchains + 1)));
+    CUDA_TRY(doff.alloc(sizeof(long long) * offk.size()));
     CUDA_TRY(dres.alloc(sizeof(DevResult) * N));
-    CUDA_TRY(dctr.alloc(64 + 8 * SKR_NPHASE));
+    CUDA_TRY(dctr.alloc(ctr_bytes));
     CUDA_TRY(cudaMemcpyAsync(dsys.p, hsys.data(), sizeof(DevSystem) * N, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(dord.p, ord.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(doff.p, off.data(), sizeof(long long) * (nchains + 1), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemsetAsync(dctr.p, 0, 64 + 8 * SKR_NPHASE, st));
+    CUDA_TRY(cudaMemcpyAsync(dord.p, ordk.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(doff.p, offk.data(), sizeof(long long) * offk.size(), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(dctr.p, 0, ctr_bytes, st));
     CUDA_TRY(cudaMemsetAsync(dres.p, 0, sizeof(DevResult) * N, st));
 
     ChainArgs a;
     a.systems = dsys.as<DevSystem>();
-    a.order = dord.as<int>();
-    a.chain_off = doff.as<long long>();
-    a.nchains = nchains;
-    a.chain_counter = dctr.as<int>();
-    a.ws = slab_bind(wb, L, nslots, ld, nodecap);
     a.results = dres.as<DevResult>();
     a.m = opt.m;
     a.k = opt.k;
@@ -698,27 +775,70 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     a.pc_blocks = opt.pc_blocks;
     a.tol = opt.tol;
     a.inner_tol = opt.inner_tol;
-    a.bytes = reinterpret_cast<unsigned long long *>(dctr.as<char>() + 32);
-    a.prof = opt.profile ? reinterpret_cast<unsigned long long *>(dctr.as<char>() + 64) : nullptr;
+    a.bytes = reinterpret_cast<unsigned long long *>(dctr.as<char>() + 64 * nlaunch);
+    a.prof = opt.profile ? reinterpret_cast<unsigned long long *>(dctr.as<char>() + 64 * nlaunch + 64) : nullptr;
     a.chain_kc = nullptr;
     a.warm_start = opt.warm_start;
     a.diagnostics = opt.diagnostics;
     a.chain_xok = nullptr;   // every chain of the call starts from x_0 = 0
-    if (encode_basis_maps(a.ws.basis, ld, nslots, (int)esz, a.tmap) != cudaSuccess)
-        return fail(SKR_ERR_CUDA, "TMA descriptors of the basis could not be encoded");
+    // recycle export: per launch, the caller's pointers in the launch's chain order
+    DBuf drec;
+    if (opt.recycle_out) {
+        std::vector<double *> rec;
+        for (int li = 0; li < nlaunch; li++)
+            for (int c : plan[li].chains) rec.push_back(opt.recycle_out[c]);
+        CUDA_TRY(drec.alloc(sizeof(double *) * rec.size()));
+        CUDA_TRY(cudaMemcpyAsync(drec.p, rec.data(), sizeof(double *) * rec.size(), cudaMemcpyHostToDevice, st));
+    }
+    std::vector<ChainArgs> args(nlaunch, a);
+    int rec0 = 0;
+    for (int li = 0; li < nlaunch; li++) {
+        ChainArgs &ak = args[li];
+        ak.order = dord.as<int>() + geo[li].ord0;
+        ak.chain_off = doff.as<long long>() + geo[li].off0;
+        ak.nchains = (int)plan[li].chains.size();
+        ak.chain_counter = reinterpret_cast<int *>(dctr.as<char>() + 64 * li);
+        ak.recycle_out = opt.recycle_out ? drec.as<double *>() + rec0 : nullptr;
+        rec0 += (int)plan[li].chains.size();
+        ak.ws = slab_bind(wb + geo[li].ws0, geo[li].L, plan[li].slots, geo[li].ld, geo[li].nodecap);
+        if (encode_basis_maps(ak.ws.basis, geo[li].ld, plan[li].slots, (int)esz, ak.tmap) != cudaSuccess)
+            return fail(SKR_ERR_CUDA, "TMA descriptors of the basis could not be encoded");
+    }
+    std::vector<cudaStream_t> lst(nlaunch, st);
+    if (nlaunch > 1) CUDA_TRY(launch_streams(nlaunch, lst.data()));
 
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
-    CUDA_TRY(cudaEventRecord(e0, st));
-    cudaError_t le = fp64 ? launch_chain_f64(a, nslots, cs, threads, smem, st)
-                          : launch_chain_f32(a, nslots, cs, threads, smem, st);
-    CUDA_TRY(cudaEventRecord(e1, st));
-    if (le != cudaSuccess) {
+    std::vector<cudaEvent_t> joins(nlaunch, nullptr);
+    auto drop_events = [&]() {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        for (cudaEvent_t ev : joins)
+            if (ev) cudaEventDestroy(ev);
+    };
+    CUDA_TRY(cudaEventRecord(e0, st));
+    cudaError_t le = cudaSuccess;
+    for (int li = 0; li < nlaunch && le == cudaSuccess; li++) {
+        if (lst[li] != st) {
+            le = cudaStreamWaitEvent(lst[li], e0, 0);
+            if (le != cudaSuccess) break;
+        }
+        le = fp64 ? launch_chain_f64(args[li], plan[li].slots, plan[li].cs, threads, smem, lst[li])
+                  : launch_chain_f32(args[li], plan[li].slots, plan[li].cs, threads, smem, lst[li]);
+        if (le == cudaSuccess && lst[li] != st) {
+            le = cudaEventCreateWithFlags(&joins[li], cudaEventDisableTiming);
+            if (le == cudaSuccess) le = cudaEventRecord(joins[li], lst[li]);
+            if (le == cudaSuccess) le = cudaStreamWaitEvent(st, joins[li], 0);
+        }
+    }
+    if (le != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        for (cudaStream_t s2 : lst) cudaStreamSynchronize(s2);
+        drop_events();
         return fail(SKR_ERR_CUDA, "chain kernel launch failed: %s", cudaGetErrorString(le));
     }
+    CUDA_TRY(cudaEventRecord(e1, st));
     std::vector<DevResult> hres(N);
     unsigned long long hbytes = 0;
     CUDA_TRY(cudaMemcpyAsync(hres.data(), dres.p, sizeof(DevResult) * N, cudaMemcpyDeviceToHost, st));
@@ -733,8 +853,7 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     cudaError_t se = cudaStreamSynchronize(st);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    drop_events();
     if (se != cudaSuccess) return fail(SKR_ERR_CUDA, "solve failed: %s", cudaGetErrorString(se));
     for (long long i = 0; i < N; i++) {
         skr_result &r = results[i];
@@ -752,9 +871,14 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     g_last.bytes = hbytes;
     for (int i = 0; i < SKR_NPHASE; i++) g_last.prof[i] = hprof[i];
     g_last.kernel_ms = ms;
-    g_last.cluster_size = cs;
-    g_last.slots = nslots;
-    g_last.launches = 1;
+    g_last.cluster_size = nlaunch == 1 ? plan[0].cs : 0;
+    g_last.slots = 0;
+    g_last.launches = nlaunch;
+    g_last.plan.clear();
+    for (const LaunchClass &k : plan) {
+        g_last.slots += k.slots;
+        g_last.plan.push_back({k.cs, k.slots, (int)k.chains.size()});
+    }
     return SKR_OK;
 }
 
@@ -765,6 +889,19 @@ skr_status skr_last_stats(uint64_t *bytes, double *kernel_ms, int32_t *cluster_s
     if (cluster_size) *cluster_size = g_last.cluster_size;
     if (slots) *slots = g_last.slots;
     if (launches) *launches = g_last.launches;
+    return SKR_OK;
+}
+
+skr_status skr_last_plan(int32_t *cluster_size, int32_t *clusters, int32_t *chains, int32_t cap,
+                         int32_t *nlaunch) {
+    if (cap < 0) return fail(SKR_ERR_INVALID_ARG, "cap < 0");
+    const int n = (int)g_last.plan.size();
+    for (int i = 0; i < n && i < cap; i++) {
+        if (cluster_size) cluster_size[i] = g_last.plan[i].cs;
+        if (clusters) clusters[i] = g_last.plan[i].slots;
+        if (chains) chains[i] = g_last.plan[i].chains;
+    }
+    if (nlaunch) *nlaunch = n;
     return SKR_OK;
 }
 

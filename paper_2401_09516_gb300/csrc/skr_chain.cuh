@@ -1413,6 +1413,26 @@ __device__ __noinline__ double recycle_delta(Ctx<T> &c, int kc_in) {
     return fail ? -1.0 : sqrt(fmin(fmax(lmax, 0.0), 1.0));
 }
 
+// Copy the chain's final recycle space out (this CTA's rows): U_k into
+// columns 0..k-1 and C_k into columns k..2k-1 of out (n doubles each),
+// zeros past the carried dimension.
+template <typename T>
+__device__ __noinline__ void export_recycle(Ctx<T> &c, double *out) {
+    __syncthreads();
+    const long long n = c.g.n;
+    const long long hi = min(c.lo + c.cnt, n);
+    for (int j = 0; j < c.k; j++) {
+        const bool have = j < c.kc;
+        const T *u = c.col(COL_U0 + j);
+        const T *cc = c.col(COL_C_END - c.kc + j);
+        for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
+            out[(long long)j * n + p] = have ? (double)u[p] : 0.0;
+            out[((long long)c.k + j) * n + p] = have ? (double)cc[p] : 0.0;
+        }
+    }
+    __syncthreads();
+}
+
 // Mixed form: recycle updates between two recomputations of C = A M^-1 U.
 constexpr int RECYCLE_REFRESH = 8;
 
@@ -1610,6 +1630,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS, CHAIN_MIN_BLOCKS) chain_kernel(
             solve_system(c, a, a.order[pos], a.warm_start && xok);
             xok = true;
         }
+        if (a.recycle_out) export_recycle(c, a.recycle_out[chain]);
         if (a.chain_kc && c.rank == 0 && threadIdx.x == 0) a.chain_kc[chain] = c.kc;
         if (a.chain_xok && c.rank == 0 && threadIdx.x == 0) a.chain_xok[chain] = 1;
     }

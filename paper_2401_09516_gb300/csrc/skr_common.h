@@ -90,6 +90,8 @@ struct ChainArgs {
     int pc_blocks;                // SKR_PC_BJACOBI: row blocks of the preconditioner
     int *chain_xok;               // per chain, optional: nonzero when the slot's x holds the
                                   // previous solution (read at chain start, set at chain end)
+    double *const *recycle_out = nullptr;   // per chain, optional: its final U_k then C_k,
+                                  // k columns of n doubles each (zero past the carried dimension)
     int *chain_kc;                // per-chain recycle dimension carried between launches
                                   // (optional: read at chain start, written at chain end;
                                   // the chain's U_k, C_k stay in its workspace slot)

@@ -28,6 +28,7 @@
 
 #include "skr_common.h"
 #include "skr_launch.h"
+#include "skr_plan.h"
 #include "skr_tma.h"
 #include "skr_workspace.h"
 
@@ -125,9 +126,12 @@ struct skr_server {
 
 namespace {
 
+// Cluster size of a chain of n unknowns: the caller's, else the one with the
+// least CTA time per Arnoldi step in the measured launch table (skr_plan.h),
+// which keeps the most requests running at once under load.
 int auto_cs(long long n, int requested) {
     if (requested > 0) return requested;
-    return (int)std::min<long long>(8, std::max<long long>(1, (n + 8191) / 8192));
+    return plan_efficient_cs(n);
 }
 
 struct ChainPlan {

@@ -699,3 +699,130 @@ def test_full_size_darcy256_in_the_bench_configuration(skr):
     for i in (int(perm[0]), int(perm[100]), int(perm[199])):
         A, b = assembly.darcy2d(L[i])
         _check_solution(xs[i], A, b, 1e-8, spla_solve(A, b), 1e-6)
+
+
+# ------------------------------------------------------------------ the recycle space itself (Sec. 4.2, App. B.1)
+
+def _gpu_recycle(skr, L, m, k, maxit, precision, cs):
+    side = L.shape[1] - 2
+    n = side * side
+    systems = [skr.darcy2d(_dev(l)) for l in L]
+    buf = torch.full((2 * k * n,), float("nan"), dtype=torch.float64, device=DEV)
+    opt = skr.skr_options_default(m=m, k=k, tol=1e-12, precond="jacobi", precision=precision, maxit=maxit,
+                                  cluster_size=cs)
+    _, res = skr.skr_solve_sequence(systems, nchains=1, options=opt, recycle_out=[buf])
+    R = buf.cpu().numpy().reshape(2 * k, n).T
+    return R[:, :k], R[:, k:], res[-1]["k_final"]
+
+
+def _oracle_recycle(L, m, k, maxit):
+    state = krylov.RecycleState()
+    for l in L:
+        A, b = assembly.darcy2d(l)
+        oskr.solve_system(A, b, "jacobi", m, k, 1e-12, state, precision="fp64", max_steps=maxit,
+                          grid=(l.shape[0] - 2, l.shape[1] - 2))
+    return state
+
+
+def _max_sine(X, Y):
+    import scipy.linalg as sla
+    return float(np.sin(np.max(sla.subspace_angles(X, Y))))
+
+
+@pytest.mark.parametrize("nsys", [1, 2])
+def test_recycle_space_invariants_and_oracle_subspace_fp64(skr, nsys):
+    # one full cycle per system (maxit = m): system 1 takes the "no recycle
+    # space" branch of Algorithm 2 (harmonic Ritz of H_m), system 2 the App.
+    # B.1 refresh and a cycle of the general branch; the exported U_k, C_k
+    # satisfy C^T C = I and A M^-1 U = C, and span the oracle's C_k
+    L = darcy2d_sequence(24, nsys, 0.2, seed=41)
+    m, k = 20, 6
+    U, C, kf = _gpu_recycle(skr, L, m, k, maxit=m, precision="fp64", cs=2)
+    state = _oracle_recycle(L, m, k, maxit=m)
+    assert kf == state.k == k
+    A, _ = assembly.darcy2d(L[-1])
+    Ahat = A @ np.diag(1.0 / A.diagonal())          # right Jacobi: A M^-1
+    assert np.abs(C.T @ C - np.eye(k)).max() <= 1e-12
+    assert np.linalg.norm(Ahat @ U - C) <= 1e-10 * np.linalg.norm(C)
+    assert _max_sine(C, state.C) <= 1e-6
+    assert _max_sine(U, state.U) <= 1e-6
+
+
+def test_recycle_space_invariants_mixed_after_a_converged_chain(skr):
+    # the mixed form stores U_k, C_k in FP32 and recomputes C = A M^-1 U at
+    # every refinement pass: after a converged chain of three systems the
+    # exported pair holds the invariants to FP32 accuracy
+    L = darcy2d_sequence(32, 3, 0.2, seed=42)
+    m, k = 30, 8
+    U, C, kf = _gpu_recycle(skr, L, m, k, maxit=10000, precision="mixed", cs=2)
+    assert 0 < kf <= k
+    U, C = U[:, :kf], C[:, :kf]
+    A, _ = assembly.darcy2d(L[-1])
+    Ahat = A @ np.diag(1.0 / A.diagonal())
+    assert np.abs(C.T @ C - np.eye(kf)).max() <= 2e-5
+    assert np.linalg.norm(Ahat @ U - C) <= 1e-4 * np.linalg.norm(C)
+
+
+def test_recycle_out_rejects_host_memory(skr):
+    L = darcy2d_sequence(8, 1, 0.2, seed=43)
+    opt = skr.skr_options_default(m=10, k=2, mem=1)
+    import ctypes
+    arr = (ctypes.c_void_p * 1)(1)
+    opt.recycle_out = ctypes.cast(arr, ctypes.c_void_p)
+    with pytest.raises(skr.SkrError):
+        skr.skr_solve_sequence([skr.darcy2d(L[0])], options=opt)
+
+
+# ------------------------------------------------------------------ full-size paths of the conv-diff and batched workloads
+
+def test_convdiff_ilu0_256_on_8_cta_clusters_matches_oracle(skr):
+    # red-black ILU(0) sweeps read neighbour rows of other CTAs through L2
+    # after a cluster barrier: at 256^2 on 8-CTA clusters that path runs on
+    # every sweep.  A sorted 3-system chain against the oracle, element-wise.
+    from workloads import convdiff_keys
+    nu, beta, f = convdiff2d_sequence(256, 3, seed=3)
+    order = osort.greedy_sort(convdiff_keys(nu, beta))
+    systems = [skr.convdiff2d(nu[i], beta[i], 256, rhs=_dev(f[i])) for i in range(3)]
+    opt = skr.skr_options_default(m=40, k=20, tol=1e-8, precond="ilu0", precision="mixed", cluster_size=8)
+    xs, res = skr.skr_solve_sequence(systems, order=order, options=opt)
+    assert skr.skr_last_stats()["cluster_size"] == 8
+    sysd = [dict(kind="convdiff2d", nu=nu[i], beta=beta[i], nside=256, rhs=f[i]) for i in range(3)]
+    xo, info = oskr.solve_sequence(sysd, order, "ilu0", 40, 20, 1e-8, precision="mixed")
+    for i in range(3):
+        A, b = assembly.convdiff2d(nu[i], beta[i], 256, rhs=f[i])
+        assert res[i]["flag"] == 0, res[i]
+        x = xs[i].cpu().numpy()
+        assert np.linalg.norm(b - A @ x) <= 1.01e-8 * np.linalg.norm(b)
+        # both solutions meet the residual tolerance; they agree to 1e-6
+        assert np.linalg.norm(x - xo[i]) <= 1e-6 * np.linalg.norm(xo[i]), i
+
+
+def test_batched_chains_of_sides_64_to_384_through_the_launch_planner(skr):
+    # chains of the batched workload's five grid sides in one call with
+    # cluster_size = 0: the planner makes one launch per cluster size; every
+    # system's true FP64 residual with the oracle's assembly, and sampled
+    # systems against a direct solve
+    from workloads import batched_chains
+    chains = batched_chains(6, 3, sides=(64, 128, 192, 256, 384), ell_range=(0.05, 0.3), seed=4)
+    systems, order, offs, fields = [], [], [0], []
+    for side, ell, sub in chains:
+        perm = osort.greedy_sort(sub.reshape(len(sub), -1))
+        base = len(systems)
+        for l in sub:
+            systems.append(skr.darcy2d(_dev(l)))
+            fields.append(l)
+        order += [base + p for p in perm]
+        offs.append(len(systems))
+    opt = skr.skr_options_default(m=40, k=20, tol=1e-8, precond="jacobi", precision="mixed", cluster_size=0)
+    xs, res = skr.skr_solve_sequence(systems, order=order, chain_offsets=offs, nchains=len(chains), options=opt)
+    plan = skr.skr_last_plan()
+    assert sum(p["chains"] for p in plan) == len(chains)
+    assert sum(p["clusters"] * p["cluster_size"] for p in plan) <= 152
+    for i, l in enumerate(fields):
+        A, b = assembly.darcy2d(l)
+        assert res[i]["flag"] == 0, (i, res[i])
+        assert np.linalg.norm(b - A @ xs[i].cpu().numpy()) <= 1.01e-8 * np.linalg.norm(b), i
+    sides = [l.shape[0] - 2 for l in fields]
+    for i in (sides.index(min(sides)), sides.index(max(sides))):
+        A, b = assembly.darcy2d(fields[i])
+        _check_solution(xs[i], A, b, 1e-8, spla_solve(A, b), 1e-6)

@@ -778,27 +778,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args):
-    """Serving: a seeded Poisson arrival stream of 2D and 3D Darcy requests
-    replayed in real time against the server (skr_server_*)."""
-    import torch
+SERVING_SIZES = {
+    # the request mix of the serving workload: 2D Darcy 128^2 - 1024^2 and
+    # 3D 7-point Darcy 64^3 - 128^3 (n up to 2.1M), half of each
+    "full": ((128, 256, 512, 1024), (64, 96, 128)),
+    # a mix that runs in seconds, for quick checks
+    "small": ((128, 256), (48, 64)),
+}
 
-    _, _, local = _dist()
-    torch.cuda.set_device(local)
-    import paper_2401_09516_gb300 as skr
-    from workloads import serving_stream
-    opts = skr.skr_options_default(m=40, k=20, tol=1e-8, inner_tol=1e-5, precond="jacobi", precision="mixed")
-    sides2d, sides3d = (128, 256), (48, 64)
-    reqs = serving_stream(args.serving_requests, args.serving_rate, seed=5, sides2d=sides2d, sides3d=sides3d)
-    systems = [skr.darcy3d(r["loga"]) if r["ndim"] == 3 else skr.darcy2d(r["loga"]) for r in reqs]
-    # warm-up on a server of its own (context, module load, first chains)
-    with skr.Server(opts) as srv:
-        for t in [srv.submit(systems[i]) for i in range(min(8, len(systems)))]:
-            srv.wait(t)
-    sampler = ClockSampler(local)
-    sampler.start()
+
+def _serve(skr, opts, reqs, systems, budget, max_chains):
+    """Replay the arrival stream in real time against one server; returns
+    (client latencies in ms, server stats, results, wall seconds, submit span)."""
     done, t_done = {}, {}
-    with skr.Server(opts) as srv:
+    with skr.Server(opts, hbm_budget=budget, max_chains=max_chains) as srv:
         tickets, pending = [], []
         t0 = time.perf_counter()
 
@@ -819,36 +812,76 @@ def run_serving(args):
             pending.append(t)
         submit_span = time.perf_counter() - t0
         while pending:
-            if time.perf_counter() - t0 > 600.0:
-                raise TimeoutError("serving stream not drained after 600 s")
+            if time.perf_counter() - t0 > 1800.0:
+                raise TimeoutError("serving stream not drained after 1800 s")
             collect()
             time.sleep(0.0002)
         elapsed = time.perf_counter() - t0
         st = srv.stats()
     # client view: from the scheduled arrival to the poll that returned the result
-    lat_client = sorted((t_done[t] - r["t"]) * 1e3 for r, t in zip(reqs, tickets))
-    pct = lambda q: lat_client[min(len(lat_client) - 1, int(round(q * (len(lat_client) - 1))))]   # noqa: E731
+    lat = sorted((t_done[t] - r["t"]) * 1e3 for r, t in zip(reqs, tickets))
+    return lat, st, [done[t][1] for t in tickets], elapsed, submit_span
+
+
+def _serving_summary(reqs, lat, st, res, elapsed, submit_span):
+    pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]   # noqa: E731
+    return {"value": round(len(reqs) / elapsed, 3), "wall_s": round(elapsed, 2),
+            "latency_ms": {"p50": round(pct(0.50), 1), "p99": round(pct(0.99), 1),
+                           "mean": round(sum(lat) / len(lat), 1),
+                           "measured": "scheduled arrival to the poll that returned the result"},
+            "server_latency_ms": {"p50": round(st["p50_ms"], 1), "p99": round(st["p99_ms"], 1),
+                                  "measured": "skr_submit return to completion, by the server"},
+            "avg_steps": round(sum(r["steps"] for r in res) / len(res), 1),
+            "flags": sorted({r["flag"] for r in res}), "max_relres": max(r["relres"] for r in res),
+            "chains": st["chains"], "evicted": st["evicted"], "submit_span_s": round(submit_span, 3)}
+
+
+def run_serving(args):
+    """Serving: a seeded Poisson arrival stream of 2D and 3D Darcy requests
+    replayed in real time against the server (skr_server_*), with recycling
+    (SKR) and, unless --serving-no-plain, again as plain GMRES (k = 0)."""
+    import torch
+
+    _, _, local = _dist()
+    torch.cuda.set_device(local)
+    import paper_2401_09516_gb300 as skr
+    from workloads import serving_stream
+    sides2d, sides3d = SERVING_SIZES[args.serving_sizes]
+    reqs = serving_stream(args.serving_requests, args.serving_rate, seed=5, sides2d=sides2d, sides3d=sides3d)
+    systems = [skr.darcy3d(r["loga"]) if r["ndim"] == 3 else skr.darcy2d(r["loga"]) for r in reqs]
+
+    def opts(k):
+        return skr.skr_options_default(m=40, k=k, tol=1e-8, inner_tol=1e-5, precond="jacobi", precision="mixed",
+                                       maxit=args.maxit)
+
+    # warm-up on a server of its own (context, module load, first chains)
+    with skr.Server(opts(20)) as srv:
+        for t in [srv.submit(systems[i]) for i in range(min(4, len(systems)))]:
+            srv.wait(t, timeout=600.0)
+    budget = int(args.serving_budget_gb * 2**30)
+    sampler = ClockSampler(local)
+    sampler.start()
+    skr_arm = _serving_summary(reqs, *_serve(skr, opts(20), reqs, systems, budget, args.serving_chains))
+    plain = None
+    if args.serving_plain:
+        plain = _serving_summary(reqs, *_serve(skr, opts(0), reqs, systems, budget, args.serving_chains))
     clocks = sampler.stop()
-    flags = sorted({res["flag"] for _, res in done.values()})
-    worst = max(res["relres"] for _, res in done.values())   # true FP64 residuals of the results
     n3 = sum(1 for r in reqs if r["ndim"] == 3)
     line = {
-        "metric": "serving: completed systems/s and submit-to-completion p50/p99 under Poisson arrivals",
-        "value": round(len(reqs) / elapsed, 2), "unit": "systems/s", "n_gpus": 1,
-        "steps": 1, "warmup": 1, "ms_per_step": round(elapsed * 1e3, 1), "higher_is_better": True,
+        "metric": "serving: completed systems/s and arrival-to-result p50/p99 under Poisson arrivals, SKR vs plain GMRES",
+        "value": skr_arm["value"], "unit": "systems/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": round(skr_arm["wall_s"] * 1e3, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": "%d Darcy requests, Poisson arrivals at %.0f/s (seed 5): %d 2D (sides %s), %d 3D "
-                               "(sides %s), a=exp(GRF ell=0.1 sigma=1), Jacobi, GCRO-DR m=40 k=20, mixed, tol 1e-8"
+        "config": {"workload": "the first %d requests of the seeded Darcy stream (seed 5), Poisson arrivals at %.0f/s: "
+                               "%d 2D (sides %s), %d 3D 7-point (sides %s), a=exp(GRF ell=0.1 sigma=1), Jacobi, "
+                               "GCRO-DR m=40 k=20, mixed, tol 1e-8"
                                % (len(reqs), args.serving_rate, len(reqs) - n3, list(sides2d), n3, list(sides3d)),
-                   "chains": st["chains"]},
-        "latency_ms": {"p50": round(pct(0.50), 2), "p99": round(pct(0.99), 2),
-                       "mean": round(sum(lat_client) / len(lat_client), 2),
-                       "measured": "scheduled arrival to the poll that returned the result"},
-        "server_latency_ms": {"p50": round(st["p50_ms"], 2), "p99": round(st["p99_ms"], 2),
-                              "measured": "skr_submit return to completion, by the server"},
-        "arrival_span_s": round(reqs[-1]["t"], 3), "submit_span_s": round(submit_span, 3),
-        "flags": flags, "max_relres": worst,
-        "gpu_launches": len(reqs), "clocks": clocks,
+                   "hbm_budget_gb": args.serving_budget_gb or None, "max_chains": args.serving_chains or 64,
+                   "arrival_span_s": round(reqs[-1]["t"], 3)},
+        "skr": skr_arm, "plain_gmres": plain,
+        "speedup_vs_gmres": None if plain is None else round(skr_arm["value"] / plain["value"], 3),
+        "latency_ms": skr_arm["latency_ms"],
+        "gpu_launches": len(reqs) * (2 if plain else 1), "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
 
@@ -970,8 +1003,16 @@ def main():
     ap.add_argument("--group-max", type=int, default=1000, help="largest group for --sort-only")
     ap.add_argument("--serving", action="store_true",
                     help="replay a Poisson arrival stream against the serving loop instead of the batch")
-    ap.add_argument("--serving-requests", type=int, default=300)
-    ap.add_argument("--serving-rate", type=float, default=100.0, help="arrivals per second")
+    ap.add_argument("--serving-requests", type=int, default=200,
+                    help="prefix of the seeded request stream to replay")
+    ap.add_argument("--serving-rate", type=float, default=200.0, help="arrivals per second")
+    ap.add_argument("--serving-sizes", default="full", choices=sorted(SERVING_SIZES),
+                    help="full: 2D 128^2-1024^2 and 3D 64^3-128^3; small: a mix that runs in seconds")
+    ap.add_argument("--serving-budget-gb", type=float, default=0.0,
+                    help="device-memory budget of the server in GiB (0 = none)")
+    ap.add_argument("--serving-chains", type=int, default=0, help="resident chain limit (0 = 64)")
+    ap.add_argument("--serving-no-plain", dest="serving_plain", action="store_false",
+                    help="skip the plain-GMRES replay of the same stream")
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="upper bound on one reference sample")
     args = ap.parse_args()

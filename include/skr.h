@@ -76,6 +76,15 @@ typedef int32_t skr_status;
                                      nx*ny interior nodes.  Indefinite once k^2 exceeds the smallest
                                      eigenvalues of the discrete -lap (2 pi^2 for the unit square) */
 
+#define SKR_FMT_CSR           8   /* an assembled sparse matrix in compressed sparse row form (Sec. 3.1's
+                                     A: any numbering of the unknowns): nx = n rows (ny = nz = 1);
+                                     rowptr = n + 1 int64 offsets (rowptr[0] = 0), colind = int32 column
+                                     indices, coef = the values (rowptr[n] doubles); every row holds its
+                                     diagonal once and at most SKR_CSR_MAX_ROW entries in all, no column
+                                     twice, columns in [0, n).  Preconditioners: SKR_PC_NONE and
+                                     SKR_PC_JACOBI (the colour sweeps need a grid) */
+#define SKR_CSR_MAX_ROW       7   /* entries per CSR row (the 5- and 7-point stencils fit) */
+
 /* right preconditioner M (App. D.3): the Krylov method solves A M^-1 y = b, x = M^-1 y */
 #define SKR_PC_NONE           0
 #define SKR_PC_JACOBI         1   /* M = diag(A) */
@@ -111,6 +120,8 @@ typedef struct skr_system {
     const double *coef;     /* format data, see SKR_FMT_* (NULL for CONVDIFF2D) */
     const double *rhs;      /* f at the n unknowns, or NULL for f = 1 */
     double params[4];       /* CONVDIFF2D: nu, beta_x, beta_y; otherwise unused */
+    const int64_t *rowptr;  /* CSR: n + 1 row offsets; otherwise unused */
+    const int32_t *colind;  /* CSR: column index of every value; otherwise unused */
 } skr_system;
 
 typedef struct skr_options {

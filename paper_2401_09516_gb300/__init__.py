@@ -9,6 +9,7 @@ from ._native import (  # noqa: F401
     System,
     SkrError,
     convdiff2d,
+    csr,
     darcy2d,
     darcy3d,
     helmholtz2d,

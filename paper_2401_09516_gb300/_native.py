@@ -34,6 +34,8 @@ SKR_FMT_STENCIL5 = 4
 SKR_FMT_STENCIL7 = 5
 SKR_FMT_HELMHOLTZ2D = 6
 SKR_FMT_POISSON2D = 7
+SKR_FMT_CSR = 8
+SKR_CSR_MAX_ROW = 7
 SKR_PC_NONE = 0
 SKR_PC_JACOBI = 1
 SKR_PC_ILU0 = 2
@@ -54,7 +56,7 @@ PRECISION = {"fp64": SKR_PREC_FP64, "mixed": SKR_PREC_MIXED}
 class SkrSystem(ctypes.Structure):
     _fields_ = [("fmt", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("nz", ctypes.c_int32), ("coef", ctypes.c_void_p), ("rhs", ctypes.c_void_p),
-                ("params", ctypes.c_double * 4)]
+                ("params", ctypes.c_double * 4), ("rowptr", ctypes.c_void_p), ("colind", ctypes.c_void_p)]
 
 
 class SkrOptions(ctypes.Structure):
@@ -173,6 +175,15 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _int(a, bits):
+    if _is_device(a):
+        want = "torch.int64" if bits == 64 else "torch.int32"
+        if str(a.dtype) != want or not a.is_contiguous():
+            raise ValueError("device index arrays must be contiguous int%d" % bits)
+        return a
+    return np.ascontiguousarray(a, dtype=np.int64 if bits == 64 else np.int32)
+
+
 def skr_last_error():
     return _lib.skr_last_error().decode()
 
@@ -199,9 +210,12 @@ def skr_options_default(**overrides):
 class System:
     """One system of the sequence; keeps its arrays alive for the call."""
 
-    def __init__(self, fmt, nx, ny, nz=1, coef=None, rhs=None, params=(0.0, 0.0, 0.0, 0.0)):
+    def __init__(self, fmt, nx, ny, nz=1, coef=None, rhs=None, params=(0.0, 0.0, 0.0, 0.0), rowptr=None,
+                 colind=None):
         self.coef = None if coef is None else _f64(coef)
         self.rhs = None if rhs is None else _f64(rhs)
+        self.rowptr = None if rowptr is None else _int(rowptr, 64)
+        self.colind = None if colind is None else _int(colind, 32)
         self.fmt, self.nx, self.ny, self.nz = int(fmt), int(nx), int(ny), int(nz)
         self.params = tuple(float(p) for p in params) + (0.0,) * (4 - len(params))
         self.n = self.nx * self.ny * (self.nz if fmt in (SKR_FMT_DARCY3D, SKR_FMT_STENCIL7) else 1)
@@ -211,12 +225,14 @@ class System:
         s.fmt, s.nx, s.ny, s.nz = self.fmt, self.nx, self.ny, self.nz
         s.coef = _ptr(self.coef)
         s.rhs = _ptr(self.rhs)
+        s.rowptr = _ptr(self.rowptr)
+        s.colind = _ptr(self.colind)
         for i in range(4):
             s.params[i] = self.params[i]
         return s
 
     def arrays(self):
-        return [self.coef, self.rhs]
+        return [self.coef, self.rhs, self.rowptr, self.colind]
 
 
 def darcy2d(loga, rhs=None):
@@ -248,6 +264,14 @@ def poisson2d(f, g):
         import torch
         coef = torch.cat([t.to(torch.float64) for t in parts])
     return System(SKR_FMT_POISSON2D, nx, ny, 1, coef, None)
+
+
+def csr(indptr, indices, data, rhs=None):
+    """System from an assembled sparse matrix in CSR form (e.g. a scipy
+    csr_matrix's indptr, indices, data): at most SKR_CSR_MAX_ROW entries per
+    row, the diagonal among them.  Host (numpy) or device (torch) arrays."""
+    n = int(indptr.shape[0]) - 1
+    return System(SKR_FMT_CSR, n, 1, 1, data, rhs, rowptr=indptr, colind=indices)
 
 
 def convdiff2d(nu, beta, nside, rhs=None):

@@ -119,6 +119,7 @@ cudaError_t launch_streams(int count, cudaStream_t *out) {
 bool is_3d(int fmt) { return fmt == SKR_FMT_DARCY3D || fmt == SKR_FMT_STENCIL7; }
 
 long long sys_n(const skr_system &s) {
+    if (s.fmt == SKR_FMT_CSR) return (long long)s.nx;
     return (long long)s.nx * s.ny * (is_3d(s.fmt) ? s.nz : 1);
 }
 
@@ -131,13 +132,19 @@ long long sys_coef_len(const skr_system &s) {
         case SKR_FMT_STENCIL7: return 7 * n;
         case SKR_FMT_HELMHOLTZ2D: return n;
         case SKR_FMT_POISSON2D: return n + 2LL * (s.nx + s.ny);
-        default: return 0;
+        default: return 0;   // CSR: the value count lives in rowptr[n]
     }
 }
 
 skr_status check_system(const skr_system &s, long long idx) {
-    if (s.fmt < SKR_FMT_DARCY2D || s.fmt > SKR_FMT_POISSON2D)
+    if (s.fmt < SKR_FMT_DARCY2D || s.fmt > SKR_FMT_CSR)
         return fail(SKR_ERR_INVALID_ARG, "system %lld: unknown format %d", idx, s.fmt);
+    if (s.fmt == SKR_FMT_CSR) {
+        if (s.nx < 1) return fail(SKR_ERR_INVALID_ARG, "system %lld: CSR with no rows", idx);
+        if (!s.rowptr || !s.colind || !s.coef)
+            return fail(SKR_ERR_INVALID_ARG, "system %lld: CSR needs rowptr, colind and coef (the values)", idx);
+        return SKR_OK;
+    }
     if (s.nx < 1 || s.ny < 1 || (is_3d(s.fmt) && s.nz < 1))
         return fail(SKR_ERR_INVALID_ARG, "system %lld: empty grid", idx);
     if (s.fmt == SKR_FMT_CONVDIFF2D && s.nx != s.ny)
@@ -154,6 +161,7 @@ skr_status check_system(const skr_system &s, long long idx) {
 }
 
 bool same_shape(const skr_system &a, const skr_system &b) {
+    if (a.fmt == SKR_FMT_CSR || b.fmt == SKR_FMT_CSR) return a.fmt == b.fmt && a.nx == b.nx;
     return a.fmt == b.fmt && a.nx == b.nx && a.ny == b.ny && (!is_3d(a.fmt) || a.nz == b.nz);
 }
 
@@ -164,7 +172,7 @@ int grid_for(long long n, int threads) {
 
 // Stage one system's data on the device when mem == HOST.
 struct Staged {
-    DBuf coef, rhs;
+    DBuf coef, rhs, rowptr, colind;
     DevSystem dev;
 };
 
@@ -175,7 +183,30 @@ skr_status stage_system(const skr_system &s, int mem, cudaStream_t st, Staged &o
     out.dev.nz = is_3d(s.fmt) ? s.nz : 1;
     for (int i = 0; i < 4; i++) out.dev.params[i] = s.params[i];
     out.dev.x_out = nullptr;
-    const long long clen = sys_coef_len(s), n = sys_n(s);
+    const long long n = sys_n(s);
+    long long clen = sys_coef_len(s);
+    out.dev.rowptr = nullptr;
+    out.dev.colind = nullptr;
+    out.dev.csr_w = 0;
+    if (s.fmt == SKR_FMT_CSR) {
+        out.dev.ny = out.dev.nz = 1;
+        if (mem == SKR_MEM_HOST) {
+            const long long nnz = s.rowptr[n];
+            if (nnz < n || nnz > (long long)SKR_CSR_MAX_ROW * n)
+                return fail(SKR_ERR_INVALID_ARG, "CSR: rowptr[n] = %lld is not a value count of n = %lld rows "
+                            "with 1..%d entries each", nnz, n, SKR_CSR_MAX_ROW);
+            clen = nnz;
+            CUDA_TRY(out.rowptr.alloc((n + 1) * 8));
+            CUDA_TRY(cudaMemcpyAsync(out.rowptr.p, s.rowptr, (n + 1) * 8, cudaMemcpyHostToDevice, st));
+            CUDA_TRY(out.colind.alloc(nnz * 4));
+            CUDA_TRY(cudaMemcpyAsync(out.colind.p, s.colind, nnz * 4, cudaMemcpyHostToDevice, st));
+            out.dev.rowptr = out.rowptr.as<long long>();
+            out.dev.colind = out.colind.as<int>();
+        } else {
+            out.dev.rowptr = reinterpret_cast<const long long *>(s.rowptr);
+            out.dev.colind = s.colind;
+        }
+    }
     if (mem == SKR_MEM_HOST) {
         if (clen > 0) {
             CUDA_TRY(out.coef.alloc(clen * 8));
@@ -190,6 +221,38 @@ skr_status stage_system(const skr_system &s, int mem, cudaStream_t st, Staged &o
     } else {
         out.dev.coef = s.coef;
         out.dev.rhs = s.rhs;
+    }
+    return SKR_OK;
+}
+
+// Check the CSR systems among hs (device descriptors; ns[i] rows) with one
+// kernel each and a single read-back, and set their row width.
+skr_status check_csr(std::vector<DevSystem> &hs, const std::vector<long long> &ns, cudaStream_t st) {
+    std::vector<int> idx;
+    for (size_t i = 0; i < hs.size(); i++)
+        if (hs[i].fmt == SKR_FMT_CSR) idx.push_back((int)i);
+    if (idx.empty()) return SKR_OK;
+    DBuf dout;
+    CUDA_TRY(dout.alloc(sizeof(int) * 2 * idx.size()));
+    CUDA_TRY(cudaMemsetAsync(dout.p, 0, sizeof(int) * 2 * idx.size(), st));
+    for (size_t q = 0; q < idx.size(); q++) {
+        const long long n = ns[idx[q]];
+        skr_csr_check_kernel<<<grid_for(n, 256), 256, 0, st>>>(hs[idx[q]].rowptr, hs[idx[q]].colind, n,
+                                                               dout.as<int>() + 2 * q);
+    }
+    CUDA_TRY(cudaGetLastError());
+    std::vector<int> h(2 * idx.size());
+    CUDA_TRY(cudaMemcpyAsync(h.data(), dout.p, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (size_t q = 0; q < idx.size(); q++) {
+        const int e = h[2 * q];
+        if (e & 1)
+            return fail(SKR_ERR_INVALID_ARG, "system %d: CSR rowptr not ascending from 0, or a row with no entry "
+                        "or more than %d", idx[q], SKR_CSR_MAX_ROW);
+        if (e & 2) return fail(SKR_ERR_INVALID_ARG, "system %d: CSR row without exactly one diagonal entry", idx[q]);
+        if (e & 4) return fail(SKR_ERR_INVALID_ARG, "system %d: CSR column index outside [0, n)", idx[q]);
+        if (e & 8) return fail(SKR_ERR_INVALID_ARG, "system %d: CSR column repeated within a row", idx[q]);
+        hs[idx[q]].csr_w = h[2 * q + 1];
     }
     return SKR_OK;
 }
@@ -482,6 +545,7 @@ skr_status skr_assemble(const skr_system *sys, int32_t mem, void *stream, double
     if (!sys) return fail(SKR_ERR_INVALID_ARG, "sys is NULL");
     skr_status s0 = check_system(*sys, 0);
     if (s0 != SKR_OK) return s0;
+    if (sys->fmt == SKR_FMT_CSR) return fail(SKR_ERR_INVALID_ARG, "a CSR system is already assembled");
     cudaStream_t st = (cudaStream_t)stream;
     Staged sg;
     s0 = stage_system(*sys, mem, st, sg);
@@ -497,7 +561,7 @@ skr_status skr_assemble(const skr_system *sys, int32_t mem, void *stream, double
     CUDA_TRY(A.alloc((size_t)g.nst * g.n * 8));
     CUDA_TRY(b.alloc((size_t)g.n * 8));
     rows_kernel<<<grid_for(g.n, 256), 256, 0, st>>>(sg.dev, g, anode.as<double>(), A.as<double>(), g.n,
-                                                     b.as<double>(), nullptr, SKR_PC_NONE);
+                                                     b.as<double>(), nullptr, SKR_PC_NONE, nullptr);
     CUDA_TRY(cudaGetLastError());
     const cudaMemcpyKind kind = (mem == SKR_MEM_HOST) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (coef_out) CUDA_TRY(cudaMemcpyAsync(coef_out, A.p, (size_t)g.nst * g.n * 8, kind, st));
@@ -518,11 +582,22 @@ skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t pc_blocks, 
     if (precond == SKR_PC_BJACOBI && pc_blocks < 1) return fail(SKR_ERR_INVALID_ARG, "pc_blocks < 1");
     if (precision != SKR_PREC_FP64 && precision != SKR_PREC_MIXED)
         return fail(SKR_ERR_INVALID_ARG, "bad precision");
+    if (sys->fmt == SKR_FMT_CSR && colour_sweep_pc(precond))
+        return fail(SKR_ERR_INVALID_ARG, "CSR input takes SKR_PC_NONE or SKR_PC_JACOBI only");
     cudaStream_t st = (cudaStream_t)stream;
     Staged sg;
     s0 = stage_system(*sys, mem, st, sg);
     if (s0 != SKR_OK) return s0;
-    const Geom g = make_geom(sys->fmt, sys->nx, sys->ny, sys->nz);
+    DBuf cols;
+    Geom g = make_geom(sys->fmt, sys->nx, sys->ny, sys->nz);
+    if (sys->fmt == SKR_FMT_CSR) {
+        std::vector<DevSystem> one(1, sg.dev);
+        s0 = check_csr(one, std::vector<long long>(1, sys_n(*sys)), st);
+        if (s0 != SKR_OK) return s0;
+        sg.dev.csr_w = one[0].csr_w;
+        CUDA_TRY(cols.alloc((size_t)one[0].csr_w * sys_n(*sys) * 4));
+        g = make_csr_geom(sys_n(*sys), one[0].csr_w, cols.as<int>(), sys_n(*sys));
+    }
     DBuf anode, A, dinv, Aw, vw, dv, dy;
     long long nn = (sys->fmt == SKR_FMT_DARCY2D || sys->fmt == SKR_FMT_DARCY3D) ? sys_coef_len(*sys) : 0;
     if (nn > 0) {
@@ -533,7 +608,8 @@ skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t pc_blocks, 
     CUDA_TRY(A.alloc((size_t)g.nst * g.n * 8));
     CUDA_TRY(dinv.alloc((size_t)g.n * 8));
     rows_kernel<<<grid_for(g.n, 256), 256, 0, st>>>(sg.dev, g, anode.as<double>(), A.as<double>(), g.n, nullptr,
-                                                     dinv.as<double>(), colour_sweep_pc(precond) ? SKR_PC_NONE : precond);
+                                                     dinv.as<double>(), colour_sweep_pc(precond) ? SKR_PC_NONE : precond,
+                                                     cols.as<int>());
     CUDA_TRY(cudaGetLastError());
     const double *vin = v;
     double *yout = y;
@@ -660,6 +736,10 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
         for (long long q = off[c] + 1; q < off[c + 1]; q++)
             if (!same_shape(systems[ord[q]], systems[ord[off[c]]]))
                 return fail(SKR_ERR_INVALID_ARG, "chain %d mixes grids or formats", c);
+    if (colour_sweep_pc(opt.precond))
+        for (long long i = 0; i < N; i++)
+            if (systems[i].fmt == SKR_FMT_CSR)
+                return fail(SKR_ERR_INVALID_ARG, "CSR input takes SKR_PC_NONE or SKR_PC_JACOBI only");
 
     // launch geometry: one launch per cluster size (skr_plan.h)
     const bool fp64 = opt.precision == SKR_PREC_FP64;
@@ -705,6 +785,7 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     for (int li = 0; li < nlaunch; li++) {
         LaunchGeo &g = geo[li];
         long long nm = 1, nodem = 0;
+        bool csr = false;
         g.ord0 = (long long)ordk.size();
         g.off0 = (long long)offk.size();
         offk.push_back(0);
@@ -713,13 +794,14 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
                 const skr_system &sy = systems[ord[q]];
                 nm = std::max(nm, sys_n(sy));
                 if (sy.fmt == SKR_FMT_DARCY2D || sy.fmt == SKR_FMT_DARCY3D) nodem = std::max(nodem, sys_coef_len(sy));
+                csr = csr || sy.fmt == SKR_FMT_CSR;
                 ordk.push_back(ord[q]);
             }
             offk.push_back((long long)ordk.size() - g.ord0);
         }
         g.ld = chain_ld(nm, plan[li].cs);
         g.nodecap = std::max<long long>(nodem, 1);
-        g.L = slab_layout(plan[li].slots, g.ld, g.nodecap, esz);
+        g.L = slab_layout(plan[li].slots, g.ld, g.nodecap, esz, csr);
         g.ws0 = wtotal;
         wtotal += (g.L.total + 255) / 256 * 256;
     }
@@ -748,6 +830,12 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
         }
     } else {
         for (long long i = 0; i < N; i++) hsys[i].x_out = x_out[i];
+    }
+    {
+        std::vector<long long> ns(N);
+        for (long long i = 0; i < N; i++) ns[i] = sys_n(systems[i]);
+        skr_status s0 = check_csr(hsys, ns, st);
+        if (s0 != SKR_OK) return s0;
     }
     // counters: one chain counter per launch (64 bytes apart), then the
     // algorithmic-bytes accumulator, then the per-phase accumulators

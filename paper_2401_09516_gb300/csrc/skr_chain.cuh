@@ -200,6 +200,7 @@ struct Ctx {
     double *A64;
     T *Aw;
     double *dinv, *x, *r, *b, *anode;
+    int *cols;   // CSR input: the slot's column indices (nullptr without that room)
     // parameters
     int m, k, maxit, precond, pc_blocks;
     long long pc_bs;   // rows per block of the colour sweeps (n unless block-Jacobi)
@@ -242,6 +243,12 @@ struct Ctx {
     __device__ int *ints() const { return reinterpret_cast<int *>(sm + P.o_int); }
     __device__ float *mon() const { return reinterpret_cast<float *>(sm + P.o_mon); }
 };
+
+// Bytes of the column indices one pass over a CSR operator reads (0 for grids).
+template <typename T>
+__device__ __forceinline__ unsigned long long csr_index_bytes(const Ctx<T> &c) {
+    return c.g.cols ? (unsigned long long)c.g.nst * c.g.n * 4 : 0ull;
+}
 
 // Sum the CTA partials red<R>()[0..nv) over the cluster into vals<R>().
 // One cluster barrier; the reduction buffers alternate so that the next
@@ -596,7 +603,7 @@ __device__ void spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
     // is a multiple of E, so all loads are 16-byte vectors
     const int last = (c.g.nst == 5) ? c.g.ny : c.g.nz;
     const int sL = (c.g.nst == 5) ? 3 : 5;   // slots of the -1 / +1 neighbours
-    if (last % E == 0) {
+    if (!c.g.cols && last % E == 0) {
         const long long n = c.g.n;
         for (long long p = c.lo + (long long)E * threadIdx.x; p < hi; p += (long long)E * blockDim.x) {
             if (p >= n) {
@@ -666,7 +673,7 @@ __device__ void spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
     }
     __syncthreads();
     c.bytes += (unsigned long long)(3 + (vout ? 1 : 0) + c.g.nst) * c.g.n * sizeof(T) -
-               (unsigned long long)(vout ? 0 : 1) * c.g.n * sizeof(T);
+               (unsigned long long)(vout ? 0 : 1) * c.g.n * sizeof(T) + csr_index_bytes(c);
 }
 
 // Operator pass with the red-black ILU(0) right preconditioner:
@@ -785,7 +792,13 @@ __device__ __noinline__ void assemble_system(Ctx<T> &c, const DevSystem &sys) {
     for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
         if (p < c.g.n) {
             double row[7];
-            system_row(sys, c.g, c.anode, p, row);
+            if (sys.fmt == SKR_FMT_CSR) {
+                int ci[7];
+                csr_row(sys, p, c.g.nst, row, ci);
+                for (int s = 0; s < c.g.nst; s++) c.cols[(long long)s * c.ld + p] = ci[s];
+            } else {
+                system_row(sys, c.g, c.anode, p, row);
+            }
             for (int s = 0; s < c.g.nst; s++) c.A64[(long long)s * c.ld + p] = row[s];
             c.b[p] = system_rhs(sys, c.g, p);
             c.dinv[p] = (c.precond == SKR_PC_NONE) ? 1.0 : 1.0 / row[0];
@@ -826,7 +839,7 @@ __device__ __noinline__ void assemble_system(Ctx<T> &c, const DevSystem &sys) {
     }
     __syncthreads();
     c.bytes += (unsigned long long)c.g.n * (8 * (c.g.nst + 3) + sizeof(T) * c.g.nst) +
-               (unsigned long long)nn * 16;
+               (unsigned long long)nn * 16 + csr_index_bytes(c) * 2;
 }
 
 // True residual r = b - A x (FP64) over own rows; returns ||r|| (cluster-wide).
@@ -843,7 +856,7 @@ __device__ __noinline__ double true_residual(Ctx<T> &c) {
     }
     block_sum<1>(acc, 1, c.D(c.P.o_wsum), c.template red<double>());
     allreduce<T, double>(c, 1);
-    c.bytes += (unsigned long long)c.g.n * 8 * (c.g.nst + 3);
+    c.bytes += (unsigned long long)c.g.n * 8 * (c.g.nst + 3) + csr_index_bytes(c);
     return sqrt(c.template vals<double>()[0]);
 }
 
@@ -882,7 +895,7 @@ __device__ __noinline__ void refresh_recycle(Ctx<T> &c) {
     }
     __syncthreads();
     c.matvecs += kc;
-    c.bytes += (unsigned long long)c.g.n * sizeof(T) * (c.g.nst + 2 * kc);
+    c.bytes += (unsigned long long)c.g.n * sizeof(T) * (c.g.nst + 2 * kc) + csr_index_bytes(c);
     double *G = c.D(c.P.o_F);
     double *R = c.D(c.P.o_Z);
     double *Ri = c.D(c.P.o_Z) + kc * kc;
@@ -1440,7 +1453,8 @@ template <typename T>
 __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx, bool warm) {
     const DevSystem sys = a.systems[sysidx];
     const unsigned long long t0 = global_ns();
-    c.g = make_geom(sys.fmt, sys.nx, sys.ny, sys.nz);
+    c.g = (sys.fmt == SKR_FMT_CSR) ? make_csr_geom(sys.nx, sys.csr_w, c.cols, c.ld)
+                                   : make_geom(sys.fmt, sys.nx, sys.ny, sys.nz);
     c.pc_bs = sweep_block_rows(c.precond, c.g.n, c.pc_blocks);
     const long long chunk = (((c.g.n + c.cs - 1) / c.cs) + 7) / 8 * 8;
     c.lo = (long long)c.rank * chunk;
@@ -1598,6 +1612,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS, CHAIN_MIN_BLOCKS) chain_kernel(
     c.r = a.ws.r + (long long)slot * c.ld;
     c.b = a.ws.b + (long long)slot * c.ld;
     c.anode = a.ws.anode + (long long)slot * a.ws.nodecap;
+    c.cols = a.ws.cols ? a.ws.cols + (long long)slot * 7 * c.ld : nullptr;
     c.bytes = 0;
     c.prof = a.prof;
     c.tmark = 0;

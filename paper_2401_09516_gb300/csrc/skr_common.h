@@ -50,6 +50,9 @@ struct DevSystem {
     const double *rhs;
     double params[4];
     double *x_out;
+    const long long *rowptr = nullptr;   // CSR input
+    const int *colind = nullptr;
+    int csr_w = 0;                        // CSR: entries of the longest row (<= SKR_CSR_MAX_ROW)
 };
 
 // Per-system outcome written by the kernel (mirrors skr_result).
@@ -68,6 +71,7 @@ struct Workspace {
     double *dinv;             // ld per slot (Jacobi: 1/diag, else 1)
     double *x, *r, *b;        // ld per slot each (FP64 solution, residual, rhs)
     double *anode;            // node scratch per slot (exp(log a)), nodecap doubles
+    int *cols = nullptr;      // CSR input: 7 * ld column indices per slot (row p's entry s at s * ld + p)
     long long ld;             // column stride (elements), multiple of 64
     long long nodecap;        // node scratch capacity per slot
     int nslots;

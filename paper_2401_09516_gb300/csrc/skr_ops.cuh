@@ -8,6 +8,34 @@
 
 namespace skr {
 
+// Checks of CSR input, one thread per row: err bits 1 (row empty or longer
+// than SKR_CSR_MAX_ROW, or rowptr not ascending from 0), 2 (diagonal missing
+// or repeated), 4 (column outside [0, n)), 8 (a column twice in a row);
+// wmax = entries of the longest row.
+__global__ void skr_csr_check_kernel(const long long *rowptr, const int *colind, long long n, int *out) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        int e = 0;
+        const long long r0 = rowptr[p], r1 = rowptr[p + 1];
+        const long long len = r1 - r0;
+        if ((p == 0 && r0 != 0) || len < 1 || len > SKR_CSR_MAX_ROW) e |= 1;
+        if (!(e & 1)) {
+            int ndiag = 0;
+            for (long long q = r0; q < r1; q++) {
+                const int col = colind[q];
+                if (col < 0 || col >= n) e |= 4;
+                if (col == p) ndiag++;
+                for (long long q2 = r0; q2 < q; q2++)
+                    if (colind[q2] == col) e |= 8;
+            }
+            if (ndiag != 1) e |= 2;
+            atomicMax(out + 1, (int)len);
+        }
+        if (e) atomicOr(out, e);
+    }
+}
+
+
 __global__ void node_exp_kernel(const double *__restrict__ loga, long long nn, double *__restrict__ anode) {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nn;
          q += (long long)gridDim.x * blockDim.x)
@@ -15,12 +43,19 @@ __global__ void node_exp_kernel(const double *__restrict__ loga, long long nn, d
 }
 
 // A (nst arrays, stride ld), b, dinv (Jacobi or 1).
+// CSR input also writes its column indices into cols (g.nst arrays of stride ld).
 __global__ void rows_kernel(DevSystem sys, Geom g, const double *anode, double *A, long long ld,
-                            double *b, double *dinv, int precond) {
+                            double *b, double *dinv, int precond, int *cols) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n;
          p += (long long)gridDim.x * blockDim.x) {
         double row[7];
-        system_row(sys, g, anode, p, row);
+        if (sys.fmt == SKR_FMT_CSR) {
+            int ci[7];
+            csr_row(sys, p, g.nst, row, ci);
+            for (int s = 0; s < g.nst; s++) cols[(long long)s * ld + p] = ci[s];
+        } else {
+            system_row(sys, g, anode, p, row);
+        }
         for (int s = 0; s < g.nst; s++) A[(long long)s * ld + p] = row[s];
         if (b) b[p] = system_rhs(sys, g, p);
         if (dinv) dinv[p] = (precond == SKR_PC_JACOBI) ? 1.0 / row[0] : 1.0;

@@ -600,6 +600,8 @@ skr_status skr_server_create(const skr_options *opt_in, size_t hbm_budget, int32
 
 skr_status skr_submit(skr_server *S, const skr_system *sys, const double *key, int64_t p, uint64_t *ticket) {
     if (!S || !sys || !ticket) return err(SKR_ERR_INVALID_ARG, "NULL pointer");
+    if (sys->fmt == SKR_FMT_CSR)
+        return err(SKR_ERR_INVALID_ARG, "the serving loop takes the grid formats; CSR input goes to skr_solve_sequence");
     if (sys->fmt < SKR_FMT_DARCY2D || sys->fmt > SKR_FMT_POISSON2D) return err(SKR_ERR_INVALID_ARG, "unknown format");
     if (sys->fmt == SKR_FMT_POISSON2D && sys->rhs) return err(SKR_ERR_INVALID_ARG, "Poisson format: rhs must be NULL");
     if (sys->nx < 1 || sys->ny < 1 || (fmt3d(sys->fmt) && sys->nz < 1)) return err(SKR_ERR_INVALID_ARG, "empty grid");

@@ -16,9 +16,11 @@ namespace skr {
 
 struct Geom {
     int nx, ny, nz;      // interior grid (nz = 1 in 2D)
-    int nst;             // 5 or 7
+    int nst;             // 5 or 7 (CSR input: entries of its longest row)
     long long n;         // unknowns
     long long off[7];    // neighbour offsets by slot (off[0] = 0)
+    const int *cols;     // CSR input: column of row p's entry s at cols[s * cld + p]; else nullptr
+    long long cld;
 };
 
 __host__ __device__ inline Geom make_geom(int fmt, int nx, int ny, int nz) {
@@ -36,14 +38,51 @@ __host__ __device__ inline Geom make_geom(int fmt, int nx, int ny, int nz) {
     g.off[4] = sy;
     g.off[5] = -1;
     g.off[6] = 1;
+    g.cols = nullptr;
+    g.cld = 0;
+    return g;
+}
+
+// Geometry of CSR input: n rows, w entries in the longest row, columns in
+// cols (w arrays of stride cld, written by the assembly; row p's entries
+// beyond its own count point at p with a zero coefficient).
+__host__ __device__ inline Geom make_csr_geom(long long n, int w, const int *cols, long long cld) {
+    Geom g = make_geom(SKR_FMT_CSR, (int)n, 1, 1);
+    g.nst = w;
+    g.cols = cols;
+    g.cld = cld;
     return g;
 }
 
 // Neighbour index for slot s, clamped to p when outside [0, n).  The
 // coefficient of an outside (boundary) neighbour is zero.
 __device__ __forceinline__ long long nb_index(const Geom &g, long long p, int s) {
+    if (g.cols) return g.cols[(long long)s * g.cld + p];
     long long q = p + g.off[s];
     return (q < 0 || q >= g.n) ? p : q;
+}
+
+// Row p of CSR input into the stencil slots: the diagonal in slot 0, the
+// other entries in slots 1.. in their stored order, slots up to w - 1
+// padded with (column p, value 0).  Input validated on the host side
+// (skr_csr_check_kernel): one diagonal, at most w entries.
+__device__ __forceinline__ void csr_row(const DevSystem &sys, long long p, int w, double *c, int *cidx) {
+    const long long r0 = sys.rowptr[p], r1 = sys.rowptr[p + 1];
+    for (int s = 0; s < w; s++) {
+        c[s] = 0.0;
+        cidx[s] = (int)p;
+    }
+    int s = 1;
+    for (long long q = r0; q < r1; q++) {
+        const int col = sys.colind[q];
+        if (col == p) {
+            c[0] = sys.coef[q];
+        } else if (s < w) {
+            c[s] = sys.coef[q];
+            cidx[s] = col;
+            s++;
+        }
+    }
 }
 
 // ---------------------------------------------------------------- assembly

@@ -9,7 +9,8 @@
 namespace skr {
 
 struct SlabLayout {
-    size_t o_basis, o_A64, o_Aw, o_dinv, o_x, o_r, o_b, o_node, total;
+    size_t o_basis, o_A64, o_Aw, o_dinv, o_x, o_r, o_b, o_node, o_cols, total;
+    bool cols;
 };
 
 // Column stride for vectors of n unknowns split over cs CTAs (rows per CTA
@@ -19,7 +20,8 @@ inline long long chain_ld(long long n, int cs) {
     return ((chunk * cs) + 63) / 64 * 64;
 }
 
-inline SlabLayout slab_layout(int nslots, long long ld, long long nodecap, size_t esz) {
+// cols: room for the column indices of CSR input (7 ints per row and slot)
+inline SlabLayout slab_layout(int nslots, long long ld, long long nodecap, size_t esz, bool cols = false) {
     SlabLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -35,6 +37,8 @@ inline SlabLayout slab_layout(int nslots, long long ld, long long nodecap, size_
     L.o_r = take((size_t)nslots * ld * 8);
     L.o_b = take((size_t)nslots * ld * 8);
     L.o_node = take((size_t)nslots * nodecap * 8);
+    L.cols = cols;
+    L.o_cols = cols ? take((size_t)nslots * 7 * ld * 4) : 0;
     L.total = o;
     return L;
 }
@@ -49,6 +53,7 @@ inline Workspace slab_bind(char *base, const SlabLayout &L, int nslots, long lon
     ws.r = reinterpret_cast<double *>(base + L.o_r);
     ws.b = reinterpret_cast<double *>(base + L.o_b);
     ws.anode = reinterpret_cast<double *>(base + L.o_node);
+    ws.cols = L.cols ? reinterpret_cast<int *>(base + L.o_cols) : nullptr;
     ws.ld = ld;
     ws.nodecap = nodecap;
     ws.nslots = nslots;

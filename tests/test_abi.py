@@ -47,6 +47,8 @@ int main(void) {
   printf("%zu %zu\n", offsetof(skr_result, relres), offsetof(skr_result, seconds));
   printf("%zu %zu %zu %zu\n", offsetof(skr_options, warm_start), offsetof(skr_options, diagnostics),
          offsetof(skr_result, delta), offsetof(skr_options, pc_blocks));
+  printf("%zu %zu %zu\n", offsetof(skr_system, rowptr), offsetof(skr_system, colind),
+         offsetof(skr_options, recycle_out));
   return 0;
 }
 '''
@@ -63,6 +65,7 @@ int main(void) {
     assert O.profile.offset == 52
     assert vals[7:9] == [R.relres.offset, R.seconds.offset]
     assert vals[9:13] == [O.warm_start.offset, O.diagnostics.offset, R.delta.offset, O.pc_blocks.offset]
+    assert vals[13:16] == [S.rowptr.offset, S.colind.offset, O.recycle_out.offset]
 
 
 def test_binding_constants_match_header(native):

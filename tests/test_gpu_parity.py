@@ -826,3 +826,108 @@ def test_batched_chains_of_sides_64_to_384_through_the_launch_planner(skr):
     for i in (sides.index(min(sides)), sides.index(max(sides))):
         A, b = assembly.darcy2d(fields[i])
         _check_solution(xs[i], A, b, 1e-8, spla_solve(A, b), 1e-6)
+
+
+# ------------------------------------------------------------------ CSR input (Sec. 3.1's assembled A)
+
+def _permuted(A, b, perm):
+    """P A P^T and P b for the permutation p_new = perm[p_old]... as row/column reindexing."""
+    import scipy.sparse as sp
+    n = A.shape[0]
+    Pm = sp.csr_matrix((np.ones(n), (perm, np.arange(n))), shape=(n, n))
+    Ap = (Pm @ A @ Pm.T).tocsr()
+    Ap.sort_indices()
+    return Ap, Pm @ b
+
+
+def _csr_system(skr, A, b=None, device=True):
+    A = A.tocsr()
+    if device:
+        return skr.csr(torch.tensor(A.indptr.astype(np.int64), device=DEV),
+                       torch.tensor(A.indices.astype(np.int32), device=DEV), _dev(A.data),
+                       None if b is None else _dev(b))
+    return skr.csr(A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data.copy(), b)
+
+
+@pytest.mark.parametrize("permute", [False, True])
+def test_csr_operator_matches_the_matrix(skr, permute):
+    rng = np.random.default_rng(51)
+    L = darcy2d_sequence(20, 1, 0.2, seed=51)[0]
+    A, b = assembly.darcy2d(L)
+    if permute:
+        A, b = _permuted(A, b, rng.permutation(A.shape[0]))
+    v = rng.standard_normal(A.shape[0])
+    want = A @ (v / A.diagonal())                    # A M^-1 v, right Jacobi
+    sysd = _csr_system(skr, A)
+    y64 = skr.skr_apply(sysd, _dev(v), precond="jacobi", precision="fp64").cpu().numpy()
+    np.testing.assert_allclose(y64, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+    y32 = skr.skr_apply(sysd, _dev(v), precond="jacobi", precision="mixed").cpu().numpy()
+    assert np.abs(y32 - want).max() <= 2e-5 * np.abs(want).max()
+    # host-memory input gives the same
+    yh = skr.skr_apply(_csr_system(skr, A, device=False), v, precond="jacobi", precision="fp64")
+    np.testing.assert_array_equal(yh, y64)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_csr_sequence_matches_oracle_in_grid_and_permuted_order(skr, precision):
+    # a sorted chain of Darcy matrices given as CSR, once in grid order and
+    # once renumbered by one random permutation (no grid structure left):
+    # both solve to the tolerance and match the oracle's solutions
+    L = darcy2d_sequence(24, 4, 0.2, seed=52)
+    order = osort.greedy_sort(L.reshape(4, -1))
+    perm = np.random.default_rng(52).permutation(24 * 24)
+    mats = [assembly.darcy2d(l) for l in L]
+    sysd = [dict(kind="matrix", A=A, b=b) for A, b in mats]
+    xo, info = oskr.solve_sequence(sysd, order, "jacobi", 30, 8, 1e-8, precision=precision)
+    for permute in (False, True):
+        systems = []
+        for A, b in mats:
+            Ap, bp = _permuted(A, b, perm) if permute else (A, b)
+            systems.append(_csr_system(skr, Ap, bp))
+        opt = skr.skr_options_default(m=30, k=8, tol=1e-8, precond="jacobi", precision=precision)
+        xs, res = skr.skr_solve_sequence(systems, order=order, options=opt)
+        for i, (A, b) in enumerate(mats):
+            assert res[i]["flag"] == 0, res[i]
+            x = xs[i].cpu().numpy()
+            if permute:
+                x = x[perm]                          # back to grid order
+            assert np.linalg.norm(b - A @ x) <= 1.01e-8 * np.linalg.norm(b)
+            assert np.linalg.norm(x - xo[i]) <= 1e-6 * np.linalg.norm(xo[i])
+            if precision == "fp64":
+                assert abs(res[i]["steps"] - info[i]["steps"]) <= max(3, 0.15 * info[i]["steps"])
+
+
+def test_csr_rejects_malformed_input_and_colour_sweeps(skr):
+    import scipy.sparse as sp
+    L = darcy2d_sequence(8, 1, 0.2, seed=53)[0]
+    A, b = assembly.darcy2d(L)
+    opt = skr.skr_options_default(m=10, k=2, precond="jacobi")
+
+    def solve(M):
+        return skr.skr_solve_sequence([_csr_system(skr, M, b)], options=opt)
+
+    solve(A)                                            # well-formed: fine
+    bad = A.tolil()
+    bad[5, 5] = 0.0                                     # drop a diagonal entry
+    bad = bad.tocsr()
+    bad.eliminate_zeros()
+    with pytest.raises(skr.SkrError):
+        solve(bad)
+    wide = A.tolil()
+    for j in range(10, 18):                             # a row of 8+ entries
+        wide[3, j] = -0.1
+    with pytest.raises(skr.SkrError):
+        solve(wide.tocsr())
+    oob = A.tocsr().copy()
+    oob.indices = oob.indices.copy()
+    oob.indices[1] = A.shape[0] + 3                    # a column outside [0, n)
+    with pytest.raises(skr.SkrError):
+        skr.skr_solve_sequence([skr.csr(torch.tensor(oob.indptr.astype(np.int64), device=DEV),
+                                        torch.tensor(oob.indices.astype(np.int32), device=DEV),
+                                        _dev(oob.data), _dev(b))], options=opt)
+    with pytest.raises(skr.SkrError):
+        skr.skr_solve_sequence([_csr_system(skr, A, b)],
+                               options=skr.skr_options_default(m=10, k=2, precond="ilu0"))
+    # and the library still solves afterwards
+    _, res = solve(A)
+    assert res[0]["flag"] == 0

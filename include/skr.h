@@ -103,7 +103,8 @@ typedef int32_t skr_status;
 /* precision form */
 #define SKR_PREC_FP64         0   /* all vectors and reductions in FP64 */
 #define SKR_PREC_MIXED        1   /* FP32 SpMV/Arnoldi/recycle vectors with FP32 accumulation,
-                                     FP64 true residual, solution, refinement and small dense step */
+                                     FP64 true residual, solution, refinement and small dense step
+                                     (least squares, harmonic-Ritz eigenproblem, QR, Cholesky) */
 
 #define SKR_MEM_DEVICE        0
 #define SKR_MEM_HOST          1
@@ -145,7 +146,9 @@ typedef struct skr_options {
                                and every system when zero (default), starts from x_0 = 0 */
     int32_t diagnostics;    /* nonzero: report skr_result.delta (one extra Gram pass per system) */
     int32_t pc_blocks;      /* SKR_PC_BJACOBI: number of row blocks, >= 1 (default 1) */
-    int32_t pad0;
+    int32_t eig_fp32;       /* SKR_PREC_MIXED: 1 runs the harmonic-Ritz eigenproblem of each cycle end
+                               (Algorithm 2) in FP32 instead of FP64 (default 0: FP64, like the rest
+                               of the small dense step); ignored in the FP64 form */
     double *const *recycle_out;  /* NULL (default), or a host array of nchains pointers to DEVICE
                                memory (skr_solve_sequence with mem = SKR_MEM_DEVICE only): chain c's
                                final recycle space, U_k (Algorithm 2) in columns 0..k-1 and C_k in

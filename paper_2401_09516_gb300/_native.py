@@ -67,7 +67,7 @@ class SkrOptions(ctypes.Structure):
                 ("max_slots", ctypes.c_int32), ("mem", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("warm_start", ctypes.c_int32), ("diagnostics", ctypes.c_int32),
-                ("pc_blocks", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("pc_blocks", ctypes.c_int32), ("eig_fp32", ctypes.c_int32),
                 ("recycle_out", ctypes.c_void_p)]
 
 

@@ -694,6 +694,7 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     if (opt.cluster_size < 0 || opt.cluster_size > 16) return fail(SKR_ERR_INVALID_ARG, "cluster_size in [0, 16]");
     if (opt.warm_start != 0 && opt.warm_start != 1) return fail(SKR_ERR_INVALID_ARG, "warm_start must be 0 or 1");
     if (opt.diagnostics != 0 && opt.diagnostics != 1) return fail(SKR_ERR_INVALID_ARG, "diagnostics must be 0 or 1");
+    if (opt.eig_fp32 != 0 && opt.eig_fp32 != 1) return fail(SKR_ERR_INVALID_ARG, "eig_fp32 must be 0 or 1");
     if (opt.recycle_out) {
         if (opt.mem != SKR_MEM_DEVICE) return fail(SKR_ERR_INVALID_ARG, "recycle_out needs mem = SKR_MEM_DEVICE");
         for (int c = 0; c < nchains; c++)
@@ -861,6 +862,7 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
     a.max_refine = opt.max_refine;
     a.precond = opt.precond;
     a.pc_blocks = opt.pc_blocks;
+    a.eig32 = opt.eig_fp32;
     a.tol = opt.tol;
     a.inner_tol = opt.inner_tol;
     a.bytes = reinterpret_cast<unsigned long long *>(dctr.as<char>() + 64 * nlaunch);

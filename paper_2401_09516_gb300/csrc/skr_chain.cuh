@@ -41,12 +41,6 @@ template <> struct Tiles<double> {
     static constexpr int TB = 8;
 };
 
-// Precision of the harmonic-Ritz eigen-solve: FP32 in the mixed form (the
-// eigenvectors only select the recycled subspace; M, G P_k, its QR and R^-1
-// stay FP64, so A U = C and C^T C = I hold to FP64 accuracy of the small
-// step), FP64 in the FP64 form.
-template <typename T> struct EigT { typedef double type; };
-template <> struct EigT<float> { typedef float type; };
 
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { typedef float2 type; };
@@ -130,10 +124,11 @@ __host__ __device__ inline SmemPlan make_plan(int m, int k, int nthreads, int es
     P.t_s = (P.t_cd + m + k + 2 + 3) & ~3;   // 16-byte aligned
     P.t_al = P.t_s + ((m + 4 + 3) & ~3);
     P.t_total = P.t_al + ((m + 4 + 3) & ~3);
-    // the eigenvector workspace (xr, xi, in the eigen-solve precision, which
-    // has the working element size) and the Gram tile buffer live in the
-    // coefficient region: it is written only after the eigen-solve
-    const int xsz = align2((kk * m * esz + 7) / 8);
+    // the eigenvector workspace (xr, xi, in the eigen-solve precision: FP64,
+    // or FP32 on request in the mixed form, so room for FP64) and the Gram
+    // tile buffer live in the coefficient region: it is written only after
+    // the eigen-solve
+    const int xsz = align2(kk * m);
     int tco = align2(P.t_total);
     if (2 * xsz > tco) tco = 2 * xsz;
     if (tco < 32) tco = 32;
@@ -203,6 +198,7 @@ struct Ctx {
     int *cols;   // CSR input: the slot's column indices (nullptr without that room)
     // parameters
     int m, k, maxit, precond, pc_blocks;
+    int eig32;         // mixed form: harmonic-Ritz eigen-solve in FP32 (opt-in)
     long long pc_bs;   // rows per block of the colour sweeps (n unless block-Jacobi)
     // shared memory
     SmemPlan P;
@@ -1220,26 +1216,25 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
             }
             __syncthreads();
         }
-        {
-            typedef typename EigT<T>::type R;
-            R *Mr, *Zr;
-            int ldm;
-            if (sizeof(R) == 4) {
-                // odd leading dimension: the row updates of the Hessenberg
-                // reduction and the bulge chase hit 32 distinct banks
-                Mr = reinterpret_cast<R *>(c.D(c.P.o_Z));
-                ldm = mt | 1;
-                Zr = Mr + mt * ldm;
-            } else {
-                Mr = reinterpret_cast<R *>(F);
-                Zr = reinterpret_cast<R *>(c.D(c.P.o_Z));
-                ldm = ldh;
-            }
-            knew = harmonic_select<R>(F, ldh, mt, c.k, Pm, mt, Mr, ldm, Zr,
-                                      reinterpret_cast<R *>(c.D(c.P.o_wr)), reinterpret_cast<R *>(c.D(c.P.o_wi)),
-                                      reinterpret_cast<R *>(c.D(c.P.o_xr)), reinterpret_cast<R *>(c.D(c.P.o_xi)),
-                                      reinterpret_cast<R *>(c.D(c.P.o_vscr)), reinterpret_cast<R *>(c.D(c.P.o_sc)),
-                                      c.ints() + 8, Rw);
+        // the harmonic-Ritz eigenproblem in FP64 (Algorithm 2's small dense
+        // step); FP32 only when the caller asks for it (skr_options.eig_fp32)
+        if (sizeof(T) == 4 && c.eig32) {
+            // odd leading dimension: the row updates of the Hessenberg
+            // reduction and the bulge chase hit 32 distinct banks
+            float *Mr = reinterpret_cast<float *>(c.D(c.P.o_Z));
+            const int ldm = mt | 1;
+            float *Zr = Mr + mt * ldm;
+            knew = harmonic_select<float>(F, ldh, mt, c.k, Pm, mt, Mr, ldm, Zr,
+                                          reinterpret_cast<float *>(c.D(c.P.o_wr)),
+                                          reinterpret_cast<float *>(c.D(c.P.o_wi)),
+                                          reinterpret_cast<float *>(c.D(c.P.o_xr)),
+                                          reinterpret_cast<float *>(c.D(c.P.o_xi)),
+                                          reinterpret_cast<float *>(c.D(c.P.o_vscr)),
+                                          reinterpret_cast<float *>(c.D(c.P.o_sc)), c.ints() + 8, Rw);
+        } else {
+            knew = harmonic_select<double>(F, ldh, mt, c.k, Pm, mt, F, ldh, c.D(c.P.o_Z), c.D(c.P.o_wr),
+                                           c.D(c.P.o_wi), c.D(c.P.o_xr), c.D(c.P.o_xi), c.D(c.P.o_vscr),
+                                           c.D(c.P.o_sc), c.ints() + 8, Rw);
         }
         __syncthreads();
         if (knew > 0) {
@@ -1419,7 +1414,7 @@ __device__ __noinline__ double recycle_delta(Ctx<T> &c, int kc_in) {
     __syncthreads();
     double *Z = c.D(c.P.o_Z), *wr = c.D(c.P.o_wr), *wi = c.D(c.P.o_wi);
     hessenberg_reduce<double>(S, lds, Z, kq, kq, c.D(c.P.o_vscr), c.D(c.P.o_sc));
-    const int fail = francis_schur<double>(S, lds, Z, kq, kq, wr, wi, c.ints() + 8);
+    const int fail = schur_form<double>(S, lds, Z, kq, kq, wr, wi, c.ints() + 8);
     double lmax = 0.0;
     for (int i = 0; i < kq; i++) lmax = fmax(lmax, wr[i]);   // symmetric: real eigenvalues
     __syncthreads();
@@ -1603,6 +1598,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS, CHAIN_MIN_BLOCKS) chain_kernel(
     c.maxit = a.maxit;
     c.precond = a.precond;
     c.pc_blocks = a.pc_blocks;
+    c.eig32 = a.eig32;
     c.ld = a.ws.ld;
     c.basis = reinterpret_cast<T *>(a.ws.basis) + (long long)slot * NCOLS * c.ld;
     c.A64 = a.ws.A64 + (long long)slot * 7 * c.ld;

@@ -92,6 +92,7 @@ struct ChainArgs {
     int warm_start;               // x_0 = previous solution of the chain
     int diagnostics;              // nonzero: compute delta per system
     int pc_blocks;                // SKR_PC_BJACOBI: row blocks of the preconditioner
+    int eig32 = 0;                // mixed form: harmonic-Ritz eigen-solve in FP32 instead of FP64
     int *chain_xok;               // per chain, optional: nonzero when the slot's x holds the
                                   // previous solution (read at chain start, set at chain end)
     double *const *recycle_out = nullptr;   // per chain, optional: its final U_k then C_k,

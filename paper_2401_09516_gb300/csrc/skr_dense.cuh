@@ -148,6 +148,11 @@ __device__ inline void hessenberg_reduce(R *A, int lda, R *Z, int ldz, int n, R 
 }
 
 // Householder vector for u = (x, y, z): P u = alpha e1.  Writes tau, v1, v2.
+// With a = -sign(x) ||u||: v = (1, y / (x - a), z / (x - a)), tau = (a - x) / a.
+// Both quotients come from one reciprocal, 1 / (a (x - a)); u is rescaled
+// first only when its entries are far from 1 (squares that could overflow or
+// underflow), since every division and square root is a long chain of FP64
+// instructions on this GPU.
 template <typename R>
 __device__ __forceinline__ void house3(R x, R y, R z, R &tau, R &v1, R &v2) {
     const R s = fabs(x) + fabs(y) + fabs(z);
@@ -156,12 +161,21 @@ __device__ __forceinline__ void house3(R x, R y, R z, R &tau, R &v1, R &v2) {
         v1 = v2 = R(0);
         return;
     }
-    const R is = R(1) / s;
-    const R xs = x * is, ys = y * is, zs = z * is;
+    constexpr R BIG = (sizeof(R) == 8) ? R(1e100) : R(1e15);
+    constexpr R SMALL = (sizeof(R) == 8) ? R(1e-100) : R(1e-15);
+    R xs = x, ys = y, zs = z;
+    if (s > BIG || s < SMALL) {
+        const R is = R(1) / s;
+        xs *= is;
+        ys *= is;
+        zs *= is;
+    }
     const R nrm = sqrt(xs * xs + ys * ys + zs * zs);
     const R a = -copysign(nrm, xs);
-    const R id = R(1) / (xs - a);
-    tau = (a - xs) / a;
+    const R d = xs - a;                 // = sign(x) (|x| + ||u||), never 0
+    const R r = R(1) / (a * d);
+    tau = -d * d * r;                   // (a - x) / a
+    const R id = a * r;                 // 1 / (x - a)
     v1 = ys * id;
     v2 = zs * id;
 }
@@ -363,6 +377,230 @@ __device__ inline int francis_schur(R *H, int ldh, R *Z, int ldz, int n, R *wr, 
     return fail;
 }
 
+// Named barrier among the first `nthreads` threads (whole warps) of the CTA.
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// francis_schur for FP64 on four warps, one per SM sub-partition: an FP64
+// warp instruction occupies a sub-partition's FP64 pipe for many cycles, so
+// the serial bulge chase is bound by the FP64 instructions one warp issues
+// per bulge step.  Every warp computes the reflector of a step from the same
+// shared values (identical results, no broadcast); warps 0-2 split the row
+// update of H and then, after a barrier among them, its column update; warp
+// 3 applies the step's reflector to the Schur vectors Z meanwhile.  A barrier
+// of all four ends each step.  The deflation scans, shifts and 2x2 blocks
+// are computed by every warp alike; their few writes are warp 0's.  Same
+// arithmetic per element as francis_schur, hence the same results.
+__device__ inline int francis_schur_4w(double *H, int ldh, double *Z, int ldz, int n, double *wr, double *wi,
+                                       int *isc) {
+    typedef double R;
+    constexpr R EPS = R(2.220446049250313e-16);
+    const unsigned FULL = 0xffffffffu;
+    constexpr int BAR_ALL = 1, BAR_H = 2;
+    if (warp_id() < 4) {
+        const int lane = lane_id(), w = warp_id();
+        int hi = n - 1, its = 0, total = 0, fail = 0;
+        while (hi >= 0) {
+            int l = 0;
+            for (int base = hi; base > 0; base -= 32) {
+                const int i = base - lane;
+                bool neg = false;
+                if (i > 0) {
+                    R sm = fabs(M_(H, ldh, i - 1, i - 1)) + fabs(M_(H, ldh, i, i));
+                    if (sm == R(0)) sm = R(1);
+                    neg = fabs(M_(H, ldh, i, i - 1)) <= EPS * sm;
+                }
+                const unsigned m = __ballot_sync(FULL, neg);
+                if (m != 0u) {
+                    l = base - (__ffs(m) - 1);
+                    break;
+                }
+            }
+            named_bar(BAR_ALL, 128);   // every warp has read the subdiagonal
+            if (l > 0 && w == 0 && lane == 0) M_(H, ldh, l, l - 1) = R(0);
+            if (l == hi) {
+                if (w == 0 && lane == 0) {
+                    wr[hi] = M_(H, ldh, hi, hi);
+                    wi[hi] = R(0);
+                }
+                hi -= 1;
+                its = 0;
+                named_bar(BAR_ALL, 128);
+                continue;
+            }
+            if (l == hi - 1) {
+                // a 2x2 block: warp 0 splits real pairs by a rotation (as francis_schur)
+                if (w == 0) {
+                    const int p = hi - 1;
+                    R cs = R(1), sn = R(0);
+                    int rot = 0;
+                    const R a = M_(H, ldh, p, p), b = M_(H, ldh, p, p + 1);
+                    const R c = M_(H, ldh, p + 1, p), d = M_(H, ldh, p + 1, p + 1);
+                    const R hp = R(0.5) * (a - d);
+                    const R disc = hp * hp + b * c;
+                    R w0, w1, i0, i1;
+                    if (disc >= R(0)) {
+                        const R q = sqrt(disc);
+                        const R zz = hp + copysign(q, hp);
+                        R l1, l2;
+                        if (zz == R(0)) {
+                            l1 = l2 = d;
+                        } else {
+                            l1 = d + zz;
+                            l2 = d - b * c / zz;
+                        }
+                        R e0 = l1 - d, e1 = c;
+                        if (fabs(e0) + fabs(e1) == R(0)) {
+                            e0 = b;
+                            e1 = l1 - a;
+                        }
+                        const R nrm = hypot(e0, e1);
+                        if (nrm > R(0)) {
+                            cs = e0 / nrm;
+                            sn = e1 / nrm;
+                        }
+                        rot = 1;
+                        w0 = l1;
+                        w1 = l2;
+                        i0 = i1 = R(0);
+                    } else {
+                        const R q = sqrt(-disc);
+                        w0 = w1 = hp + d;
+                        i0 = q;
+                        i1 = -q;
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        wr[p] = w0;
+                        wr[p + 1] = w1;
+                        wi[p] = i0;
+                        wi[p + 1] = i1;
+                    }
+                    if (rot) {
+                        for (int j = p + lane; j < n; j += 32) {
+                            const R a0 = M_(H, ldh, p, j), a1 = M_(H, ldh, p + 1, j);
+                            M_(H, ldh, p, j) = cs * a0 + sn * a1;
+                            M_(H, ldh, p + 1, j) = -sn * a0 + cs * a1;
+                        }
+                        __syncwarp();
+                        for (int i = lane; i < p + 2; i += 32) {
+                            const R a0 = M_(H, ldh, i, p), a1 = M_(H, ldh, i, p + 1);
+                            M_(H, ldh, i, p) = cs * a0 + sn * a1;
+                            M_(H, ldh, i, p + 1) = -sn * a0 + cs * a1;
+                        }
+                        for (int i = lane; i < n; i += 32) {
+                            const R a0 = M_(Z, ldz, i, p), a1 = M_(Z, ldz, i, p + 1);
+                            M_(Z, ldz, i, p) = cs * a0 + sn * a1;
+                            M_(Z, ldz, i, p + 1) = -sn * a0 + cs * a1;
+                        }
+                        __syncwarp();
+                        if (lane == 0) M_(H, ldh, p + 1, p) = R(0);
+                    }
+                }
+                hi -= 2;
+                its = 0;
+                named_bar(BAR_ALL, 128);
+                continue;
+            }
+            its++;
+            total++;
+            if (total > 40 * n) {
+                fail = 1;
+                break;
+            }
+            R x, y, z;
+            {
+                R sh, t;
+                if (its == 10 || its == 20) {
+                    const R ww = fabs(M_(H, ldh, hi, hi - 1)) + fabs(M_(H, ldh, hi - 1, hi - 2));
+                    const R xx = R(0.75) * ww + M_(H, ldh, hi, hi);
+                    sh = R(2) * xx;
+                    t = xx * xx + R(0.4375) * ww * ww;
+                } else {
+                    const R a = M_(H, ldh, hi - 1, hi - 1), b = M_(H, ldh, hi - 1, hi);
+                    const R c = M_(H, ldh, hi, hi - 1), d = M_(H, ldh, hi, hi);
+                    sh = a + d;
+                    t = a * d - b * c;
+                }
+                const R h00 = M_(H, ldh, l, l), h01 = M_(H, ldh, l, l + 1);
+                const R h10 = M_(H, ldh, l + 1, l), h11 = M_(H, ldh, l + 1, l + 1);
+                const R h21 = M_(H, ldh, l + 2, l + 1);
+                x = h00 * h00 + h01 * h10 - sh * h00 + t;
+                y = h10 * (h00 + h11 - sh);
+                z = h10 * h21;
+            }
+            named_bar(BAR_ALL, 128);   // every warp has read the shift inputs
+            for (int kk = l; kk <= hi - 1; kk++) {
+                const int nr = (kk == hi - 1) ? 2 : 3;
+                R tau, v1, v2;
+                house3(x, y, nr == 3 ? z : R(0), tau, v1, v2);
+                if (tau != R(0)) {
+                    if (w == 3) {
+                        // the Schur vectors: independent of H
+                        for (int i = lane; i < n; i += 32) {
+                            R tt = M_(Z, ldz, i, kk) + v1 * M_(Z, ldz, i, kk + 1);
+                            if (nr == 3) tt += v2 * M_(Z, ldz, i, kk + 2);
+                            tt *= tau;
+                            M_(Z, ldz, i, kk) -= tt;
+                            M_(Z, ldz, i, kk + 1) -= tt * v1;
+                            if (nr == 3) M_(Z, ldz, i, kk + 2) -= tt * v2;
+                        }
+                    } else {
+                        // rows kk..kk+2 of H from column c0 on, columns dealt to warps 0-2
+                        const int c0 = (kk > l) ? kk - 1 : l;
+                        for (int j = c0 + w + 3 * lane; j < n; j += 96) {
+                            R tt = M_(H, ldh, kk, j) + v1 * M_(H, ldh, kk + 1, j);
+                            if (nr == 3) tt += v2 * M_(H, ldh, kk + 2, j);
+                            tt *= tau;
+                            M_(H, ldh, kk, j) -= tt;
+                            M_(H, ldh, kk + 1, j) -= tt * v1;
+                            if (nr == 3) M_(H, ldh, kk + 2, j) -= tt * v2;
+                        }
+                        named_bar(BAR_H, 96);
+                        // columns kk..kk+2 of H down to row rmax, rows dealt to warps 0-2
+                        const int rmax = min(kk + 3, hi);
+                        for (int i = w + 3 * lane; i <= rmax; i += 96) {
+                            R tt = M_(H, ldh, i, kk) + v1 * M_(H, ldh, i, kk + 1);
+                            if (nr == 3) tt += v2 * M_(H, ldh, i, kk + 2);
+                            tt *= tau;
+                            M_(H, ldh, i, kk) -= tt;
+                            M_(H, ldh, i, kk + 1) -= tt * v1;
+                            if (nr == 3) M_(H, ldh, i, kk + 2) -= tt * v2;
+                        }
+                    }
+                }
+                named_bar(BAR_ALL, 128);   // H of this step complete
+                if (kk < hi - 1) {
+                    x = M_(H, ldh, kk + 1, kk);
+                    y = M_(H, ldh, kk + 2, kk);
+                    z = (kk < hi - 2) ? M_(H, ldh, kk + 3, kk) : R(0);
+                }
+                if (w == 0 && lane == 0 && kk > l) {
+                    // the bulge entries of column kk - 1: no warp reads them again in this sweep
+                    M_(H, ldh, kk + 1, kk - 1) = R(0);
+                    if (nr == 3) M_(H, ldh, kk + 2, kk - 1) = R(0);
+                }
+                named_bar(BAR_ALL, 128);   // every warp has read x, y, z
+            }
+        }
+        if (w == 0 && lane == 0) isc[0] = fail;
+    }
+    sync();
+    const int fail = isc[0];
+    sync();
+    return fail;
+}
+
+// FP64 Schur forms run on four warps, FP32 ones on one (its instructions are
+// cheap enough that barriers between warps would cost more than they save).
+template <typename R>
+__device__ inline int schur_form(R *H, int ldh, R *Z, int ldz, int n, R *wr, R *wi, int *isc) {
+    if constexpr (sizeof(R) == 8)
+        return francis_schur_4w(H, ldh, Z, ldz, n, wr, wi, isc);
+    else
+        return francis_schur(H, ldh, Z, ldz, n, wr, wi, isc);
+}
 // Complex helpers (re, im pairs).
 template <typename R>
 __device__ __forceinline__ void cdiv(R ar, R ai, R br, R bi, R &cr, R &ci) {
@@ -471,7 +709,7 @@ __device__ __noinline__ int harmonic_select(const double *M64, int ld64, int n, 
         sync();
     }
     hessenberg_reduce(Mr, ldm, Zr, n, n, vscr, scr);
-    const int fail = francis_schur(Mr, ldm, Zr, n, n, wr, wi, isc);
+    const int fail = schur_form(Mr, ldm, Zr, n, n, wr, wi, isc);
     if (fail) return -1;
     int *rank = isc + 8;
     int *pick = isc + 8 + MMAX;

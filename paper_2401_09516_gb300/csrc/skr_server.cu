@@ -282,6 +282,7 @@ bool launch(skr_server *S, Chain *c, Request *r) {
     a.max_refine = S->opt.max_refine;
     a.precond = S->opt.precond;
     a.pc_blocks = S->opt.pc_blocks;
+    a.eig32 = S->opt.eig_fp32;
     a.tol = S->opt.tol;
     a.inner_tol = S->opt.inner_tol;
     a.bytes = c->dbytes;

@@ -931,3 +931,30 @@ def test_csr_rejects_malformed_input_and_colour_sweeps(skr):
     # and the library still solves afterwards
     _, res = solve(A)
     assert res[0]["flag"] == 0
+
+
+def test_mixed_form_eigen_solve_fp64_default_and_fp32_opt_in(skr):
+    # the mixed form runs the harmonic-Ritz eigenproblem in FP64 by default;
+    # eig_fp32 = 1 runs it in FP32.  Both reach the tolerance and the oracle's
+    # solutions; after one first cycle their recycle subspaces agree to the
+    # FP32 accuracy of the eigenvectors
+    L = darcy2d_sequence(32, 4, 0.2, seed=44)
+    order = osort.greedy_sort(L.reshape(4, -1))
+    sysd = [dict(kind="darcy2d", loga=l) for l in L]
+    xo, _ = oskr.solve_sequence(sysd, order, "jacobi", 30, 8, 1e-8, precision="mixed")
+    for e32 in (0, 1):
+        opt = skr.skr_options_default(m=30, k=8, tol=1e-8, precond="jacobi", precision="mixed", eig_fp32=e32)
+        xs, res = skr.skr_solve_sequence([skr.darcy2d(_dev(l)) for l in L], order=order, options=opt)
+        for i in range(4):
+            assert res[i]["flag"] == 0, (e32, res[i])
+            x = xs[i].cpu().numpy()
+            assert np.linalg.norm(x - xo[i]) <= 1e-6 * np.linalg.norm(xo[i]), (e32, i)
+    subspaces = []
+    for e32 in (0, 1):
+        n, k = 32 * 32, 8
+        buf = torch.zeros(2 * k * n, dtype=torch.float64, device=DEV)
+        opt = skr.skr_options_default(m=30, k=k, tol=1e-12, precond="jacobi", precision="mixed", maxit=30,
+                                      max_refine=1, eig_fp32=e32, cluster_size=1)
+        skr.skr_solve_sequence([skr.darcy2d(_dev(L[0]))], options=opt, recycle_out=[buf])
+        subspaces.append(buf.cpu().numpy().reshape(2 * k, n).T[:, k:])
+    assert _max_sine(subspaces[0], subspaces[1]) <= 1e-3

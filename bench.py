@@ -385,7 +385,8 @@ def run_gpu(args):
                                        maxit=args.maxit, precond=W["precond"], pc_blocks=W["pc_blocks"],
                                        precision=precision or W["precision"], cluster_size=cluster_size,
                                        stream=stream, warm_start=int(args.warm_start),
-                                       diagnostics=int(args.diagnostics), profile=profile)
+                                       diagnostics=int(args.diagnostics), profile=profile,
+                                       eig_fp32=int(args.eig_fp32))
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -546,6 +547,7 @@ def run_gpu(args):
             "workload": W["desc"] % N,
             "chains": len(offs) - 1, "cluster_size": st_skr[-1]["cluster_size"],
             "warm_start": bool(args.warm_start), "sorted": not args.no_sort,
+            "eigen_solve": "fp32" if (args.eig_fp32 and W["precision"] == "mixed") else "fp64",
             "slots": st_skr[-1]["slots"], "launches": st_skr[-1]["plan"],
             "maxit": args.maxit, "l2": "flushed between steps (256 MB write)",
             "parallelism": "replicas" if ws > 1 else "single GPU",
@@ -973,6 +975,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
                     help="named workload (default %s)" % DEFAULT_WORKLOAD)
     ap.add_argument("--warm-start", action="store_true", help="x_0 = previous solution of the chain")
+    ap.add_argument("--eig-fp32", action="store_true",
+                    help="mixed form: harmonic-Ritz eigen-solve in FP32 instead of FP64")
     ap.add_argument("--no-sort", action="store_true", help="solve in input order (ablation)")
     ap.add_argument("--precond", default=None, choices=sorted(PRECOND_NAMES),
                     help="override the workload's preconditioner")

@@ -10,17 +10,8 @@
 // growth of a 2D elliptic problem's iteration count with the grid side); only
 // ratios between chains matter.
 //
-// Plan:
-//   1. each chain starts at the cluster size with the least CTA time per
-//      step (t x cs; ties to the smaller cluster);
-//   2. the ideal makespan L is the total CTA time over the GPU's CTAs; a
-//      chain whose own time exceeds L gets the smallest larger cluster that
-//      brings it under L (or the fastest), and L is recomputed (a few rounds);
-//   3. chains of one cluster size form one launch; each launch gets clusters
-//      in proportion to its CTA time, at most one per chain and at most as
-//      many as fit, and the CTAs left over go to the launch that would finish
-//      last;
-//   4. inside a launch, chains are handed out longest first.
+// Plan: see plan_launches below (a makespan model of the launches, searched
+// over the cluster size of each group of equal-size chains).
 // Launches of different cluster sizes run concurrently on their own streams;
 // their clusters never wait on one another, so a cluster that finds no SM
 // free simply starts later.
@@ -87,107 +78,146 @@ struct LaunchClass {
     double est_us = 0.0;       // estimated time of the launch
 };
 
+// Finish time of chains of the given durations (descending) handed out
+// longest first to `slots` clusters, each taking the next chain when free.
+inline double plan_lpt_makespan(const std::vector<double> &dur_desc, int slots) {
+    if (dur_desc.empty()) return 0.0;
+    if (slots < 1) return 1e300;
+    std::vector<double> fin(std::min<size_t>((size_t)slots, dur_desc.size()), 0.0);
+    for (double d : dur_desc) {
+        size_t w = 0;
+        for (size_t i = 1; i < fin.size(); i++)
+            if (fin[i] < fin[w]) w = i;
+        fin[w] += d;
+    }
+    double mx = 0.0;
+    for (double f : fin) mx = std::max(mx, f);
+    return mx;
+}
+
 // chain_n[c]: unknowns of chain c's systems; chain_len[c]: its systems.
 // maxc(cs): clusters of cs CTAs that fit at once (0 if none); cap_ctas:
 // CTAs that fit at once; max_clusters: cap on clusters over all launches
 // (0 = none).  Returns the launches (empty if nothing can be scheduled).
+//
+// Model: a chain of len systems of n unknowns takes len x sqrt(n) x
+// t(n, cs) (the measured table, steps per system taken proportional to
+// sqrt(n)); a launch's finish time is its chains' longest-first list
+// schedule over its clusters; the plan's time is the latest launch's.
+// Clusters go one at a time to the launch that finishes last while CTAs
+// (and the cluster cap) allow; the cluster size of each group of equal-n
+// chains is chosen by coordinate descent on the plan's time, starting from
+// one CTA per cluster.
 template <typename MaxClusters>
 std::vector<LaunchClass> plan_launches(const std::vector<long long> &chain_n, const std::vector<long long> &chain_len,
                                        int cap_ctas, MaxClusters maxc, int max_clusters) {
     const int nc = (int)chain_n.size();
     std::vector<LaunchClass> out;
     if (nc == 0 || cap_ctas < 1) return out;
+    const int cap_clusters = max_clusters > 0 ? max_clusters : (1 << 30);
+    std::vector<int> cands;
+    for (int j = 0; j < SKR_TUNE_COLS; j++)
+        if (SKR_TUNE_CS[j] <= cap_ctas && maxc(SKR_TUNE_CS[j]) > 0) cands.push_back(SKR_TUNE_CS[j]);
+    if (cands.empty()) return out;
     auto chain_us = [&](int c, int cs) {
         return (double)chain_len[c] * plan_step_weight(chain_n[c]) * tuned_step_us(chain_n[c], cs);
     };
-    auto usable = [&](int cs) { return cs <= cap_ctas && maxc(cs) > 0; };
-    std::vector<int> cs(nc);
+    // groups of chains with equal n
+    std::vector<long long> gn;
+    std::vector<int> gof(nc);
     for (int c = 0; c < nc; c++) {
-        cs[c] = plan_efficient_cs(chain_n[c]);
-        while (!usable(cs[c]) && cs[c] > 1) cs[c] /= 2;
+        auto it = std::find(gn.begin(), gn.end(), chain_n[c]);
+        if (it == gn.end()) {
+            gof[c] = (int)gn.size();
+            gn.push_back(chain_n[c]);
+        } else {
+            gof[c] = (int)(it - gn.begin());
+        }
     }
-    // 2. chains longer than the ideal makespan get larger clusters
-    for (int round = 0; round < 6; round++) {
-        double tot = 0.0;
-        for (int c = 0; c < nc; c++) tot += chain_us(c, cs[c]) * cs[c];
-        const double L = tot / cap_ctas;
-        bool changed = false;
-        for (int c = 0; c < nc; c++) {
-            if (chain_us(c, cs[c]) <= L) continue;
-            int best = cs[c];
-            for (int j = 0; j < SKR_TUNE_COLS; j++) {
-                const int q = SKR_TUNE_CS[j];
-                if (q <= cs[c] || !usable(q)) continue;
-                if (chain_us(c, q) < chain_us(c, best)) best = q;
-                if (chain_us(c, best) <= L) break;
+    const int ng = (int)gn.size();
+    // launches and cluster counts for one cluster size per group; returns the plan's time
+    auto build = [&](const std::vector<int> &gcs, std::vector<LaunchClass> &L) {
+        L.clear();
+        for (int cs : cands) {
+            LaunchClass k;
+            k.cs = cs;
+            for (int c = 0; c < nc; c++)
+                if (gcs[gof[c]] == cs) k.chains.push_back(c);
+            if (k.chains.empty()) continue;
+            std::stable_sort(k.chains.begin(), k.chains.end(),
+                             [&](int a, int b) { return chain_us(a, cs) > chain_us(b, cs); });
+            L.push_back(k);
+        }
+        std::vector<std::vector<double>> dur(L.size());
+        int used_ctas = 0, used_clusters = 0;
+        for (size_t i = 0; i < L.size(); i++) {
+            for (int c : L[i].chains) dur[i].push_back(chain_us(c, L[i].cs));
+            L[i].slots = 1;
+            used_ctas += L[i].cs;
+            used_clusters += 1;
+        }
+        if (used_ctas > cap_ctas || used_clusters > cap_clusters) return 1e300;
+        for (size_t i = 0; i < L.size(); i++) L[i].est_us = plan_lpt_makespan(dur[i], L[i].slots);
+        for (;;) {
+            size_t w = 0;
+            for (size_t i = 1; i < L.size(); i++)
+                if (L[i].est_us > L[w].est_us) w = i;
+            LaunchClass &k = L[w];
+            const int lim = std::min<int>((int)k.chains.size(), maxc(k.cs));
+            if (k.slots >= lim || used_ctas + k.cs > cap_ctas || used_clusters + 1 > cap_clusters) break;
+            k.slots += 1;
+            used_ctas += k.cs;
+            used_clusters += 1;
+            k.est_us = plan_lpt_makespan(dur[w], k.slots);
+        }
+        double t = 0.0;
+        for (const LaunchClass &k : L) t = std::max(t, k.est_us);
+        // CTAs still free: to the other launches, latest first (the model is
+        // an estimate; idle SMs help no one)
+        for (bool grew = true; grew;) {
+            grew = false;
+            size_t w = L.size();
+            for (size_t i = 0; i < L.size(); i++) {
+                const int lim = std::min<int>((int)L[i].chains.size(), maxc(L[i].cs));
+                if (L[i].slots >= lim || used_ctas + L[i].cs > cap_ctas || used_clusters + 1 > cap_clusters) continue;
+                if (w == L.size() || L[i].est_us > L[w].est_us) w = i;
             }
-            if (best != cs[c]) {
-                cs[c] = best;
-                changed = true;
+            if (w < L.size()) {
+                L[w].slots += 1;
+                used_ctas += L[w].cs;
+                used_clusters += 1;
+                L[w].est_us = plan_lpt_makespan(dur[w], L[w].slots);
+                grew = true;
             }
         }
-        if (!changed) break;
-    }
-    // 3. one launch per cluster size
-    for (int j = 0; j < SKR_TUNE_COLS; j++) {
-        LaunchClass k;
-        k.cs = SKR_TUNE_CS[j];
-        for (int c = 0; c < nc; c++)
-            if (cs[c] == k.cs) k.chains.push_back(c);
-        if (k.chains.empty()) continue;
-        std::stable_sort(k.chains.begin(), k.chains.end(),
-                         [&](int a, int b) { return chain_us(a, k.cs) > chain_us(b, k.cs); });
-        out.push_back(k);
-    }
-    std::vector<double> work(out.size(), 0.0), longest(out.size(), 0.0);
-    double tot = 0.0;
-    for (size_t i = 0; i < out.size(); i++) {
-        for (int c : out[i].chains) {
-            work[i] += chain_us(c, out[i].cs);
-            longest[i] = std::max(longest[i], chain_us(c, out[i].cs));
-        }
-        tot += work[i] * out[i].cs;
-    }
-    const int cap_clusters = max_clusters > 0 ? max_clusters : (1 << 30);
-    int used_ctas = 0, used_clusters = 0;
-    auto limit = [&](size_t i) {
-        return std::min<int>((int)out[i].chains.size(), maxc(out[i].cs));
+        return t;
     };
-    for (size_t i = 0; i < out.size(); i++) {
-        const double share = tot > 0.0 ? work[i] * out[i].cs / tot : 1.0 / out.size();
-        int s = (int)std::floor(share * cap_ctas / out[i].cs);
-        s = std::max(1, std::min(s, limit(i)));
-        out[i].slots = s;
-        used_ctas += s * out[i].cs;
-        used_clusters += s;
-    }
-    // too many (the minimum of one cluster each can overshoot): trim the largest
-    while ((used_ctas > cap_ctas || used_clusters > cap_clusters)) {
-        size_t w = out.size();
-        for (size_t i = 0; i < out.size(); i++)
-            if (out[i].slots > 1 && (w == out.size() || out[i].slots * out[i].cs > out[w].slots * out[w].cs)) w = i;
-        if (w == out.size()) break;
-        out[w].slots -= 1;
-        used_ctas -= out[w].cs;
-        used_clusters -= 1;
-    }
-    // CTAs left over: to the launch that would finish last
-    auto finish = [&](size_t i) { return std::max(work[i] / out[i].slots, longest[i]); };
-    for (;;) {
-        size_t w = out.size();
-        for (size_t i = 0; i < out.size(); i++) {
-            if (out[i].slots >= limit(i) || used_ctas + out[i].cs > cap_ctas || used_clusters + 1 > cap_clusters)
-                continue;
-            if (finish(i) <= longest[i] * (1.0 + 1e-9)) continue;   // more clusters would not help
-            if (w == out.size() || finish(i) > finish(w)) w = i;
+    std::vector<int> gcs(ng, cands[0]);
+    std::vector<LaunchClass> best;
+    double bt = build(gcs, best);
+    for (int round = 0; round < 8; round++) {
+        bool improved = false;
+        for (int g = ng - 1; g >= 0; g--) {   // largest grids first (usually listed last)
+            const int keep = gcs[g];
+            for (int cs : cands) {
+                if (cs == keep) continue;
+                gcs[g] = cs;
+                std::vector<LaunchClass> L;
+                const double t = build(gcs, L);
+                if (t < bt * (1.0 - 1e-9)) {
+                    bt = t;
+                    best = L;
+                    improved = true;
+                    break;
+                }
+                gcs[g] = keep;
+            }
+            if (improved) break;
         }
-        if (w == out.size()) break;
-        out[w].slots += 1;
-        used_ctas += out[w].cs;
-        used_clusters += 1;
+        if (!improved) break;
     }
-    for (size_t i = 0; i < out.size(); i++) out[i].est_us = finish(i);
-    return out;
+    if (bt >= 1e299) return out;
+    return best;
 }
 
 }  // namespace skr

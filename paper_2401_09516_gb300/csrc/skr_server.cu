@@ -110,6 +110,7 @@ struct skr_server {
     size_t budget = 0, used = 0, smem = 0;
     int max_chains = 64, device = 0, threads = 0;
     int cap_ctas = 0;          // CTAs of the chain kernel that fit on the GPU at once
+    int maxc[SKR_TUNE_COLS] = {};   // clusters of each table size that fit at once
     uint64_t launches = 0;     // launch counter (chain recency)
     int64_t evicted = 0;
     std::mutex mu;
@@ -126,13 +127,14 @@ struct skr_server {
 
 namespace {
 
-// Cluster size of a chain of n unknowns: the caller's, else the one with the
-// least CTA time per Arnoldi step in the measured launch table (skr_plan.h),
-// which keeps the most requests running at once under load.
-int auto_cs(long long n, int requested) {
-    if (requested > 0) return requested;
-    return plan_efficient_cs(n);
-}
+// Cluster size of one request of n unknowns: the caller's if set; else,
+// from the measured launch table (skr_plan.h), the fastest size whose CTA
+// time per Arnoldi step is within 1.6x of the cheapest size's and whose CTAs
+// leave room for the other waiting requests (share = free CTAs / requests
+// waiting, at least 1): one fast cluster per request under light load, the
+// cheapest clusters when the queue is long.
+int request_cs(const skr_server *S, long long n, int share);
+
 
 struct ChainPlan {
     SlabLayout L;
@@ -146,8 +148,12 @@ struct ChainPlan {
 ChainPlan chain_plan(const skr_server *S, const Request &r) {
     ChainPlan P;
     const size_t esz = S->opt.precision == SKR_PREC_FP64 ? 8 : 4;
-    P.cs = auto_cs(r.n, S->opt.cluster_size);
-    P.ld = chain_ld(r.n, P.cs);
+    // a chain may run each request on another cluster size: its column
+    // stride holds the row split of every size
+    P.cs = 1;
+    P.ld = 0;
+    for (int j = 0; j < SKR_TUNE_COLS; j++) P.ld = std::max(P.ld, chain_ld(r.n, SKR_TUNE_CS[j]));
+    if (S->opt.cluster_size > 0) P.ld = std::max(P.ld, chain_ld(r.n, S->opt.cluster_size));
     P.nodecap = std::max<long long>(1, (r.fmt == SKR_FMT_DARCY2D || r.fmt == SKR_FMT_DARCY3D)
                                            ? coef_len(r.fmt, r.nx, r.ny, r.nz)
                                            : 1);
@@ -248,7 +254,7 @@ Chain *create_chain(skr_server *S, const Request &r) {
 }
 
 // Launch request r on chain c (server lock held).  Returns false on a CUDA error.
-bool launch(skr_server *S, Chain *c, Request *r) {
+bool launch(skr_server *S, Chain *c, Request *r, int cs) {
     cudaStream_t st = c->st;
     std::memcpy(c->hcoef, r->coef.data(), r->coef.size() * 8);
     if (!r->coef.empty()) cudaMemcpyAsync(c->dcoef, c->hcoef, r->coef.size() * 8, cudaMemcpyHostToDevice, st);
@@ -291,6 +297,7 @@ bool launch(skr_server *S, Chain *c, Request *r) {
     a.warm_start = S->opt.warm_start;
     a.diagnostics = S->opt.diagnostics;
     a.chain_xok = c->dkc + 16;   // the chain's x holds its previous request's solution
+    c->cs = cs;
     if (encode_basis_maps(a.ws.basis, a.ws.ld, a.ws.nslots, S->opt.precision == SKR_PREC_FP64 ? 8 : 4, a.tmap) !=
         cudaSuccess)
         return false;
@@ -375,7 +382,28 @@ struct Admit {
     Request *r;
     Chain *chain;                  // an idle chain of r's shape, or nullptr: a new chain
     std::vector<Chain *> victims;  // idle chains to evict first (new chain only)
+    int cs;                        // cluster size of this request's launch
 };
+
+int request_cs(const skr_server *S, long long n, int share) {
+    if (S->opt.cluster_size > 0) return S->opt.cluster_size;
+    double cheapest = 1e300;
+    for (int j = 0; j < SKR_TUNE_COLS; j++)
+        if (S->maxc[j] > 0) cheapest = std::min(cheapest, tuned_step_us(n, SKR_TUNE_CS[j]) * SKR_TUNE_CS[j]);
+    int best = 1;
+    double bt = 1e300;
+    for (int j = 0; j < SKR_TUNE_COLS; j++) {
+        const int cs = SKR_TUNE_CS[j];
+        if (S->maxc[j] <= 0 || cs > std::max(1, share)) continue;
+        const double t = tuned_step_us(n, cs);
+        if (t * cs > 1.6 * cheapest) continue;
+        if (t < bt) {
+            bt = t;
+            best = cs;
+        }
+    }
+    return best;
+}
 
 bool same_shape(const Chain *c, const Request *r) {
     return c->fmt == r->fmt && c->nx == r->nx && c->ny == r->ny && c->nz == r->nz && c->p == r->key.size();
@@ -433,8 +461,10 @@ void loop(skr_server *S) {
             }
             long long free_slots = (long long)S->max_chains - (long long)nchains;
             long long free_bytes = S->budget == 0 ? (1LL << 62) : (long long)S->budget - (long long)used;
-            for (Request *r : queued) {
-                const int cs = auto_cs(r->n, S->opt.cluster_size);
+            for (size_t qi = 0; qi < queued.size(); qi++) {
+                Request *r = queued[qi];
+                const int waiting = (int)(queued.size() - qi);
+                const int cs = request_cs(S, r->n, free_ctas / std::max(1, waiting));
                 if (cs > free_ctas && running > 0) continue;      // wait for SMs
                 int best = -1;
                 double bd = INFINITY;
@@ -452,7 +482,7 @@ void loop(skr_server *S) {
                 }
                 if (best >= 0) {
                     state[best] = 2;
-                    plan.push_back({r, S->chains[best], {}});
+                    plan.push_back({r, S->chains[best], {}, cs});
                 } else {
                     const long long need = (long long)chain_bytes(S, *r);
                     std::vector<Chain *> victims;
@@ -480,7 +510,7 @@ void loop(skr_server *S) {
                     }
                     free_slots -= 1;
                     free_bytes -= need;
-                    plan.push_back({r, nullptr, victims});
+                    plan.push_back({r, nullptr, victims, cs});
                 }
                 free_ctas -= cs;
                 running++;
@@ -535,7 +565,7 @@ void loop(skr_server *S) {
                     continue;
                 }
             }
-            if (!launch(S, c, r)) {
+            if (!launch(S, c, r, ad.cs)) {
                 cudaGetLastError();
                 finish(S, r, nullptr, false);
                 c->busy = false;
@@ -590,6 +620,9 @@ skr_status skr_server_create(const skr_options *opt_in, size_t hbm_budget, int32
     // CTAs of the chain kernel resident at once (clusters of one CTA)
     S->cap_ctas = opt.precision == SKR_PREC_FP64 ? max_active_clusters_f64(1, S->threads, S->smem)
                                                  : max_active_clusters_f32(1, S->threads, S->smem);
+    for (int j = 0; j < SKR_TUNE_COLS; j++)
+        S->maxc[j] = opt.precision == SKR_PREC_FP64 ? max_active_clusters_f64(SKR_TUNE_CS[j], S->threads, S->smem)
+                                                    : max_active_clusters_f32(SKR_TUNE_CS[j], S->threads, S->smem);
     if (S->cap_ctas < 1) {
         delete S;
         return err(SKR_ERR_CUDA, "the chain kernel cannot be scheduled with this shared memory");

@@ -241,7 +241,8 @@ TRAFFIC = {"workload": "darcy256", "sources_sha256": "e4f99adf54da31ed8a0398a251
 # do not change a chain-kernel launch)
 CHAIN_KERNEL_SOURCES = ("skr_api.cu", "skr_chain.cuh", "skr_chain_f32.cu", "skr_chain_f64.cu",
                         "skr_chain_launch.cuh", "skr_common.h", "skr_dense.cuh", "skr_device.cuh",
-                        "skr_launch.h", "skr_stencil.cuh", "skr_tma.h", "skr_workspace.h")
+                        "skr_launch.h", "skr_plan.h", "skr_stencil.cuh", "skr_tma.h", "skr_tuned.inc",
+                        "skr_workspace.h")
 
 
 def _kernel_sources_sha256():
@@ -841,7 +842,7 @@ def _serving_summary(reqs, lat, st, res, elapsed, submit_span):
 def run_serving(args):
     """Serving: a seeded Poisson arrival stream of 2D and 3D Darcy requests
     replayed in real time against the server (skr_server_*), with recycling
-    (SKR) and, unless --serving-no-plain, again as plain GMRES (k = 0)."""
+    (SKR) and, with --serving-plain, again as plain GMRES (k = 0)."""
     import torch
 
     _, _, local = _dist()
@@ -1015,8 +1016,9 @@ def main():
     ap.add_argument("--serving-budget-gb", type=float, default=0.0,
                     help="device-memory budget of the server in GiB (0 = none)")
     ap.add_argument("--serving-chains", type=int, default=0, help="resident chain limit (0 = 64)")
-    ap.add_argument("--serving-no-plain", dest="serving_plain", action="store_false",
-                    help="skip the plain-GMRES replay of the same stream")
+    ap.add_argument("--serving-plain", action="store_true",
+                    help="replay the same stream again with plain GMRES (k = 0); on the full mix plain GMRES "
+                         "needs tens of thousands of steps on the 1024^2 and 128^3 requests")
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="upper bound on one reference sample")
     args = ap.parse_args()

@@ -221,6 +221,19 @@ struct Ctx {
     const CUtensorMap *tmap;        // basis boxes of 16 >> i columns, i < NBOX
     int ybase;                      // first column of this slot in the tensor maps
 
+    // the Schur form and eigenvector parts of a harmonic-Ritz solve, from the
+    // device clock marks it wrote (mk[0] after the Schur form, mk[1] after the
+    // eigenvectors); call after a tick that closed the phase before it
+    __device__ __forceinline__ void tick_eigen(const unsigned long long *mk) {
+        if (prof != nullptr && rank == 0 && threadIdx.x == 0) {
+            const unsigned long long m0 = mk[0] > tmark ? mk[0] : tmark;
+            const unsigned long long m1 = mk[1] > m0 ? mk[1] : m0;
+            atomicAdd(prof + PH_SCHUR, m0 - tmark);
+            atomicAdd(prof + PH_EIGVEC, m1 - m0);
+            tmark = m1;
+        }
+    }
+
     __device__ __forceinline__ void tick(int ph) {
         if (prof != nullptr && rank == 0 && threadIdx.x == 0) {
             const unsigned long long t = global_ns();
@@ -1218,6 +1231,9 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
         }
         // the harmonic-Ritz eigenproblem in FP64 (Algorithm 2's small dense
         // step); FP32 only when the caller asks for it (skr_options.eig_fp32)
+        unsigned long long *mk = reinterpret_cast<unsigned long long *>(c.D(c.P.o_sc) + 12);
+        if (threadIdx.x == 0) mk[0] = mk[1] = 0ull;
+        c.tick(PH_DENSE);
         if (sizeof(T) == 4 && c.eig32) {
             // odd leading dimension: the row updates of the Hessenberg
             // reduction and the bulge chase hit 32 distinct banks
@@ -1230,12 +1246,13 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
                                           reinterpret_cast<float *>(c.D(c.P.o_xr)),
                                           reinterpret_cast<float *>(c.D(c.P.o_xi)),
                                           reinterpret_cast<float *>(c.D(c.P.o_vscr)),
-                                          reinterpret_cast<float *>(c.D(c.P.o_sc)), c.ints() + 8, Rw);
+                                          reinterpret_cast<float *>(c.D(c.P.o_sc)), c.ints() + 8, Rw, mk);
         } else {
             knew = harmonic_select<double>(F, ldh, mt, c.k, Pm, mt, F, ldh, c.D(c.P.o_Z), c.D(c.P.o_wr),
                                            c.D(c.P.o_wi), c.D(c.P.o_xr), c.D(c.P.o_xi), c.D(c.P.o_vscr),
-                                           c.D(c.P.o_sc), c.ints() + 8, Rw);
+                                           c.D(c.P.o_sc), c.ints() + 8, Rw, mk);
         }
+        c.tick_eigen(mk);
         __syncthreads();
         if (knew > 0) {
             // G P_k, G = [[D, B], [0, Hbar]]

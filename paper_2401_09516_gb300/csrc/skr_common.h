@@ -106,6 +106,7 @@ struct ChainArgs {
     CUtensorMap tmap[NBOX];
 };
 
-enum Phase { PH_ASM, PH_REFRESH, PH_PROJ, PH_SPMV, PH_DOT, PH_UPD, PH_GRAM, PH_DENSE, PH_CUPD, PH_RESID, PH_OTHER };
+enum Phase { PH_ASM, PH_REFRESH, PH_PROJ, PH_SPMV, PH_DOT, PH_UPD, PH_GRAM, PH_DENSE, PH_CUPD, PH_RESID, PH_OTHER,
+             PH_SCHUR, PH_EIGVEC };
 
 }  // namespace skr

@@ -690,6 +690,106 @@ __device__ inline void schur_eigvec(const R *T, int ldt, int n, const R *wr, con
     }
 }
 
+// Eigenvectors of the quasi-triangular T for the npick eigenvalues at
+// positions pick[0..npick) (real, or the first of a complex pair when
+// wi[p] > 0), by back substitution, all at once on warp 0: lane q solves for
+// pick[q] (npick <= 32), every lane stepping through the same rows in the
+// same order (the 2x2 blocks of T are common to all), inactive above its own
+// eigenvalue.  x is stored lane-interleaved, xr[c * npick + q] (conflict-free
+// shared-memory access); xi = 0 for a real eigenvalue.  A growing vector is
+// rescaled when an entry exceeds `big`, as one vector at a time would be.
+template <typename R>
+__device__ inline void schur_eigvecs_lanes(const R *T, int ldt, int n, const R *wr, const R *wi, const int *pick,
+                                           int npick, R *xr, R *xi, R tnorm) {
+    constexpr R EPS = (sizeof(R) == 8) ? R(2.220446049250313e-16) : R(5.9604645e-8);
+    const R big = (sizeof(R) == 8) ? R(1e100) : R(1e20);
+    if (warp_id() == 0) {
+        const int q = lane_id();
+        const bool on = q < npick;
+        const int p = on ? pick[q] : n;
+        const R lr = on ? wr[p] : R(0), li = on ? wi[p] : R(0);
+        const R small = EPS * fmax(tnorm, R(1e-30));
+        if (on) {
+            for (int c = 0; c < n; c++) {
+                xr[c * npick + q] = R(0);
+                xi[c * npick + q] = R(0);
+            }
+            if (li == R(0)) {
+                xr[p * npick + q] = R(1);
+            } else {
+                xr[p * npick + q] = lr - M_(T, ldt, p + 1, p + 1);
+                xi[p * npick + q] = li;
+                xr[(p + 1) * npick + q] = M_(T, ldt, p + 1, p);
+            }
+        }
+        __syncwarp();
+        int i = n - 1;
+        while (i >= 0) {
+            const bool two = (i > 0) && (M_(T, ldt, i, i - 1) != R(0));
+            const bool act = on && i < p;
+            R mx = R(0);
+            if (!two) {
+                R sr = R(0), si = R(0);
+                for (int c = i + 1; c < n; c++) {
+                    const R t = M_(T, ldt, i, c);
+                    sr += t * xr[c * npick + q * (int)on];
+                    si += t * xi[c * npick + q * (int)on];
+                }
+                if (act) {
+                    R dr = M_(T, ldt, i, i) - lr, di = -li;
+                    if (fabs(dr) + fabs(di) < small) dr = small;
+                    R qr, qi;
+                    cdiv(-sr, -si, dr, di, qr, qi);
+                    xr[i * npick + q] = qr;
+                    xi[i * npick + q] = qi;
+                    mx = fabs(qr) + fabs(qi);
+                }
+                i -= 1;
+            } else {
+                const int a = i - 1;
+                R s0r = R(0), s0i = R(0), s1r = R(0), s1i = R(0);
+                for (int c = i + 1; c < n; c++) {
+                    const R t0 = M_(T, ldt, a, c), t1 = M_(T, ldt, i, c);
+                    const R vr = xr[c * npick + q * (int)on], vi = xi[c * npick + q * (int)on];
+                    s0r += t0 * vr;
+                    s0i += t0 * vi;
+                    s1r += t1 * vr;
+                    s1i += t1 * vi;
+                }
+                if (act) {
+                    const R b00r = M_(T, ldt, a, a) - lr, b00i = -li;
+                    const R b01 = M_(T, ldt, a, i), b10 = M_(T, ldt, i, a);
+                    const R b11r = M_(T, ldt, i, i) - lr, b11i = -li;
+                    R detr = b00r * b11r - b00i * b11i - b01 * b10;
+                    R deti = b00r * b11i + b00i * b11r;
+                    if (fabs(detr) + fabs(deti) < small * small) detr = small * small;
+                    const R n0r = -(s0r * b11r - s0i * b11i) + b01 * s1r;
+                    const R n0i = -(s0r * b11i + s0i * b11r) + b01 * s1i;
+                    const R n1r = -(s1r * b00r - s1i * b00i) + b10 * s0r;
+                    const R n1i = -(s1r * b00i + s1i * b00r) + b10 * s0i;
+                    R ar, ai, cr, ci;
+                    cdiv(n0r, n0i, detr, deti, ar, ai);
+                    cdiv(n1r, n1i, detr, deti, cr, ci);
+                    xr[a * npick + q] = ar;
+                    xi[a * npick + q] = ai;
+                    xr[i * npick + q] = cr;
+                    xi[i * npick + q] = ci;
+                    mx = fmax(fabs(ar) + fabs(ai), fabs(cr) + fabs(ci));
+                }
+                i -= 2;
+            }
+            if (act && mx > big) {
+                const R f = R(1) / mx;
+                for (int c = 0; c < n; c++) {
+                    xr[c * npick + q] *= f;
+                    xi[c * npick + q] *= f;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // Harmonic-Ritz selection (Algorithm 2): eigen-decompose M (n x n), keep the
 // eigenvectors whose eigenvalues mu have the largest |mu|, i.e. the smallest
 // |theta| for theta = 1/mu (ties: smaller Re theta, then smaller Im theta,
@@ -699,10 +799,12 @@ __device__ inline void schur_eigvec(const R *T, int ldt, int n, const R *wr, con
 // in precision R on Mr (n x n, ldm; may alias M64 when R = double) with
 // Schur vectors Zr (ldz = n).  Writes P (FP64, n x knew, ldp) and returns
 // knew (-1 if the QR iteration failed).
+// marks (optional, thread 0 writes): the device clock after the Schur form
+// and after the eigenvectors.
 template <typename R>
 __device__ __noinline__ int harmonic_select(const double *M64, int ld64, int n, int kwant, double *P, int ldp,
                                       R *Mr, int ldm, R *Zr, R *wr, R *wi, R *xr, R *xi, R *vscr,
-                                      R *scr, int *isc, double *keys) {
+                                      R *scr, int *isc, double *keys, unsigned long long *marks = nullptr) {
     const int tid = threadIdx.x, nt = blockDim.x;
     if ((const void *)Mr != (const void *)M64) {
         for (int e = tid; e < n * n; e += nt) M_(Mr, ldm, e % n, e / n) = (R)M_(M64, ld64, e % n, e / n);
@@ -710,6 +812,7 @@ __device__ __noinline__ int harmonic_select(const double *M64, int ld64, int n, 
     }
     hessenberg_reduce(Mr, ldm, Zr, n, n, vscr, scr);
     const int fail = schur_form(Mr, ldm, Zr, n, n, wr, wi, isc);
+    if (marks && threadIdx.x == 0) marks[0] = global_ns();
     if (fail) return -1;
     int *rank = isc + 8;
     int *pick = isc + 8 + MMAX;
@@ -769,12 +872,10 @@ __device__ __noinline__ int harmonic_select(const double *M64, int ld64, int n, 
     sync();
     const int npick = isc[1], knew = isc[2];
     const R tnorm = scr[3];
-    // one eigenvector per warp (lane 0): the back substitutions differ in
-    // length and branches, so lanes of one warp would serialise them
-    if (lane_id() == 0)
-        for (int q = warp_id(); q < npick; q += num_warps())
-            schur_eigvec(Mr, ldm, n, wr, wi, pick[q], xr + q * n, xi + q * n, tnorm);
+    // all picked eigenvectors at once, one per lane of warp 0
+    schur_eigvecs_lanes(Mr, ldm, n, wr, wi, pick, npick, xr, xi, tnorm);
     sync();
+    if (marks && threadIdx.x == 0) marks[1] = global_ns();
     int *colof = isc + 8 + 2 * MMAX;
     if (tid == 0) {
         int c = 0;
@@ -788,9 +889,9 @@ __device__ __noinline__ int harmonic_select(const double *M64, int ld64, int n, 
         const int i = e % n, q = (e / n) % npick, part = e / (n * npick);
         const bool pair = wi[pick[q]] != R(0);
         if (part == 1 && !pair) continue;
-        const R *x = (part == 0) ? (xr + q * n) : (xi + q * n);
+        const R *x = (part == 0) ? xr : xi;
         R s = R(0);
-        for (int c = 0; c < n; c++) s += M_(Zr, n, i, c) * x[c];
+        for (int c = 0; c < n; c++) s += M_(Zr, n, i, c) * x[c * npick + q];
         M_(P, ldp, i, colof[q] + part) = (double)s;
     }
     sync();

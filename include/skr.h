@@ -416,12 +416,13 @@ skr_status skr_last_plan(int32_t *cluster_size, int32_t *clusters, int32_t *chai
  * call made with opt->profile != 0, summed over all clusters (rank-0 CTA
  * clocks, globaltimer): ns_out[i] for phase i < min(nphase, SKR_NPHASE),
  * in the order assembly, refresh, projection, operator, multi-dot, update,
- * gram, dense, cycle-update, true-residual, other, schur, eigenvectors
- * (the last two are the parts of the dense step spent on the Hessenberg
- * reduction plus Schur form of the harmonic-Ritz matrix, and on its selected
- * eigenvectors; "dense" holds the rest of the cycle-end small step).
+ * gram, dense, cycle-update, true-residual, other, schur, eigenvectors,
+ * hessenberg (the last three are the parts of the dense step spent on the
+ * Francis iteration to the Schur form of the harmonic-Ritz matrix, on its
+ * selected eigenvectors, and on its Hessenberg reduction; "dense" holds the
+ * rest of the cycle-end small step).
  */
-#define SKR_NPHASE 13
+#define SKR_NPHASE 14
 skr_status skr_last_profile(double *ns_out, int32_t nphase);
 
 /* Free the device workspace cached by skr_solve_sequence (all devices). */

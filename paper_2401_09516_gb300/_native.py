@@ -442,7 +442,7 @@ def skr_last_plan():
 
 
 PHASES = ["assembly", "refresh", "projection", "operator", "multidot", "update", "gram", "dense",
-          "cycle_update", "true_residual", "other", "schur", "eigenvectors"]
+          "cycle_update", "true_residual", "other", "schur", "eigenvectors", "hessenberg"]
 
 
 def skr_last_profile():

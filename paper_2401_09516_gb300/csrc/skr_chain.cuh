@@ -221,14 +221,17 @@ struct Ctx {
     const CUtensorMap *tmap;        // basis boxes of 16 >> i columns, i < NBOX
     int ybase;                      // first column of this slot in the tensor maps
 
-    // the Schur form and eigenvector parts of a harmonic-Ritz solve, from the
-    // device clock marks it wrote (mk[0] after the Schur form, mk[1] after the
-    // eigenvectors); call after a tick that closed the phase before it
+    // the Hessenberg, Schur form and eigenvector parts of a harmonic-Ritz
+    // solve, from the device clock marks it wrote (mk[2] after the Hessenberg
+    // reduction, mk[0] after the Schur form, mk[1] after the eigenvectors);
+    // call after a tick that closed the phase before it
     __device__ __forceinline__ void tick_eigen(const unsigned long long *mk) {
         if (prof != nullptr && rank == 0 && threadIdx.x == 0) {
-            const unsigned long long m0 = mk[0] > tmark ? mk[0] : tmark;
+            const unsigned long long mh = mk[2] > tmark ? mk[2] : tmark;
+            const unsigned long long m0 = mk[0] > mh ? mk[0] : mh;
             const unsigned long long m1 = mk[1] > m0 ? mk[1] : m0;
-            atomicAdd(prof + PH_SCHUR, m0 - tmark);
+            atomicAdd(prof + PH_HESS, mh - tmark);
+            atomicAdd(prof + PH_SCHUR, m0 - mh);
             atomicAdd(prof + PH_EIGVEC, m1 - m0);
             tmark = m1;
         }
@@ -1232,7 +1235,7 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
         // the harmonic-Ritz eigenproblem in FP64 (Algorithm 2's small dense
         // step); FP32 only when the caller asks for it (skr_options.eig_fp32)
         unsigned long long *mk = reinterpret_cast<unsigned long long *>(c.D(c.P.o_sc) + 12);
-        if (threadIdx.x == 0) mk[0] = mk[1] = 0ull;
+        if (threadIdx.x == 0) mk[0] = mk[1] = mk[2] = 0ull;
         c.tick(PH_DENSE);
         if (sizeof(T) == 4 && c.eig32) {
             // odd leading dimension: the row updates of the Hessenberg

@@ -107,6 +107,6 @@ struct ChainArgs {
 };
 
 enum Phase { PH_ASM, PH_REFRESH, PH_PROJ, PH_SPMV, PH_DOT, PH_UPD, PH_GRAM, PH_DENSE, PH_CUPD, PH_RESID, PH_OTHER,
-             PH_SCHUR, PH_EIGVEC };
+             PH_SCHUR, PH_EIGVEC, PH_HESS };
 
 }  // namespace skr

@@ -147,6 +147,87 @@ __device__ inline void hessenberg_reduce(R *A, int lda, R *Z, int ldz, int n, R 
     }
 }
 
+// hessenberg_reduce for FP64 with the dot products of each reflector
+// application split over four row (or column) chunks per thread group
+// instead of warp-shuffle reductions: on this GPU every FP64 instruction,
+// the five additions of a warp reduction included, costs a sub-partition's
+// FP64 pipe many cycles, and the chunked form issues about half as many.
+// part: scratch of at least 8 n doubles.  Same reflectors as
+// hessenberg_reduce (norm, tau, v), sums in a different order.
+__device__ inline void hessenberg_reduce_chunked(double *A, int lda, double *Z, int ldz, int n, double *v,
+                                                 double *sc, double *part) {
+    typedef double R;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = lane_id(), w = warp_id();
+    for (int e = tid; e < n * n; e += nt) M_(Z, ldz, e % n, e / n) = (e % n == e / n) ? R(1) : R(0);
+    sync();
+    for (int c = 0; c + 2 < n; c++) {
+        if (w == 0) {
+            R s = R(0);
+            for (int i = c + 1 + lane; i < n; i += 32) s += M_(A, lda, i, c) * M_(A, lda, i, c);
+            s = warp_sum(s);
+            if (lane == 0) {
+                const R x0 = M_(A, lda, c + 1, c);
+                const R nrm = sqrt(s);
+                R tau = R(0), alpha = x0;
+                if (nrm > R(0) && s - x0 * x0 > R(0)) {
+                    alpha = -copysign(nrm, x0);
+                    tau = (alpha - x0) / alpha;
+                    sc[1] = R(1) / (x0 - alpha);
+                } else {
+                    sc[1] = R(0);
+                }
+                sc[0] = tau;
+                sc[2] = alpha;
+            }
+        }
+        sync();
+        const R tau = sc[0], inv = sc[1];
+        sync();
+        if (tau == R(0)) continue;
+        for (int i = c + 1 + tid; i < n; i += nt) v[i] = (i == c + 1) ? R(1) : M_(A, lda, i, c) * inv;
+        sync();
+        // left: columns j in [c, n), rows in four interleaved chunks
+        const int ncl = n - c;
+        for (int t = tid; t < 4 * ncl; t += nt) {
+            const int j = c + t % ncl, r = t / ncl;
+            R s = R(0);
+            for (int i = c + 1 + r; i < n; i += 4) s += v[i] * M_(A, lda, i, j);
+            part[r * n + j] = s;
+        }
+        sync();
+        for (int t = tid; t < 4 * ncl; t += nt) {
+            const int j = c + t % ncl, r = t / ncl;
+            const R d = tau * ((part[j] + part[n + j]) + (part[2 * n + j] + part[3 * n + j]));
+            for (int i = c + 1 + r; i < n; i += 4) M_(A, lda, i, j) -= d * v[i];
+        }
+        sync();
+        // right: rows of A and Z (2n), columns in [c+1, n) in four interleaved chunks
+        for (int t = tid; t < 8 * n; t += nt) {
+            const int rho = t % (2 * n), r = t / (2 * n);
+            const R *Mx = (rho < n) ? A : Z;
+            const int ldm = (rho < n) ? lda : ldz;
+            const int i = (rho < n) ? rho : rho - n;
+            R s = R(0);
+            for (int j = c + 1 + r; j < n; j += 4) s += M_(Mx, ldm, i, j) * v[j];
+            part[r * 2 * n + rho] = s;
+        }
+        sync();
+        for (int t = tid; t < 8 * n; t += nt) {
+            const int rho = t % (2 * n), r = t / (2 * n);
+            R *Mx = (rho < n) ? A : Z;
+            const int ldm = (rho < n) ? lda : ldz;
+            const int i = (rho < n) ? rho : rho - n;
+            const R d = tau * ((part[rho] + part[2 * n + rho]) + (part[4 * n + rho] + part[6 * n + rho]));
+            for (int j = c + 1 + r; j < n; j += 4) M_(Mx, ldm, i, j) -= d * v[j];
+        }
+        sync();
+        if (tid == 0) M_(A, lda, c + 1, c) = sc[2];
+        for (int i = c + 2 + tid; i < n; i += nt) M_(A, lda, i, c) = R(0);
+        sync();
+    }
+}
+
 // Householder vector for u = (x, y, z): P u = alpha e1.  Writes tau, v1, v2.
 // With a = -sign(x) ||u||: v = (1, y / (x - a), z / (x - a)), tau = (a - x) / a.
 // Both quotients come from one reciprocal, 1 / (a (x - a)); u is rescaled
@@ -799,8 +880,8 @@ __device__ inline void schur_eigvecs_lanes(const R *T, int ldt, int n, const R *
 // in precision R on Mr (n x n, ldm; may alias M64 when R = double) with
 // Schur vectors Zr (ldz = n).  Writes P (FP64, n x knew, ldp) and returns
 // knew (-1 if the QR iteration failed).
-// marks (optional, thread 0 writes): the device clock after the Schur form
-// and after the eigenvectors.
+// marks (optional, thread 0 writes): the device clock after the Hessenberg
+// reduction, after the Schur form and after the eigenvectors.
 template <typename R>
 __device__ __noinline__ int harmonic_select(const double *M64, int ld64, int n, int kwant, double *P, int ldp,
                                       R *Mr, int ldm, R *Zr, R *wr, R *wi, R *xr, R *xi, R *vscr,
@@ -810,7 +891,16 @@ __device__ __noinline__ int harmonic_select(const double *M64, int ld64, int n, 
         for (int e = tid; e < n * n; e += nt) M_(Mr, ldm, e % n, e / n) = (R)M_(M64, ld64, e % n, e / n);
         sync();
     }
-    hessenberg_reduce(Mr, ldm, Zr, n, n, vscr, scr);
+    if constexpr (sizeof(R) == 8) {
+        // xr, xi (contiguous, 2 (k + 1) m doubles) are free until the eigenvectors
+        if (2 * (kwant + 1) * n >= 8 * n)
+            hessenberg_reduce_chunked(Mr, ldm, Zr, n, n, vscr, scr, xr);
+        else
+            hessenberg_reduce(Mr, ldm, Zr, n, n, vscr, scr);
+    } else {
+        hessenberg_reduce(Mr, ldm, Zr, n, n, vscr, scr);
+    }
+    if (marks && threadIdx.x == 0) marks[2] = global_ns();
     const int fail = schur_form(Mr, ldm, Zr, n, n, wr, wi, isc);
     if (marks && threadIdx.x == 0) marks[0] = global_ns();
     if (fail) return -1;

@@ -91,11 +91,6 @@ struct Chain {
     int *dorder = nullptr, *dctr = nullptr, *dkc = nullptr;
     long long *doff = nullptr;
     unsigned long long *dbytes = nullptr;
-    char *pinned = nullptr;   // host staging
-    double *hcoef = nullptr, *hrhs = nullptr, *hx = nullptr;
-    DevSystem *hsys = nullptr;
-    DevResult *hres = nullptr;
-    size_t pin_bytes = 0;     // capacity of the pinned staging buffer
     bool busy = false;
     uint64_t ticket = 0;
     uint64_t last_used = 0;   // launch counter at this chain's last launch (LRU eviction)
@@ -144,7 +139,7 @@ struct ChainPlan {
     size_t bytes = 0, pin = 0;
 };
 
-// Device and pinned-host layout of a chain shaped like request r.
+// Device layout of a chain shaped like request r.
 ChainPlan chain_plan(const skr_server *S, const Request &r) {
     ChainPlan P;
     const size_t esz = S->opt.precision == SKR_PREC_FP64 ? 8 : 4;
@@ -170,7 +165,6 @@ ChainPlan chain_plan(const skr_server *S, const Request &r) {
     P.o_ctr = o;   o += 256;
     P.o_kc = o;    o += 256;
     P.bytes = o;
-    P.pin = al256(P.clen * 8) + 2 * al256(r.n * 8) + 512;
     return P;
 }
 
@@ -179,14 +173,12 @@ size_t chain_bytes(const skr_server *S, const Request &r) { return chain_plan(S,
 void destroy_chain(Chain *c) {
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->slab) cudaFree(c->slab);
-    if (c->pinned) cudaFreeHost(c->pinned);
     if (c->ev) cudaEventDestroy(c->ev);
     if (c->st) cudaStreamDestroy(c->st);
     delete c;
 }
 
-// Shape an idle chain (its device slab and pinned buffer already large
-// enough) like request r: bind the layout, forget any recycle space and
+// Shape an idle chain (its device slab already large enough) like request r: bind the layout, forget any recycle space and
 // previous solution, and set the constant descriptors of a one-system chain.
 // Returns false on a CUDA error.
 bool shape_chain(skr_server *S, Chain *c, const Request &r, const ChainPlan &P) {
@@ -213,11 +205,6 @@ bool shape_chain(skr_server *S, Chain *c, const Request &r, const ChainPlan &P) 
     c->dctr = reinterpret_cast<int *>(c->slab + P.o_ctr);
     c->dbytes = reinterpret_cast<unsigned long long *>(c->slab + P.o_ctr + 64);
     c->dkc = reinterpret_cast<int *>(c->slab + P.o_kc);
-    c->hcoef = reinterpret_cast<double *>(c->pinned);
-    c->hrhs = reinterpret_cast<double *>(c->pinned + al256(c->clen * 8));
-    c->hx = reinterpret_cast<double *>(c->pinned + al256(c->clen * 8) + al256(r.n * 8));
-    c->hsys = reinterpret_cast<DevSystem *>(c->pinned + al256(c->clen * 8) + 2 * al256(r.n * 8));
-    c->hres = reinterpret_cast<DevResult *>(c->pinned + al256(c->clen * 8) + 2 * al256(r.n * 8) + 256);
     // one chain of one system, starting with no recycle space
     cudaMemsetAsync(c->ws.basis, 0, (size_t)NCOLS * c->ld * esz, c->st);
     cudaMemsetAsync(c->slab + P.o_ord, 0, P.bytes - P.o_ord, c->st);
@@ -232,15 +219,13 @@ Chain *create_chain(skr_server *S, const Request &r) {
     const ChainPlan P = chain_plan(S, r);
     Chain *c = new Chain();
     c->bytes = P.bytes;
-    c->pin_bytes = P.pin;
     if (cudaMalloc(&c->slab, c->bytes) != cudaSuccess) {
         cudaGetLastError();
         c->slab = nullptr;
         destroy_chain(c);
         return nullptr;
     }
-    if (cudaMallocHost(&c->pinned, P.pin) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess ||
+    if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         destroy_chain(c);
@@ -256,11 +241,11 @@ Chain *create_chain(skr_server *S, const Request &r) {
 // Launch request r on chain c (server lock held).  Returns false on a CUDA error.
 bool launch(skr_server *S, Chain *c, Request *r, int cs) {
     cudaStream_t st = c->st;
-    std::memcpy(c->hcoef, r->coef.data(), r->coef.size() * 8);
-    if (!r->coef.empty()) cudaMemcpyAsync(c->dcoef, c->hcoef, r->coef.size() * 8, cudaMemcpyHostToDevice, st);
+    // copies from the request's own (pageable) host memory: the call returns
+    // once the data is staged, and the request outlives it
+    if (!r->coef.empty()) cudaMemcpyAsync(c->dcoef, r->coef.data(), r->coef.size() * 8, cudaMemcpyHostToDevice, st);
     if (!r->rhs.empty()) {
-        std::memcpy(c->hrhs, r->rhs.data(), r->n * 8);
-        cudaMemcpyAsync(c->drhs, c->hrhs, r->n * 8, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(c->drhs, r->rhs.data(), r->n * 8, cudaMemcpyHostToDevice, st);
     }
     DevSystem ds;
     ds.fmt = r->fmt;
@@ -271,8 +256,7 @@ bool launch(skr_server *S, Chain *c, Request *r, int cs) {
     ds.rhs = r->rhs.empty() ? nullptr : c->drhs;
     for (int i = 0; i < 4; i++) ds.params[i] = r->params[i];
     ds.x_out = c->dx;
-    *c->hsys = ds;
-    cudaMemcpyAsync(c->dsys, c->hsys, sizeof(DevSystem), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->dsys, &ds, sizeof(DevSystem), cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(c->dctr, 0, 128, st);
     ChainArgs a;
     a.systems = c->dsys;
@@ -305,8 +289,6 @@ bool launch(skr_server *S, Chain *c, Request *r, int cs) {
                               ? launch_chain_f64(a, 1, c->cs, S->threads, S->smem, st)
                               : launch_chain_f32(a, 1, c->cs, S->threads, S->smem, st);
     if (e != cudaSuccess) return false;
-    cudaMemcpyAsync(c->hx, c->dx, r->n * 8, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(c->hres, c->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, st);
     cudaEventRecord(c->ev, st);
     c->busy = true;
     c->ticket = r->ticket;
@@ -350,7 +332,7 @@ double sqdist(const std::vector<double> &a, const std::vector<double> &b) {
 
 // The server thread.  Each round: under the lock, collect the chains whose
 // launch finished and take a snapshot of the queue; without the lock, copy
-// their results out of the pinned staging buffers and plan the admissions;
+// their results to the requests and plan the admissions;
 // under the lock again, publish the results, evict, create chains and
 // launch.  The chain list and every chain's state are written by this
 // thread only, and only under the lock, so the unlocked reads race with
@@ -415,6 +397,7 @@ void loop(skr_server *S) {
         Chain *c;
         Request *r;
         bool ok;
+        DevResult res;
     };
     std::vector<Done> done;
     std::vector<Request *> queued;
@@ -434,7 +417,7 @@ void loop(skr_server *S) {
             }
             if (q != cudaSuccess) cudaGetLastError();
             auto it = S->reqs.find(c->ticket);
-            done.push_back({c, it != S->reqs.end() ? it->second : nullptr, q == cudaSuccess});
+            done.push_back({c, it != S->reqs.end() ? it->second : nullptr, q == cudaSuccess, DevResult{}});
         }
         if (S->stop && !any_busy && done.empty()) break;
         if (!S->stop)
@@ -442,8 +425,18 @@ void loop(skr_server *S) {
         const size_t nchains = S->chains.size();
         const size_t used = S->used;
         lk.unlock();
-        for (const Done &d : done)
-            if (d.r && d.ok) d.r->x.assign(d.c->hx, d.c->hx + d.r->n);
+        // results of finished launches: the chain's stream is idle, so these
+        // copies wait for nothing but themselves
+        for (Done &d : done) {
+            if (!d.r || !d.ok) continue;
+            d.r->x.resize(d.r->n);
+            if (cudaMemcpyAsync(d.r->x.data(), d.c->dx, d.r->n * 8, cudaMemcpyDeviceToHost, d.c->st) != cudaSuccess ||
+                cudaMemcpyAsync(&d.res, d.c->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, d.c->st) != cudaSuccess ||
+                cudaStreamSynchronize(d.c->st) != cudaSuccess) {
+                cudaGetLastError();
+                d.ok = false;
+            }
+        }
         {
             // 0 idle, 1 busy, 2 taken this round (admitted onto or evicted)
             std::vector<char> state(nchains, 0);
@@ -463,7 +456,9 @@ void loop(skr_server *S) {
             long long free_bytes = S->budget == 0 ? (1LL << 62) : (long long)S->budget - (long long)used;
             for (size_t qi = 0; qi < queued.size(); qi++) {
                 Request *r = queued[qi];
-                const int waiting = (int)(queued.size() - qi);
+                // requests that could start now: the waiting ones, at most as
+                // many as the chain limit leaves room to run beside the running ones
+                const int waiting = std::min<int>((int)(queued.size() - qi), std::max(1, S->max_chains - running));
                 const int cs = request_cs(S, r->n, free_ctas / std::max(1, waiting));
                 if (cs > free_ctas && running > 0) continue;      // wait for SMs
                 int best = -1;
@@ -518,7 +513,7 @@ void loop(skr_server *S) {
         }
         lk.lock();
         for (const Done &d : done) {
-            if (d.r) finish(S, d.r, d.ok ? d.c->hres : nullptr, d.ok);
+            if (d.r) finish(S, d.r, d.ok ? &d.res : nullptr, d.ok);
             d.c->busy = false;
         }
         for (Admit &ad : plan) {
@@ -529,8 +524,7 @@ void loop(skr_server *S) {
                 const ChainPlan P = chain_plan(S, *r);
                 // reuse the last victim in place when its memory is large enough
                 Chain *reuse = nullptr;
-                if (!ad.victims.empty() && ad.victims.back()->bytes >= P.bytes &&
-                    ad.victims.back()->pin_bytes >= P.pin) {
+                if (!ad.victims.empty() && ad.victims.back()->bytes >= P.bytes) {
                     reuse = ad.victims.back();
                     ad.victims.pop_back();
                 }

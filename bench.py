@@ -30,9 +30,11 @@ sys.path.insert(0, ROOT)
 METRIC = "systems/s to rel-res 1e-8, SKR vs plain GMRES on 1 GB300; HBM GB/s frac; p99"
 WORKLOADS = {
     # Darcy 32^2, 20 systems, no preconditioner, FP64 throughout: the small
-    # case the oracle finishes in seconds; one chain, one CTA
+    # case the oracle finishes in seconds.  Latency-bound: the sorted order is
+    # cut into 4 chains and the planner gives each a 16-CTA cluster (measured
+    # 45 against 12 systems/s for one chain on one CTA)
     "darcy32_fp64": dict(kind="darcy2d", nside=32, nsys=20, ell=0.2, sigma=1.0, seed=1, m=30, k=10,
-                         precond="none", precision="fp64", tol=1e-8, inner_tol=1e-5, chains=1, cluster_size=1,
+                         precond="none", precision="fp64", tol=1e-8, inner_tol=1e-5, chains=4, cluster_size=0,
                          desc="darcy2d 32x32 (n=1024), %d systems, a=exp(GRF ell=0.2 sigma=1), f=1, "
                               "no preconditioner, GCRO-DR m=30 k=10, FP64, tol 1e-8"),
     # Darcy on 256^2 (n = 65,536), 200 systems

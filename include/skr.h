@@ -336,7 +336,7 @@ typedef struct skr_server_info {
  * hbm_budget   bytes of device memory the server may hold for chains (each
  *              chain holds one workspace slot sized for its grid plus its
  *              request buffers); 0 = no limit
- * max_chains   upper bound on resident chains (0 = 64)
+ * max_chains   upper bound on resident chains (0 = as many as chain-kernel CTAs fit on the GPU)
  * A host thread owned by the server admits, routes, launches and collects
  * requests.  Errors: bad options -> SKR_ERR_INVALID_ARG.
  */
@@ -356,11 +356,10 @@ skr_status skr_server_create(const skr_options *opt, size_t hbm_budget, int32_t 
  * later ones.  A request waits until its cluster's CTAs fit on the GPU
  * beside the running requests (one request always runs).  It then goes to
  * the nearest idle chain of its shape (format, grid and p); else to a new
- * chain if max_chains and the budget leave room; else, when no chain of its
- * shape exists, to a new chain that replaces the least recently used idle
- * chains of other shapes (evicted: their recycle spaces are dropped); a
- * request whose shape has only busy chains waits for one of them.  So every
- * request that fits the budget on its own is eventually served.
+ * chain if max_chains and the budget leave room; else to a new chain that
+ * replaces the least recently used idle chains (evicted: their recycle
+ * spaces are dropped).  So every request that fits the budget on its own is
+ * eventually served, and no SM waits while a request could use it.
  * A request larger than the whole budget is rejected (SKR_ERR_OOM).
  */
 skr_status skr_submit(skr_server *srv, const skr_system *sys, const double *key, int64_t p,

@@ -748,10 +748,14 @@ __device__ void part_gram(Ctx<T> &c, int xa0, int na, int yb0, int nb, T *out) {
     const int nvec = (int)(c.cnt / E);
     T *wsum = reinterpret_cast<T *>(c.D(c.P.o_wsum));
     T *tmp = reinterpret_cast<T *>(c.D(c.P.o_dscr));   // TA*TB <= 64 values needed
+    // a symmetric Gram (the same columns on both sides) needs the tiles on
+    // and above the diagonal only; the rest are mirrored
+    const bool sym = (xa0 == yb0 && na == nb && TA == TB);
     for (int a0 = 0; a0 < na; a0 += TA) {
         const int ta = min(TA, na - a0);
         for (int b0 = 0; b0 < nb; b0 += TB) {
             const int tb = min(TB, nb - b0);
+            if (sym && b0 < a0) continue;
             T acc[TA * TB];
 #pragma unroll
             for (int e = 0; e < TA * TB; e++) acc[e] = T(0);
@@ -779,11 +783,12 @@ __device__ void part_gram(Ctx<T> &c, int xa0, int na, int yb0, int nb, T *out) {
             for (int e = threadIdx.x; e < ta * tb; e += blockDim.x) {
                 const int aa = e / tb, bb = e % tb;
                 out[(a0 + aa) * nb + (b0 + bb)] = res[aa * TB + bb];
+                if (sym && b0 > a0) out[(b0 + bb) * nb + (a0 + aa)] = res[aa * TB + bb];
             }
             __syncthreads();
         }
     }
-    c.bytes += (unsigned long long)(na + nb) * c.g.n * sizeof(T);
+    c.bytes += (unsigned long long)(sym ? na : na + nb) * c.g.n * sizeof(T);
 }
 
 // ------------------------------------------------------------------ assembly

@@ -349,12 +349,13 @@ double sqdist(const std::vector<double> &a, const std::vector<double> &b) {
 //      length) takes it;
 //   3. else a new chain, if the chain limit and the device-memory budget
 //      leave room;
-//   4. else, if no chain of its shape exists at all, the least recently used
-//      idle chains of other shapes are evicted until the new chain fits (an
-//      evicted chain's memory is reused in place when it is large enough);
-//      a request whose shape has a busy chain waits for it instead, so that
-//      chains of the shapes in use are not evicted back and forth.
-// So a request of a new shape is never starved by idle chains of others.
+//   4. else the least recently used idle chains are evicted until the new
+//      chain fits (an evicted chain's memory is reused in place when it is
+//      large enough).
+// A request reaches 2-4 only when its cluster fits on the free SMs, so
+// chains are evicted only for work that starts at once: while the GPU is
+// full, requests wait instead of evicting back and forth.  No request is
+// starved by idle chains of other shapes.
 void dequeue(skr_server *S, uint64_t ticket) {
     auto it = std::find(S->queue.begin(), S->queue.end(), ticket);
     if (it != S->queue.end()) S->queue.erase(it);
@@ -463,11 +464,9 @@ void loop(skr_server *S) {
                 if (cs > free_ctas && running > 0) continue;      // wait for SMs
                 int best = -1;
                 double bd = INFINITY;
-                bool resident = false;
                 for (size_t ci = 0; ci < nchains; ci++) {
                     const Chain *c = S->chains[ci];
                     if (!same_shape(c, r)) continue;
-                    resident = true;
                     if (state[ci] != 0) continue;
                     const double dist = c->key.empty() ? 0.0 : sqdist(c->key, r->key);
                     if (dist < bd) {
@@ -482,7 +481,8 @@ void loop(skr_server *S) {
                     const long long need = (long long)chain_bytes(S, *r);
                     std::vector<Chain *> victims;
                     if (free_slots < 1 || need > free_bytes) {
-                        if (resident) continue;                   // wait for a chain of its own shape
+                        // the request's cluster fits on free SMs (checked above):
+                        // run it now on a new chain in place of idle ones
                         std::vector<size_t> idle;
                         for (size_t ci = 0; ci < nchains; ci++)
                             if (state[ci] == 0) idle.push_back(ci);
@@ -600,7 +600,7 @@ skr_status skr_server_create(const skr_options *opt_in, size_t hbm_budget, int32
     skr_server *S = new skr_server();
     S->opt = opt;
     S->budget = hbm_budget;
-    S->max_chains = max_chains > 0 ? max_chains : 64;
+    S->max_chains = max_chains;   // 0: set below, one chain per resident CTA
     S->threads = chain_threads();
     S->smem = chain_smem_bytes(opt.m, opt.k, S->threads, opt.precision == SKR_PREC_FP64 ? 8 : 4);
     if (S->smem > 227 * 1024) {
@@ -617,6 +617,7 @@ skr_status skr_server_create(const skr_options *opt_in, size_t hbm_budget, int32
     for (int j = 0; j < SKR_TUNE_COLS; j++)
         S->maxc[j] = opt.precision == SKR_PREC_FP64 ? max_active_clusters_f64(SKR_TUNE_CS[j], S->threads, S->smem)
                                                     : max_active_clusters_f32(SKR_TUNE_CS[j], S->threads, S->smem);
+    if (S->max_chains == 0) S->max_chains = std::max(1, S->cap_ctas);
     if (S->cap_ctas < 1) {
         delete S;
         return err(SKR_ERR_CUDA, "the chain kernel cannot be scheduled with this shared memory");

@@ -845,6 +845,10 @@ def run_serving(args):
     """Serving: a seeded Poisson arrival stream of 2D and 3D Darcy requests
     replayed in real time against the server (skr_server_*), with recycling
     (SKR) and, with --serving-plain, again as plain GMRES (k = 0)."""
+    # every resident chain has its own stream: give them the most hardware
+    # work queues, so that a new request does not queue behind another
+    # chain's running solve (must be set before CUDA starts)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
 
     _, _, local = _dist()

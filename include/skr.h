@@ -338,7 +338,11 @@ typedef struct skr_server_info {
  *              request buffers); 0 = no limit
  * max_chains   upper bound on resident chains (0 = as many as chain-kernel CTAs fit on the GPU)
  * A host thread owned by the server admits, routes, launches and collects
- * requests.  Errors: bad options -> SKR_ERR_INVALID_ARG.
+ * requests.  Every chain has its own stream; streams share the device's
+ * hardware work queues (CUDA_DEVICE_MAX_CONNECTIONS, 8 by default), and a
+ * request whose stream shares a queue with a running solve can start only
+ * after it, so processes that serve many chains should set that variable to
+ * 32 before CUDA starts.  Errors: bad options -> SKR_ERR_INVALID_ARG.
  */
 skr_status skr_server_create(const skr_options *opt, size_t hbm_budget, int32_t max_chains,
                              skr_server **srv);

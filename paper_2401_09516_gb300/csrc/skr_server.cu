@@ -238,7 +238,8 @@ Chain *create_chain(skr_server *S, const Request &r) {
     return c;
 }
 
-// Launch request r on chain c (server lock held).  Returns false on a CUDA error.
+// Launch request r on chain c (without the server lock: this touches only
+// the chain's own device memory and stream).  Returns false on a CUDA error.
 bool launch(skr_server *S, Chain *c, Request *r, int cs) {
     cudaStream_t st = c->st;
     // copies from the request's own (pageable) host memory: the call returns
@@ -290,11 +291,6 @@ bool launch(skr_server *S, Chain *c, Request *r, int cs) {
                               : launch_chain_f32(a, 1, c->cs, S->threads, S->smem, st);
     if (e != cudaSuccess) return false;
     cudaEventRecord(c->ev, st);
-    c->busy = true;
-    c->ticket = r->ticket;
-    c->key = r->key;
-    c->last_used = ++S->launches;
-    r->state = 1;
     return cudaGetLastError() == cudaSuccess;
 }
 
@@ -516,55 +512,90 @@ void loop(skr_server *S) {
             if (d.r) finish(S, d.r, d.ok ? &d.res : nullptr, d.ok);
             d.c->busy = false;
         }
-        for (Admit &ad : plan) {
-            if (S->stop) break;
+        // victims leave the chain list under the lock (stats reads it); the
+        // one whose memory will be reshaped in place stays
+        std::vector<Chain *> dead;
+        std::vector<Chain *> reuse(plan.size(), nullptr);
+        for (size_t a = 0; a < plan.size(); a++) {
+            Admit &ad = plan[a];
+            if (ad.chain || ad.victims.empty()) continue;
+            const ChainPlan P = chain_plan(S, *ad.r);
+            if (ad.victims.back()->bytes >= P.bytes) {
+                reuse[a] = ad.victims.back();
+                ad.victims.pop_back();
+            }
+            for (Chain *v : ad.victims) {
+                S->chains.erase(std::find(S->chains.begin(), S->chains.end(), v));
+                S->used -= v->bytes;
+                S->evicted += 1;
+                dead.push_back(v);
+            }
+        }
+        const bool stopping = S->stop;
+        lk.unlock();
+        // every CUDA call of the admissions runs without the lock, so that
+        // skr_submit and skr_poll never wait for one (a copy from pageable
+        // memory can wait behind a running solve)
+        for (Chain *v : dead) destroy_chain(v);
+        std::vector<Chain *> fresh(plan.size(), nullptr), ran(plan.size(), nullptr);
+        std::vector<char> failed(plan.size(), 0);
+        size_t used_after = S->used;
+        for (size_t a = 0; a < plan.size() && !stopping; a++) {
+            Admit &ad = plan[a];
             Request *r = ad.r;
             Chain *c = ad.chain;
             if (!c) {
                 const ChainPlan P = chain_plan(S, *r);
-                // reuse the last victim in place when its memory is large enough
-                Chain *reuse = nullptr;
-                if (!ad.victims.empty() && ad.victims.back()->bytes >= P.bytes) {
-                    reuse = ad.victims.back();
-                    ad.victims.pop_back();
-                }
-                for (Chain *v : ad.victims) {
-                    S->chains.erase(std::find(S->chains.begin(), S->chains.end(), v));
-                    S->used -= v->bytes;
-                    destroy_chain(v);
-                    S->evicted += 1;
-                }
-                if (reuse) {
-                    S->evicted += 1;
-                    if (shape_chain(S, reuse, *r, P)) {
-                        c = reuse;
-                    } else {
-                        S->chains.erase(std::find(S->chains.begin(), S->chains.end(), reuse));
-                        S->used -= reuse->bytes;
-                        destroy_chain(reuse);
-                    }
-                } else {
-                    if (S->budget != 0 && S->used + P.bytes > S->budget) continue;   // stays queued
+                if (reuse[a]) {
+                    if (shape_chain(S, reuse[a], *r, P)) c = reuse[a];
+                } else if (S->budget == 0 || used_after + P.bytes <= S->budget) {
                     c = create_chain(S, *r);
                     if (c) {
-                        S->chains.push_back(c);
-                        S->used += c->bytes;
+                        fresh[a] = c;
+                        used_after += c->bytes;
                     }
+                } else {
+                    continue;   // stays queued
                 }
                 if (!c) {
-                    // device memory could not be obtained: fail the request
-                    // rather than keep it queued
-                    finish(S, r, nullptr, false);
-                    dequeue(S, r->ticket);
+                    failed[a] = 1;   // device memory could not be obtained
                     continue;
                 }
             }
-            if (!launch(S, c, r, ad.cs)) {
+            if (launch(S, c, r, ad.cs))
+                ran[a] = c;
+            else
+                failed[a] = 1;
+        }
+        lk.lock();
+        for (size_t a = 0; a < plan.size(); a++) {
+            Request *r = plan[a].r;
+            if (fresh[a]) {
+                S->chains.push_back(fresh[a]);
+                S->used += fresh[a]->bytes;
+            }
+            if (reuse[a] && !ran[a] && failed[a]) {
+                // the reshape failed: drop the chain (rare; its stream is idle)
+                S->chains.erase(std::find(S->chains.begin(), S->chains.end(), reuse[a]));
+                S->used -= reuse[a]->bytes;
+                S->evicted += 1;
+                destroy_chain(reuse[a]);
+            } else if (reuse[a]) {
+                S->evicted += 1;
+            }
+            if (ran[a]) {
+                Chain *c = ran[a];
+                c->busy = true;
+                c->ticket = r->ticket;
+                c->key = r->key;
+                c->last_used = ++S->launches;
+                r->state = 1;
+                dequeue(S, r->ticket);
+            } else if (failed[a]) {
                 cudaGetLastError();
                 finish(S, r, nullptr, false);
-                c->busy = false;
+                dequeue(S, r->ticket);
             }
-            dequeue(S, r->ticket);
         }
         S->cv.wait_for(lk, std::chrono::microseconds(50));
     }

@@ -764,11 +764,13 @@ skr_status skr_solve_sequence(const skr_system *systems, int64_t N, const int32_
         plan.push_back(k);
     } else {
         std::vector<long long> cn(nchains), cl(nchains);
+        std::vector<char> c3(nchains);
         for (int c = 0; c < nchains; c++) {
             cn[c] = sys_n(systems[ord[off[c]]]);
             cl[c] = off[c + 1] - off[c];
+            c3[c] = is_3d(systems[ord[off[c]]].fmt) ? 1 : 0;
         }
-        plan = plan_launches(cn, cl, maxc(1), maxc, opt.max_slots);
+        plan = plan_launches(cn, cl, maxc(1), maxc, opt.max_slots, &c3);
         if (plan.empty()) return fail(SKR_ERR_CUDA, "no launch shape of the chain kernel can be scheduled");
     }
     const int nlaunch = (int)plan.size();

@@ -495,7 +495,24 @@ __device__ void dual_update(Ctx<T> &c, int c0, int q, const T *sv, const T *al, 
     const VT *uv = reinterpret_cast<const VT *>(c.col(ucol) + c.lo);
     VT *wv = reinterpret_cast<VT *>(c.col(wcol) + c.lo);
     VT *ov = reinterpret_cast<VT *>(c.col(vcol) + c.lo);
+    // the loads of one block of rows per thread are few (one vector per
+    // column, eight columns in flight): warp 0 asks L2 for the block two
+    // ahead of every column the pass reads, so that the loads find it there
+    const int bv = blockDim.x;   // vectors per block of rows
+    auto prefetch = [&](int blk) {
+        const long long v0 = (long long)blk * bv;
+        if (warp_id() != 0 || v0 >= nvec) return;
+        const unsigned bytes = (unsigned)(min((long long)bv, (long long)nvec - v0) * sizeof(VT));
+        for (int j = lane_id(); j < q + 2; j += 32) {
+            const int col = (j < q) ? c0 + j : (j == q ? ucol : wcol);
+            if (j == q + 1 && !NEXT) continue;
+            prefetch_l2(c.col(col) + c.lo + v0 * E, bytes);
+        }
+    };
+    prefetch(0);
+    prefetch(1);
     for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+        prefetch(i / bv + 2);
         VT vv = uv[i];
         VT nx = vv;
         if (NEXT) nx = vaxmy(wv[i], bet, vv);
@@ -617,7 +634,20 @@ __device__ void spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
     const int sL = (c.g.nst == 5) ? 3 : 5;   // slots of the -1 / +1 neighbours
     if (!c.g.cols && last % E == 0) {
         const long long n = c.g.n;
+        // warp 0 asks L2 for the coefficient rows and the source rows two
+        // blocks ahead (a block = E rows per thread)
+        const long long brows = (long long)E * blockDim.x;
+        auto prefetch = [&](long long blk) {
+            const long long r0 = c.lo + blk * brows;
+            if (warp_id() != 0 || r0 >= hi) return;
+            const unsigned bytes = (unsigned)(min(brows, hi - r0) * sizeof(T));
+            for (int s = lane_id(); s <= c.g.nst; s += 32)
+                prefetch_l2((s < c.g.nst ? c.Aw + (long long)s * c.ld : src) + r0, bytes);
+        };
+        prefetch(0);
+        prefetch(1);
         for (long long p = c.lo + (long long)E * threadIdx.x; p < hi; p += (long long)E * blockDim.x) {
+            prefetch((p - c.lo) / brows + 2);
             if (p >= n) {
                 if (vout) *reinterpret_cast<VT *>(vout + p) = vzero(T(0));
                 *reinterpret_cast<VT *>(y + p) = vzero(T(0));
@@ -1325,7 +1355,23 @@ __device__ double run_cycle(Ctx<T> &c, double rnw, double target) {
     const int nin_a = kc + Ld + 1, nin_b = kc + Ld;
     T tacc[1] = {T(0)};
     constexpr int UB = 8;
+    // warp 0 asks L2 for every input column's rows two blocks ahead (a block
+    // = two rows per thread): [C, V_0..V_Ld], U, r and d
+    const long long brows = 2LL * blockDim.x, pend = c.lo + c.cnt;
+    auto prefetch = [&](long long blk) {
+        const long long r0 = c.lo + blk * brows;
+        if (warp_id() != 0 || r0 >= pend) return;
+        const unsigned bytes = (unsigned)(min(brows, pend - r0) * sizeof(T));
+        for (int j = lane_id(); j < nin_a + kc + 2; j += 32) {
+            const T *col = (j < nin_a) ? c.col(cQ0 + j) : (j < nin_a + kc) ? c.col(COL_U0 + j - nin_a)
+                                                                           : (j == nin_a + kc ? rw : dh);
+            prefetch_l2(col + r0, bytes);
+        }
+    };
+    prefetch(0);
+    prefetch(1);
     for (long long p = c.lo + 2 * threadIdx.x; p < c.lo + c.cnt; p += 2 * blockDim.x) {
+        prefetch((p - c.lo) / brows + 2);
         T o0[KMAX], o1[KMAX];
 #pragma unroll
         for (int b2 = 0; b2 < KMAX; b2++) o0[b2] = o1[b2] = T(0);

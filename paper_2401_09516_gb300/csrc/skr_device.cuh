@@ -136,6 +136,12 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
         : "memory");
     return ok != 0;
 }
+// Hint: fetch `bytes` (a multiple of 16) of global memory from the 16-byte
+// aligned address p into L2 ahead of use; nothing waits for it.
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(bytes)
+                 : "memory");
+}
 // Order this thread's earlier generic-proxy global writes before later
 // async-proxy (bulk copy) reads of the same addresses.
 __device__ __forceinline__ void fence_proxy_async_global() {

@@ -53,8 +53,12 @@ inline double tuned_step_us(long long n, int cs) {
     return col(SKR_TUNE_COLS - 1);
 }
 
-// Relative Arnoldi steps per system of n unknowns.
-inline double plan_step_weight(long long n) { return std::sqrt((double)std::max<long long>(n, 1)); }
+// Relative Arnoldi steps per system of n unknowns: they grow like the grid
+// side for these elliptic problems, sqrt(n) in 2D and cbrt(n) in 3D.
+inline double plan_step_weight(long long n, bool three_d = false) {
+    const double x = (double)std::max<long long>(n, 1);
+    return three_d ? std::cbrt(x) : std::sqrt(x);
+}
 
 // Cluster size with the least CTA time per step (ties to the smaller).
 inline int plan_efficient_cs(long long n) {
@@ -100,9 +104,9 @@ inline double plan_lpt_makespan(const std::vector<double> &dur_desc, int slots) 
 // CTAs that fit at once; max_clusters: cap on clusters over all launches
 // (0 = none).  Returns the launches (empty if nothing can be scheduled).
 //
-// Model: a chain of len systems of n unknowns takes len x sqrt(n) x
-// t(n, cs) (the measured table, steps per system taken proportional to
-// sqrt(n)); a launch's finish time is its chains' longest-first list
+// Model: a chain of len systems of n unknowns takes len x w(n) x t(n, cs)
+// (the measured table; steps per system w(n) proportional to the grid side,
+// sqrt(n) in 2D, cbrt(n) in 3D); a launch's finish time is its chains' longest-first list
 // schedule over its clusters; the plan's time is the latest launch's.
 // Clusters go one at a time to the launch that finishes last while CTAs
 // (and the cluster cap) allow; the cluster size of each group of equal-n
@@ -110,7 +114,8 @@ inline double plan_lpt_makespan(const std::vector<double> &dur_desc, int slots) 
 // one CTA per cluster.
 template <typename MaxClusters>
 std::vector<LaunchClass> plan_launches(const std::vector<long long> &chain_n, const std::vector<long long> &chain_len,
-                                       int cap_ctas, MaxClusters maxc, int max_clusters) {
+                                       int cap_ctas, MaxClusters maxc, int max_clusters,
+                                       const std::vector<char> *chain_3d = nullptr) {
     const int nc = (int)chain_n.size();
     std::vector<LaunchClass> out;
     if (nc == 0 || cap_ctas < 1) return out;
@@ -120,7 +125,8 @@ std::vector<LaunchClass> plan_launches(const std::vector<long long> &chain_n, co
         if (SKR_TUNE_CS[j] <= cap_ctas && maxc(SKR_TUNE_CS[j]) > 0) cands.push_back(SKR_TUNE_CS[j]);
     if (cands.empty()) return out;
     auto chain_us = [&](int c, int cs) {
-        return (double)chain_len[c] * plan_step_weight(chain_n[c]) * tuned_step_us(chain_n[c], cs);
+        const bool d3 = chain_3d && (*chain_3d)[c];
+        return (double)chain_len[c] * plan_step_weight(chain_n[c], d3) * tuned_step_us(chain_n[c], cs);
     };
     // groups of chains with equal n
     std::vector<long long> gn;

@@ -124,10 +124,13 @@ namespace {
 
 // Cluster size of one request of n unknowns: the caller's if set; else,
 // from the measured launch table (skr_plan.h), the fastest size whose CTA
-// time per Arnoldi step is within 1.6x of the cheapest size's and whose CTAs
-// leave room for the other waiting requests (share = free CTAs / requests
-// waiting, at least 1): one fast cluster per request under light load, the
-// cheapest clusters when the queue is long.
+// time per Arnoldi step is within 1.6x of the cheapest size's and that is
+// at most `share` CTAs.  The share is the request's part of the GPU's CTAs
+// in proportion to its estimated work (n times the grid side, the planner's
+// weight)
+// among the running and waiting requests, and never more than the CTAs
+// free now: one fast cluster per request under light load, and under load
+// clusters sized so that the largest requests do not straggle on one SM.
 int request_cs(const skr_server *S, long long n, int share);
 
 
@@ -449,14 +452,19 @@ void loop(skr_server *S) {
                     running++;
                 }
             }
+            // estimated work of the running and waiting requests (the share of each)
+            double work_total = 0.0;
+            for (size_t ci = 0; ci < nchains; ci++)
+                if (state[ci] == 1)
+                    work_total += (double)S->chains[ci]->n * plan_step_weight(S->chains[ci]->n, fmt3d(S->chains[ci]->fmt));
+            for (Request *r : queued) work_total += (double)r->n * plan_step_weight(r->n, fmt3d(r->fmt));
             long long free_slots = (long long)S->max_chains - (long long)nchains;
             long long free_bytes = S->budget == 0 ? (1LL << 62) : (long long)S->budget - (long long)used;
             for (size_t qi = 0; qi < queued.size(); qi++) {
                 Request *r = queued[qi];
-                // requests that could start now: the waiting ones, at most as
-                // many as the chain limit leaves room to run beside the running ones
-                const int waiting = std::min<int>((int)(queued.size() - qi), std::max(1, S->max_chains - running));
-                const int cs = request_cs(S, r->n, free_ctas / std::max(1, waiting));
+                const double wr = (double)r->n * plan_step_weight(r->n, fmt3d(r->fmt));
+                const int want = (int)std::floor(S->cap_ctas * wr / std::max(wr, work_total));
+                const int cs = request_cs(S, r->n, std::min(std::max(1, want), std::max(1, free_ctas)));
                 if (cs > free_ctas && running > 0) continue;      // wait for SMs
                 int best = -1;
                 double bd = INFINITY;

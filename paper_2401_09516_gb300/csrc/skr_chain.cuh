@@ -726,37 +726,55 @@ template <typename T>
 __device__ void ilu_spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
     const T *inv = c.Aw + (long long)7 * c.ld;
     T *z = c.col(COL_Z);
-    const long long hi = c.lo + c.cnt;
+    const long long hi = c.lo + c.cnt, n = c.g.n;
     const bool blocks = c.pc_bs < c.g.n;
-    for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
-        if (p < c.g.n) {
-            if (vout) vout[p] = s * __ldcg(src + p);
-            if (grid_color(c.g, p) == 1) {
-                long long blo, bhi;
-                pc_block(p, c.pc_bs, c.g.n, blo, bhi);
-                z[p] = ilu_sweep1_row<T, T>(c.g, c.Aw, c.ld, inv, src, s, p, blo, bhi);
+    // two consecutive rows per thread: along a grid line the first rows of
+    // all lanes share a colour, so each colour sweep runs without divergence
+    // and every thread has two rows' loads in flight (chunks hold an even
+    // number of rows)
+    const long long step = 2LL * blockDim.x;
+    for (long long p0 = c.lo + 2LL * threadIdx.x; p0 < hi; p0 += step) {
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const long long p = p0 + e;
+            if (p < n) {
+                if (vout) vout[p] = s * __ldcg(src + p);
+                if (grid_color(c.g, p) == 1) {
+                    long long blo, bhi;
+                    pc_block(p, c.pc_bs, n, blo, bhi);
+                    z[p] = ilu_sweep1_row<T, T>(c.g, c.Aw, c.ld, inv, src, s, p, blo, bhi);
+                }
+            } else {
+                if (vout) vout[p] = T(0);
+                z[p] = T(0);
+                y[p] = T(0);
             }
-        } else {
-            if (vout) vout[p] = T(0);
-            z[p] = T(0);
-            y[p] = T(0);
         }
     }
     cl_sync();
-    for (long long p = c.lo + threadIdx.x; p < hi && p < c.g.n; p += blockDim.x) {
-        if (grid_color(c.g, p) == 0) {
-            long long blo, bhi;
-            pc_block(p, c.pc_bs, c.g.n, blo, bhi);
-            z[p] = ilu_sweep2_row<T, T>(c.g, c.Aw, c.ld, inv, src, s, z, p, blo, bhi);
-            // block-Jacobi leaves the couplings to other blocks out of M, so
-            // the red rows of A M^-1 keep them
-            const T v = s * __ldcg(src + p);
-            y[p] = blocks ? v + ilu_red_cross_row(c.g, c.Aw, c.ld, z, p, blo, bhi) : v;
+    for (long long p0 = c.lo + 2LL * threadIdx.x; p0 < hi; p0 += step) {
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const long long p = p0 + e;
+            if (p < n && grid_color(c.g, p) == 0) {
+                long long blo, bhi;
+                pc_block(p, c.pc_bs, n, blo, bhi);
+                z[p] = ilu_sweep2_row<T, T>(c.g, c.Aw, c.ld, inv, src, s, z, p, blo, bhi);
+                // block-Jacobi leaves the couplings to other blocks out of M, so
+                // the red rows of A M^-1 keep them
+                const T v = s * __ldcg(src + p);
+                y[p] = blocks ? v + ilu_red_cross_row(c.g, c.Aw, c.ld, z, p, blo, bhi) : v;
+            }
         }
     }
     cl_sync();
-    for (long long p = c.lo + threadIdx.x; p < hi && p < c.g.n; p += blockDim.x)
-        if (grid_color(c.g, p) == 1) y[p] = ilu_black_apply_row(c.g, c.Aw, c.ld, z, p);
+    for (long long p0 = c.lo + 2LL * threadIdx.x; p0 < hi; p0 += step) {
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const long long p = p0 + e;
+            if (p < n && grid_color(c.g, p) == 1) y[p] = ilu_black_apply_row(c.g, c.Aw, c.ld, z, p);
+        }
+    }
     __syncthreads();
     c.bytes += (unsigned long long)(6 + (vout ? 1 : 0) + 2 * c.g.nst) * c.g.n * sizeof(T);
 }

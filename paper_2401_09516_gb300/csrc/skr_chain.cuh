@@ -738,11 +738,11 @@ __device__ void ilu_spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
         for (int e = 0; e < 2; e++) {
             const long long p = p0 + e;
             if (p < n) {
-                if (vout) vout[p] = s * __ldcg(src + p);
+                if (vout) vout[p] = s * src[p];
                 if (grid_color(c.g, p) == 1) {
                     long long blo, bhi;
                     pc_block(p, c.pc_bs, n, blo, bhi);
-                    z[p] = ilu_sweep1_row<T, T>(c.g, c.Aw, c.ld, inv, src, s, p, blo, bhi);
+                    z[p] = ilu_sweep1_row<T, T>(c.g, c.Aw, c.ld, inv, src, s, p, blo, bhi, c.lo, hi);
                 }
             } else {
                 if (vout) vout[p] = T(0);
@@ -759,11 +759,11 @@ __device__ void ilu_spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
             if (p < n && grid_color(c.g, p) == 0) {
                 long long blo, bhi;
                 pc_block(p, c.pc_bs, n, blo, bhi);
-                z[p] = ilu_sweep2_row<T, T>(c.g, c.Aw, c.ld, inv, src, s, z, p, blo, bhi);
+                z[p] = ilu_sweep2_row<T, T>(c.g, c.Aw, c.ld, inv, src, s, z, p, blo, bhi, c.lo, hi);
                 // block-Jacobi leaves the couplings to other blocks out of M, so
                 // the red rows of A M^-1 keep them
-                const T v = s * __ldcg(src + p);
-                y[p] = blocks ? v + ilu_red_cross_row(c.g, c.Aw, c.ld, z, p, blo, bhi) : v;
+                const T v = s * src[p];
+                y[p] = blocks ? v + ilu_red_cross_row(c.g, c.Aw, c.ld, z, p, blo, bhi, c.lo, hi) : v;
             }
         }
     }
@@ -772,7 +772,7 @@ __device__ void ilu_spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
 #pragma unroll
         for (int e = 0; e < 2; e++) {
             const long long p = p0 + e;
-            if (p < n && grid_color(c.g, p) == 1) y[p] = ilu_black_apply_row(c.g, c.Aw, c.ld, z, p);
+            if (p < n && grid_color(c.g, p) == 1) y[p] = ilu_black_apply_row(c.g, c.Aw, c.ld, z, p, c.lo, hi);
         }
     }
     __syncthreads();

@@ -282,6 +282,16 @@ __device__ __forceinline__ int grid_color(const Geom &g, long long p) {
     return (int)((i + j + l) & 1);
 }
 
+// Value at index q of a vector that CTAs of the cluster write between
+// passes: rows in [olo, ohi) belong to the calling CTA, whose own stores keep
+// its L1 coherent, so they may come through L1; other rows come from L2
+// (another SM's L1 could hold a stale copy).  olo = ohi reads everything
+// from L2.
+template <typename V>
+__device__ __forceinline__ V ld_owned(const V *v, long long q, long long olo, long long ohi) {
+    return (q >= olo && q < ohi) ? v[q] : __ldcg(v + q);
+}
+
 // slot of the coefficient that couples the neighbour back to p
 __device__ __forceinline__ int opposite_slot(int s) { return (s & 1) ? s + 1 : s - 1; }
 
@@ -338,12 +348,13 @@ __device__ __forceinline__ double sweep_inv_pivot(const Geom &g, const double *A
 // (neighbours outside [lo, hi) are skipped: block-Jacobi)
 template <typename R, typename Tv>
 __device__ __forceinline__ R ilu_sweep1_row(const Geom &g, const R *Aw, long long ld, const R *inv, const Tv *src,
-                                            R scale, long long p, long long lo, long long hi) {
-    R acc = scale * (R)__ldcg(src + p);
+                                            R scale, long long p, long long lo, long long hi, long long olo = 0,
+                                            long long ohi = 0) {
+    R acc = scale * (R)ld_owned(src, p, olo, ohi);
     for (int s = 1; s < g.nst; s++) {
         const long long q = nb_index(g, p, s);
         if (q < lo || q >= hi) continue;
-        acc -= Aw[(long long)s * ld + p] * __ldcg(inv + q) * (scale * (R)__ldcg(src + q));
+        acc -= Aw[(long long)s * ld + p] * ld_owned(inv, q, olo, ohi) * (scale * (R)ld_owned(src, q, olo, ohi));
     }
     return inv[p] * acc;
 }
@@ -351,12 +362,13 @@ __device__ __forceinline__ R ilu_sweep1_row(const Geom &g, const R *Aw, long lon
 // sweep 2 (red rows): z_r = inv_r (v_r - sum_b a_rb z_b), b in [lo, hi)
 template <typename R, typename Tv>
 __device__ __forceinline__ R ilu_sweep2_row(const Geom &g, const R *Aw, long long ld, const R *inv, const Tv *src,
-                                            R scale, const R *z, long long p, long long lo, long long hi) {
-    R acc = scale * (R)__ldcg(src + p);
+                                            R scale, const R *z, long long p, long long lo, long long hi,
+                                            long long olo = 0, long long ohi = 0) {
+    R acc = scale * (R)ld_owned(src, p, olo, ohi);
     for (int s = 1; s < g.nst; s++) {
         const long long q = nb_index(g, p, s);
         if (q < lo || q >= hi) continue;
-        acc -= Aw[(long long)s * ld + p] * __ldcg(z + q);
+        acc -= Aw[(long long)s * ld + p] * ld_owned(z, q, olo, ohi);
     }
     return inv[p] * acc;
 }
@@ -366,23 +378,24 @@ __device__ __forceinline__ R ilu_sweep2_row(const Geom &g, const R *Aw, long lon
 // the red rows of A M^-1 are unit rows)
 template <typename R>
 __device__ __forceinline__ R ilu_red_cross_row(const Geom &g, const R *Aw, long long ld, const R *z, long long p,
-                                               long long lo, long long hi) {
+                                               long long lo, long long hi, long long olo = 0, long long ohi = 0) {
     R acc = R(0);
     for (int s = 1; s < g.nst; s++) {
         const long long q = nb_index(g, p, s);
         if (q >= lo && q < hi) continue;
-        acc += Aw[(long long)s * ld + p] * __ldcg(z + q);
+        acc += Aw[(long long)s * ld + p] * ld_owned(z, q, olo, ohi);
     }
     return acc;
 }
 
 // A z on a black row: a_bb z_b + sum_r a_br z_r
 template <typename R>
-__device__ __forceinline__ R ilu_black_apply_row(const Geom &g, const R *Aw, long long ld, const R *z, long long p) {
-    R acc = Aw[p] * __ldcg(z + p);
+__device__ __forceinline__ R ilu_black_apply_row(const Geom &g, const R *Aw, long long ld, const R *z, long long p,
+                                                 long long olo = 0, long long ohi = 0) {
+    R acc = Aw[p] * ld_owned(z, p, olo, ohi);
     for (int s = 1; s < g.nst; s++) {
         const long long q = nb_index(g, p, s);
-        acc += Aw[(long long)s * ld + p] * __ldcg(z + q);
+        acc += Aw[(long long)s * ld + p] * ld_owned(z, q, olo, ohi);
     }
     return acc;
 }

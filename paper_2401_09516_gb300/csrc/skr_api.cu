@@ -645,6 +645,13 @@ skr_status skr_apply(const skr_system *sys, int32_t precond, int32_t pc_blocks, 
                                                              zb.as<double>(), yout, stage, bs);
         }
         CUDA_TRY(cudaGetLastError());
+    } else if (precision == SKR_PREC_MIXED && sym_compact_form(sys->fmt, precond, 4, g)) {
+        // the chain kernel's compact symmetric operator
+        CUDA_TRY(Aw.alloc((size_t)sym_compact_slots(g) * g.n * 4));
+        CUDA_TRY(vw.alloc((size_t)g.n * 4));
+        sym_fold_kernel<<<gb, 256, 0, st>>>(g, A.as<double>(), g.n, dinv.as<double>(), Aw.as<float>());
+        to_working_kernel<float><<<gb, 256, 0, st>>>(vin, g.n, vw.as<float>());
+        sym_apply_kernel<<<gb, 256, 0, st>>>(g, Aw.as<float>(), g.n, vw.as<float>(), yout);
     } else if (precision == SKR_PREC_MIXED) {
         CUDA_TRY(Aw.alloc((size_t)g.nst * g.n * 4));
         CUDA_TRY(vw.alloc((size_t)g.n * 4));

@@ -199,6 +199,7 @@ struct Ctx {
     // parameters
     int m, k, maxit, precond, pc_blocks;
     int eig32;         // mixed form: harmonic-Ritz eigen-solve in FP32 (opt-in)
+    int symc;          // operator kept in the compact symmetric form (sym_compact_form)
     long long pc_bs;   // rows per block of the colour sweeps (n unless block-Jacobi)
     // shared memory
     SmemPlan P;
@@ -260,6 +261,12 @@ struct Ctx {
 template <typename T>
 __device__ __forceinline__ unsigned long long csr_index_bytes(const Ctx<T> &c) {
     return c.g.cols ? (unsigned long long)c.g.nst * c.g.n * 4 : 0ull;
+}
+
+// Arrays of the working-precision operator one pass over it reads.
+template <typename T>
+__device__ __forceinline__ int op_slots(const Ctx<T> &c) {
+    return c.symc ? sym_compact_slots(c.g) : c.g.nst;
 }
 
 // Sum the CTA partials red<R>()[0..nv) over the cluster into vals<R>().
@@ -619,6 +626,93 @@ __device__ __noinline__ void staged_gram(Ctx<T> &c, int a0, int na, int b0, int 
     __syncthreads();
 }
 
+// Own rows of an operator pass in the compact symmetric form (FP32 only;
+// see sym_compact_form): E consecutive rows per thread, the fastest grid
+// index along the vector.  Row p gets
+//   y_p = s (u_p + f_p d_{p+1} u_{p+1} + f_{p-1} d_{p-1} u_{p-1}
+//            + sum over the other axis pairs t of the same two terms at +-o_t),
+// with d = D^-1 and f the plus-side couplings of the pair.  The rows of this
+// CTA were written by it (read through L1); neighbour rows through L2.
+template <typename T>
+__device__ __forceinline__ void spmv_sym_rows(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
+    typedef typename Vec<T>::type VT;
+    constexpr int E = Vec<T>::N;
+    const long long n = c.g.n, hi = c.lo + c.cnt;
+    const int tf = (c.g.nst - 1) >> 1;            // the pair of the fastest axis
+    const T *dv = c.Aw;                            // D^-1
+    const T *ff = c.Aw + (long long)tf * c.ld;     // couplings to p + 1
+    const long long brows = (long long)E * blockDim.x;
+    auto prefetch = [&](long long blk) {
+        const long long r0 = c.lo + blk * brows;
+        if (warp_id() != 0 || r0 >= hi) return;
+        const unsigned bytes = (unsigned)(min(brows, hi - r0) * sizeof(T));
+        for (int t = lane_id(); t <= tf + 1; t += 32)
+            prefetch_l2((t <= tf ? c.Aw + (long long)t * c.ld : src) + r0, bytes);
+    };
+    prefetch(0);
+    prefetch(1);
+    for (long long p = c.lo + (long long)E * threadIdx.x; p < hi; p += (long long)E * blockDim.x) {
+        prefetch((p - c.lo) / brows + 2);
+        if (p >= n) {
+            if (vout) *reinterpret_cast<VT *>(vout + p) = vzero(T(0));
+            *reinterpret_cast<VT *>(y + p) = vzero(T(0));
+            continue;
+        }
+        const VT xc = __ldcg(reinterpret_cast<const VT *>(src + p));
+        const VT dc = *reinterpret_cast<const VT *>(dv + p);
+        const VT fc = *reinterpret_cast<const VT *>(ff + p);
+        const bool hl = p > 0, hr = p + E < n;
+        const T xlf = hl ? __ldcg(src + p - 1) : T(0), dlf = hl ? __ldcg(dv + p - 1) : T(0);
+        const T flf = hl ? __ldcg(ff + p - 1) : T(0);
+        const T xrg = hr ? __ldcg(src + p + E) : T(0), drg = hr ? __ldcg(dv + p + E) : T(0);
+        const T *xa = reinterpret_cast<const T *>(&xc);
+        const T *da = reinterpret_cast<const T *>(&dc);
+        const T *fa = reinterpret_cast<const T *>(&fc);
+        T acc[E];
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            const T xr = (e == E - 1) ? xrg : xa[e + 1], dr = (e == E - 1) ? drg : da[e + 1];
+            const T xl = (e == 0) ? xlf : xa[e - 1], dl = (e == 0) ? dlf : da[e - 1];
+            const T fl = (e == 0) ? flf : fa[e - 1];
+            acc[e] = xa[e] + fa[e] * (dr * xr) + fl * (dl * xl);
+        }
+        for (int t = 1; t < tf; t++) {
+            const long long o = c.g.off[2 * t];   // > 0, a multiple of E
+            const T *ft = c.Aw + (long long)t * c.ld;
+            if (p + o < n) {
+                const VT fp = *reinterpret_cast<const VT *>(ft + p);
+                const VT xq = __ldcg(reinterpret_cast<const VT *>(src + p + o));
+                const VT dq = __ldcg(reinterpret_cast<const VT *>(dv + p + o));
+                const T *f1 = reinterpret_cast<const T *>(&fp);
+                const T *x1 = reinterpret_cast<const T *>(&xq);
+                const T *d1 = reinterpret_cast<const T *>(&dq);
+#pragma unroll
+                for (int e = 0; e < E; e++) acc[e] += f1[e] * (d1[e] * x1[e]);
+            }
+            if (p - o >= 0) {
+                const VT fm = __ldcg(reinterpret_cast<const VT *>(ft + p - o));
+                const VT xq = __ldcg(reinterpret_cast<const VT *>(src + p - o));
+                const VT dq = __ldcg(reinterpret_cast<const VT *>(dv + p - o));
+                const T *f1 = reinterpret_cast<const T *>(&fm);
+                const T *x1 = reinterpret_cast<const T *>(&xq);
+                const T *d1 = reinterpret_cast<const T *>(&dq);
+#pragma unroll
+                for (int e = 0; e < E; e++) acc[e] += f1[e] * (d1[e] * x1[e]);
+            }
+        }
+        VT out, vv;
+        T *oa = reinterpret_cast<T *>(&out);
+        T *va = reinterpret_cast<T *>(&vv);
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            oa[e] = s * acc[e];
+            va[e] = s * xa[e];
+        }
+        if (vout) *reinterpret_cast<VT *>(vout + p) = vv;
+        *reinterpret_cast<VT *>(y + p) = out;
+    }
+}
+
 // Operator pass of an Arnoldi step: for own rows, vout = s * src (the new
 // basis vector, if vout) and y = A M^-1 (s * src); padded rows get zeros.
 template <typename T>
@@ -632,7 +726,9 @@ __device__ void spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
     // is a multiple of E, so all loads are 16-byte vectors
     const int last = (c.g.nst == 5) ? c.g.ny : c.g.nz;
     const int sL = (c.g.nst == 5) ? 3 : 5;   // slots of the -1 / +1 neighbours
-    if (!c.g.cols && last % E == 0) {
+    if (sizeof(T) == 4 && c.symc) {
+        spmv_sym_rows(c, src, s, vout, y);
+    } else if (!c.g.cols && last % E == 0) {
         const long long n = c.g.n;
         // warp 0 asks L2 for the coefficient rows and the source rows two
         // blocks ahead (a block = E rows per thread)
@@ -714,7 +810,7 @@ __device__ void spmv_pass(Ctx<T> &c, const T *src, T s, T *vout, T *y) {
         }
     }
     __syncthreads();
-    c.bytes += (unsigned long long)(3 + (vout ? 1 : 0) + c.g.nst) * c.g.n * sizeof(T) -
+    c.bytes += (unsigned long long)(3 + (vout ? 1 : 0) + op_slots(c)) * c.g.n * sizeof(T) -
                (unsigned long long)(vout ? 0 : 1) * c.g.n * sizeof(T) + csr_index_bytes(c);
 }
 
@@ -889,6 +985,19 @@ __device__ __noinline__ void assemble_system(Ctx<T> &c, const DevSystem &sys) {
                 for (int s = 0; s < c.g.nst; s++) c.Aw[(long long)s * c.ld + p] = T(0);
             }
         }
+    } else if (c.symc) {
+        // compact symmetric form: D^-1 and the plus-side couplings of own
+        // rows; operator passes read the neighbours' rows of it, so the
+        // cluster waits for every CTA's part
+        const int ns = sym_compact_slots(c.g);
+        for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
+            if (p < c.g.n) {
+                sym_compact_fold_row(c.g, c.A64, c.ld, c.dinv, c.Aw, p);
+            } else {
+                for (int t = 0; t < ns; t++) c.Aw[(long long)t * c.ld + p] = T(0);
+            }
+        }
+        cl_sync();
     } else {
         for (long long p = c.lo + threadIdx.x; p < hi; p += blockDim.x) {
             if (p < c.g.n) {
@@ -903,7 +1012,7 @@ __device__ __noinline__ void assemble_system(Ctx<T> &c, const DevSystem &sys) {
         }
     }
     __syncthreads();
-    c.bytes += (unsigned long long)c.g.n * (8 * (c.g.nst + 3) + sizeof(T) * c.g.nst) +
+    c.bytes += (unsigned long long)c.g.n * (8 * (c.g.nst + 3) + sizeof(T) * op_slots(c)) +
                (unsigned long long)nn * 16 + csr_index_bytes(c) * 2;
 }
 
@@ -948,7 +1057,7 @@ __device__ __noinline__ void refresh_recycle(Ctx<T> &c) {
         if (p < c.g.n) {
             for (int s = 0; s < c.g.nst; s++) {
                 const long long q = nb_index(c.g, p, s);
-                const T a = c.Aw[(long long)s * c.ld + p];
+                const T a = c.symc ? sym_folded(c.g, c.Aw, c.ld, p, s) : c.Aw[(long long)s * c.ld + p];
 #pragma unroll
                 for (int b = 0; b < KMAX; b++)
                     if (b < kc) acc[b] += a * __ldcg(c.col(COL_U0 + b) + q);
@@ -960,7 +1069,7 @@ __device__ __noinline__ void refresh_recycle(Ctx<T> &c) {
     }
     __syncthreads();
     c.matvecs += kc;
-    c.bytes += (unsigned long long)c.g.n * sizeof(T) * (c.g.nst + 2 * kc) + csr_index_bytes(c);
+    c.bytes += (unsigned long long)c.g.n * sizeof(T) * (op_slots(c) + 2 * kc) + csr_index_bytes(c);
     double *G = c.D(c.P.o_F);
     double *R = c.D(c.P.o_Z);
     double *Ri = c.D(c.P.o_Z) + kc * kc;
@@ -1540,6 +1649,7 @@ __device__ void solve_system(Ctx<T> &c, const ChainArgs &a, int sysidx, bool war
     c.g = (sys.fmt == SKR_FMT_CSR) ? make_csr_geom(sys.nx, sys.csr_w, c.cols, c.ld)
                                    : make_geom(sys.fmt, sys.nx, sys.ny, sys.nz);
     c.pc_bs = sweep_block_rows(c.precond, c.g.n, c.pc_blocks);
+    c.symc = sym_compact_form(sys.fmt, c.precond, (int)sizeof(T), c.g) ? 1 : 0;
     const long long chunk = (((c.g.n + c.cs - 1) / c.cs) + 7) / 8 * 8;
     c.lo = (long long)c.rank * chunk;
     c.cnt = chunk;

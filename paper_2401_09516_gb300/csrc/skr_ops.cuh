@@ -87,6 +87,19 @@ __global__ void apply_kernel(Geom g, const T *Aw, long long ld, const T *v, doub
         y[p] = (double)stencil_apply_row(g, Aw, ld, v, T(1), p);
 }
 
+// the compact symmetric form (sym_compact_form) for the stand-alone operator entry point
+__global__ void sym_fold_kernel(Geom g, const double *A, long long ld, const double *dinv, float *Aw) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n;
+         p += (long long)gridDim.x * blockDim.x)
+        sym_compact_fold_row(g, A, ld, dinv, Aw, p);
+}
+
+__global__ void sym_apply_kernel(Geom g, const float *Aw, long long ld, const float *v, double *y) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n;
+         p += (long long)gridDim.x * blockDim.x)
+        y[p] = (double)sym_apply_row(g, Aw, ld, v, 1.0f, p);
+}
+
 // red-black ILU(0) / SSOR for the stand-alone operator entry point
 __global__ void ilu_pivot_kernel(Geom g, const double *A, long long ld, double *inv, int pc, long long bs) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.n;

@@ -250,6 +250,62 @@ __device__ __forceinline__ T stencil_apply_row(const Geom &g, const T *Aw, long 
     return acc;
 }
 
+// ---------------------------------------------------------------- compact symmetric operator
+//
+// The symmetric grid formats (Darcy 2D/3D, Helmholtz, Poisson: a_pq = a_qp,
+// couplings that leave the grid zero) under right Jacobi in FP32 keep the
+// folded operator A D^-1 in 1 + (nst - 1) / 2 arrays instead of nst: slot 0
+// holds D^-1, slot t (t = 1 .. (nst - 1) / 2) the coupling a_{p, p + off[2t]}
+// of row p to its neighbour on the plus side of axis pair t.  Row p's
+// coupling to its minus-side neighbour q = p - off[2t] is slot t of row q,
+// and the diagonal of A D^-1 is one (the FP32 rounding of d * (1 / d) is
+// exactly 1).  An operator pass then moves 5 n values in 2D (D^-1, two
+// coupling arrays, the source and the result) and 6 n in 3D.  Used when the
+// fastest grid extent is a multiple of 4 (one float4 of rows per thread).
+__host__ __device__ inline bool sym_compact_form(int fmt, int precond, int wbytes, const Geom &g) {
+    const int last = (g.nst == 5) ? g.ny : g.nz;
+    return wbytes == 4 && precond == SKR_PC_JACOBI && g.cols == nullptr &&
+           (fmt == SKR_FMT_DARCY2D || fmt == SKR_FMT_DARCY3D || fmt == SKR_FMT_HELMHOLTZ2D ||
+            fmt == SKR_FMT_POISSON2D) &&
+           last % 4 == 0;
+}
+
+// Arrays an operator pass reads in the compact form (D^-1 and the couplings).
+__host__ __device__ inline int sym_compact_slots(const Geom &g) { return 1 + (g.nst - 1) / 2; }
+
+// Compact form of row p from the FP64 rows A (slots of stride ld) and D^-1.
+template <typename T>
+__device__ __forceinline__ void sym_compact_fold_row(const Geom &g, const double *A, long long ld,
+                                                     const double *dinv, T *Aw, long long p) {
+    Aw[p] = (T)dinv[p];
+    for (int t = 1; t <= (g.nst - 1) / 2; t++) Aw[(long long)t * ld + p] = (T)A[(long long)(2 * t) * ld + p];
+}
+
+// Entry of A D^-1 in row p, stencil slot s, from the compact form (zero for
+// a neighbour outside [0, n)).  Neighbour rows may belong to other CTAs:
+// read through L2.
+template <typename T>
+__device__ __forceinline__ T sym_folded(const Geom &g, const T *Aw, long long ld, long long p, int s) {
+    if (s == 0) return T(1);
+    const long long q = p + g.off[s];
+    if (q < 0 || q >= g.n) return T(0);
+    const int t = (s + 1) >> 1;
+    const T a = __ldcg(Aw + (long long)t * ld + ((s & 1) ? q : p));   // odd slots: minus side
+    return a * __ldcg(Aw + q);
+}
+
+// y_p = scale * (A D^-1 src)_p from the compact form.
+template <typename T>
+__device__ __forceinline__ T sym_apply_row(const Geom &g, const T *Aw, long long ld, const T *src, T scale,
+                                           long long p) {
+    T acc = scale * __ldcg(src + p);
+    for (int s = 1; s < g.nst; s++) {
+        const long long q = p + g.off[s];
+        if (q >= 0 && q < g.n) acc += sym_folded(g, Aw, ld, p, s) * (scale * __ldcg(src + q));
+    }
+    return acc;
+}
+
 // r_p = b_p - sum_s A[s][p] * x[nb_s(p)]  (FP64 true residual).
 __device__ __forceinline__ double residual_row(const Geom &g, const double *A, long long ld,
                                                const double *b, const double *x, long long p) {

@@ -207,6 +207,55 @@ def test_apply_operator(skr, pc):
     assert np.abs(y32 - want).max() <= 5e-6 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("kind", ["darcy2d", "darcy3d", "helmholtz2d", "poisson2d"])
+def test_apply_operator_compact_symmetric(skr, kind):
+    """Symmetric grids whose fastest extent is a multiple of 4, right Jacobi, FP32:
+    the operator is kept as D^-1 plus one coupling array per axis (each
+    coupling stored once, on its plus side); A M^-1 v must still be the
+    oracle's to FP32 rounding, on every boundary row."""
+    rng = np.random.default_rng(23)
+    if kind == "darcy2d":
+        loga = rng.standard_normal((13 + 2, 32 + 2))
+        A, _ = assembly.darcy2d(loga)
+        sysd = skr.darcy2d(_dev(loga))
+    elif kind == "darcy3d":
+        loga = rng.standard_normal((5 + 2, 6 + 2, 8 + 2))
+        A, _ = assembly.darcy3d(loga)
+        sysd = skr.darcy3d(_dev(loga))
+    elif kind == "helmholtz2d":
+        k = rng.uniform(1.0, 12.0, size=(9, 16))
+        A, _ = assembly.helmholtz2d(k)
+        sysd = skr.helmholtz2d(_dev(k))
+    else:
+        f = rng.standard_normal((7, 12))
+        g = (rng.standard_normal(12), rng.standard_normal(12), rng.standard_normal(7), rng.standard_normal(7))
+        A, _ = assembly.poisson2d_dirichlet(f, *g)
+        sysd = _poisson_system(skr, f, g)
+    M = oprecond.RightPreconditioner(A, "jacobi")
+    for trial in range(3):
+        v = rng.standard_normal(A.shape[0])
+        want = A @ M.apply(v)
+        y32 = skr.skr_apply(sysd, _dev(v), precond="jacobi", precision="mixed").cpu().numpy()
+        assert np.abs(y32 - want).max() <= 5e-6 * np.abs(want).max(), trial
+
+
+@pytest.mark.parametrize("cs", [1, 3, 7])
+def test_mixed_compact_operator_across_cluster_chunks(skr, cs):
+    """Mixed-form solves on the compact symmetric operator with clusters whose
+    row chunks start mid grid row: every CTA reads its neighbours' D^-1 and
+    couplings at the chunk edges (2D 36 x 20, 3D 6 x 5 x 8)."""
+    L = darcy2d_sequence(20, 4, 0.2, seed=61)
+    L2 = [np.ascontiguousarray(np.pad(l, ((8, 8), (0, 0)), mode="reflect")) for l in L]   # 36 x 20 interior
+    L3 = [np.random.default_rng(62 + i).standard_normal((6 + 2, 5 + 2, 8 + 2)) * 0.5 for i in range(3)]
+    opt = skr.skr_options_default(m=20, k=6, tol=1e-9, precond="jacobi", precision="mixed", cluster_size=cs)
+    for fields, make, asm in ((L2, skr.darcy2d, assembly.darcy2d), (L3, skr.darcy3d, assembly.darcy3d)):
+        xs, res = skr.skr_solve_sequence([make(_dev(l)) for l in fields], options=opt)
+        for i, l in enumerate(fields):
+            A, b = asm(l)
+            assert res[i]["flag"] == 0, res[i]
+            _check_solution(xs[i], A, b, 1e-9, spla_solve(A, b), 1e-6)
+
+
 # ------------------------------------------------------------------ solves
 
 def _check_solution(x_gpu, A, b, tol_res, x_ref=None, tol_err=None):

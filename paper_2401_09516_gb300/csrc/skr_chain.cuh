@@ -1612,7 +1612,7 @@ __device__ __noinline__ double recycle_delta(Ctx<T> &c, int kc_in) {
     __syncthreads();
     double *Z = c.D(c.P.o_Z), *wr = c.D(c.P.o_wr), *wi = c.D(c.P.o_wi);
     hessenberg_reduce<double>(S, lds, Z, kq, kq, c.D(c.P.o_vscr), c.D(c.P.o_sc));
-    const int fail = schur_form<double>(S, lds, Z, kq, kq, wr, wi, c.ints() + 8);
+    const int fail = schur_form<double>(S, lds, Z, kq, kq, wr, wi, c.ints() + 8, c.D(c.P.o_vscr));
     double lmax = 0.0;
     for (int i = 0; i < kq; i++) lmax = fmax(lmax, wr[i]);   // symmetric: real eigenvalues
     __syncthreads();

@@ -465,20 +465,29 @@ __device__ __forceinline__ void named_bar(int id, int nthreads) {
 
 // francis_schur for FP64 on four warps, one per SM sub-partition: an FP64
 // warp instruction occupies a sub-partition's FP64 pipe for many cycles, so
-// the serial bulge chase is bound by the FP64 instructions one warp issues
-// per bulge step.  Every warp computes the reflector of a step from the same
-// shared values (identical results, no broadcast); warps 0-2 split the row
-// update of H and then, after a barrier among them, its column update; warp
-// 3 applies the step's reflector to the Schur vectors Z meanwhile.  A barrier
-// of all four ends each step.  The deflation scans, shifts and 2x2 blocks
-// are computed by every warp alike; their few writes are warp 0's.  Same
-// arithmetic per element as francis_schur, hence the same results.
+// the serial bulge chase is bound by the chain of dependent FP64
+// instructions per bulge step, the reflector above all.  The chase runs with
+// a one-step lookahead, in two phases per step kk separated by barriers of
+// all four warps:
+//   A: warp 0 computes the reflector of step kk from (x, y, z); warps 1-3
+//      apply the reflector of step kk - 1 to everything outside its critical
+//      block (rows kk-1..kk+1 right of column kk+2, columns kk-1..kk+1 down
+//      to row kk-1, and the Schur vectors Z);
+//   B: warp 0 applies the reflector of step kk to its critical block (rows
+//      kk..kk+2 from column c0 to kk+3, then columns kk..kk+2 from row kk+1
+//      to kk+3), which holds every entry the next reflector reads, takes the
+//      next (x, y, z) from it and publishes the reflector in `pub`.
+// So the reflector chain no longer waits for the long row, column and Z
+// updates.  Every entry receives the same updates, in the same order and
+// with the same arithmetic, as in francis_schur, hence the same results.
+// The deflation scans, shifts and 2x2 blocks are computed by every warp
+// alike; their few writes are warp 0's.
 __device__ inline int francis_schur_4w(double *H, int ldh, double *Z, int ldz, int n, double *wr, double *wi,
-                                       int *isc) {
+                                       int *isc, double *pub) {
     typedef double R;
     constexpr R EPS = R(2.220446049250313e-16);
     const unsigned FULL = 0xffffffffu;
-    constexpr int BAR_ALL = 1, BAR_H = 2;
+    constexpr int BAR_ALL = 1;
     if (warp_id() < 4) {
         const int lane = lane_id(), w = warp_id();
         int hi = n - 1, its = 0, total = 0, fail = 0;
@@ -612,57 +621,99 @@ __device__ inline int francis_schur_4w(double *H, int ldh, double *Z, int ldz, i
                 z = h10 * h21;
             }
             named_bar(BAR_ALL, 128);   // every warp has read the shift inputs
-            for (int kk = l; kk <= hi - 1; kk++) {
-                const int nr = (kk == hi - 1) ? 2 : 3;
-                R tau, v1, v2;
-                house3(x, y, nr == 3 ? z : R(0), tau, v1, v2);
-                if (tau != R(0)) {
-                    if (w == 3) {
-                        // the Schur vectors: independent of H
-                        for (int i = lane; i < n; i += 32) {
-                            R tt = M_(Z, ldz, i, kk) + v1 * M_(Z, ldz, i, kk + 1);
-                            if (nr == 3) tt += v2 * M_(Z, ldz, i, kk + 2);
-                            tt *= tau;
-                            M_(Z, ldz, i, kk) -= tt;
-                            M_(Z, ldz, i, kk + 1) -= tt * v1;
-                            if (nr == 3) M_(Z, ldz, i, kk + 2) -= tt * v2;
-                        }
-                    } else {
-                        // rows kk..kk+2 of H from column c0 on, columns dealt to warps 0-2
-                        const int c0 = (kk > l) ? kk - 1 : l;
-                        for (int j = c0 + w + 3 * lane; j < n; j += 96) {
-                            R tt = M_(H, ldh, kk, j) + v1 * M_(H, ldh, kk + 1, j);
-                            if (nr == 3) tt += v2 * M_(H, ldh, kk + 2, j);
-                            tt *= tau;
-                            M_(H, ldh, kk, j) -= tt;
-                            M_(H, ldh, kk + 1, j) -= tt * v1;
-                            if (nr == 3) M_(H, ldh, kk + 2, j) -= tt * v2;
-                        }
-                        named_bar(BAR_H, 96);
-                        // columns kk..kk+2 of H down to row rmax, rows dealt to warps 0-2
-                        const int rmax = min(kk + 3, hi);
-                        for (int i = w + 3 * lane; i <= rmax; i += 96) {
-                            R tt = M_(H, ldh, i, kk) + v1 * M_(H, ldh, i, kk + 1);
-                            if (nr == 3) tt += v2 * M_(H, ldh, i, kk + 2);
-                            tt *= tau;
-                            M_(H, ldh, i, kk) -= tt;
-                            M_(H, ldh, i, kk + 1) -= tt * v1;
-                            if (nr == 3) M_(H, ldh, i, kk + 2) -= tt * v2;
+            R tau = R(0), v1 = R(0), v2 = R(0);
+            for (int kk = l; kk <= hi; kk++) {
+                // phase A
+                if (w == 0) {
+                    if (kk <= hi - 1) house3(x, y, (kk == hi - 1) ? R(0) : z, tau, v1, v2);
+                } else if (kk > l) {
+                    // step pk = kk - 1 outside its critical block
+                    const int pk = kk - 1;
+                    const bool three = pk < hi - 1;
+                    const R ptau = pub[0], pv1 = pub[1], pv2 = pub[2];
+                    if (ptau != R(0)) {
+                        const int cend = min(pk + 3, n - 1);
+                        const int nzr = n, ncol = n - 1 - cend, nrow = pk;
+                        for (int it = (w - 1) * 32 + lane; it < nzr + ncol + nrow; it += 96) {
+                            if (it < nzr) {
+                                // row it of the Schur vectors
+                                const int i = it;
+                                R tt = M_(Z, ldz, i, pk) + pv1 * M_(Z, ldz, i, pk + 1);
+                                if (three) tt += pv2 * M_(Z, ldz, i, pk + 2);
+                                tt *= ptau;
+                                M_(Z, ldz, i, pk) -= tt;
+                                M_(Z, ldz, i, pk + 1) -= tt * pv1;
+                                if (three) M_(Z, ldz, i, pk + 2) -= tt * pv2;
+                            } else if (it < nzr + ncol) {
+                                // column j of rows pk..pk+2, right of the critical block
+                                const int j = cend + 1 + (it - nzr);
+                                R tt = M_(H, ldh, pk, j) + pv1 * M_(H, ldh, pk + 1, j);
+                                if (three) tt += pv2 * M_(H, ldh, pk + 2, j);
+                                tt *= ptau;
+                                M_(H, ldh, pk, j) -= tt;
+                                M_(H, ldh, pk + 1, j) -= tt * pv1;
+                                if (three) M_(H, ldh, pk + 2, j) -= tt * pv2;
+                            } else {
+                                // row i < pk of columns pk..pk+2, above the critical block
+                                const int i = it - nzr - ncol;
+                                R tt = M_(H, ldh, i, pk) + pv1 * M_(H, ldh, i, pk + 1);
+                                if (three) tt += pv2 * M_(H, ldh, i, pk + 2);
+                                tt *= ptau;
+                                M_(H, ldh, i, pk) -= tt;
+                                M_(H, ldh, i, pk + 1) -= tt * pv1;
+                                if (three) M_(H, ldh, i, pk + 2) -= tt * pv2;
+                            }
                         }
                     }
                 }
-                named_bar(BAR_ALL, 128);   // H of this step complete
-                if (kk < hi - 1) {
-                    x = M_(H, ldh, kk + 1, kk);
-                    y = M_(H, ldh, kk + 2, kk);
-                    z = (kk < hi - 2) ? M_(H, ldh, kk + 3, kk) : R(0);
+                named_bar(BAR_ALL, 128);   // reflector kk ready; step kk - 1 complete
+                if (kk == hi) break;
+                // phase B: the critical block of step kk (warp 0)
+                if (w == 0) {
+                    const bool three = kk < hi - 1;
+                    if (tau != R(0)) {
+                        const int c0 = (kk > l) ? kk - 1 : l;
+                        const int cend = min(kk + 3, n - 1);
+                        const int j = c0 + lane;
+                        if (j <= cend) {
+                            R tt = M_(H, ldh, kk, j) + v1 * M_(H, ldh, kk + 1, j);
+                            if (three) tt += v2 * M_(H, ldh, kk + 2, j);
+                            tt *= tau;
+                            M_(H, ldh, kk, j) -= tt;
+                            M_(H, ldh, kk + 1, j) -= tt * v1;
+                            if (three) M_(H, ldh, kk + 2, j) -= tt * v2;
+                        }
+                        __syncwarp();
+                        const int rmax = min(kk + 3, hi);
+                        const int i = kk + lane;
+                        if (i <= rmax) {
+                            R tt = M_(H, ldh, i, kk) + v1 * M_(H, ldh, i, kk + 1);
+                            if (three) tt += v2 * M_(H, ldh, i, kk + 2);
+                            tt *= tau;
+                            M_(H, ldh, i, kk) -= tt;
+                            M_(H, ldh, i, kk + 1) -= tt * v1;
+                            if (three) M_(H, ldh, i, kk + 2) -= tt * v2;
+                        }
+                        __syncwarp();
+                    }
+                    if (kk < hi - 1) {
+                        x = M_(H, ldh, kk + 1, kk);
+                        y = M_(H, ldh, kk + 2, kk);
+                        z = (kk < hi - 2) ? M_(H, ldh, kk + 3, kk) : R(0);
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (kk > l) {
+                            // the bulge entries of column kk - 1: nothing reads them again in this sweep
+                            M_(H, ldh, kk + 1, kk - 1) = R(0);
+                            if (three) M_(H, ldh, kk + 2, kk - 1) = R(0);
+                        }
+                        pub[0] = tau;
+                        pub[1] = v1;
+                        pub[2] = v2;
+                    }
                 }
-                if (w == 0 && lane == 0 && kk > l) {
-                    // the bulge entries of column kk - 1: no warp reads them again in this sweep
-                    M_(H, ldh, kk + 1, kk - 1) = R(0);
-                    if (nr == 3) M_(H, ldh, kk + 2, kk - 1) = R(0);
-                }
-                named_bar(BAR_ALL, 128);   // every warp has read x, y, z
+                named_bar(BAR_ALL, 128);   // critical block of step kk and its reflector published
             }
         }
         if (w == 0 && lane == 0) isc[0] = fail;
@@ -676,9 +727,9 @@ __device__ inline int francis_schur_4w(double *H, int ldh, double *Z, int ldz, i
 // FP64 Schur forms run on four warps, FP32 ones on one (its instructions are
 // cheap enough that barriers between warps would cost more than they save).
 template <typename R>
-__device__ inline int schur_form(R *H, int ldh, R *Z, int ldz, int n, R *wr, R *wi, int *isc) {
+__device__ inline int schur_form(R *H, int ldh, R *Z, int ldz, int n, R *wr, R *wi, int *isc, R *pub) {
     if constexpr (sizeof(R) == 8)
-        return francis_schur_4w(H, ldh, Z, ldz, n, wr, wi, isc);
+        return francis_schur_4w(H, ldh, Z, ldz, n, wr, wi, isc, pub);
     else
         return francis_schur(H, ldh, Z, ldz, n, wr, wi, isc);
 }
@@ -901,7 +952,7 @@ __device__ __noinline__ int harmonic_select(const double *M64, int ld64, int n, 
         hessenberg_reduce(Mr, ldm, Zr, n, n, vscr, scr);
     }
     if (marks && threadIdx.x == 0) marks[2] = global_ns();
-    const int fail = schur_form(Mr, ldm, Zr, n, n, wr, wi, isc);
+    const int fail = schur_form(Mr, ldm, Zr, n, n, wr, wi, isc, vscr);   // vscr: free during the Schur form
     if (marks && threadIdx.x == 0) marks[0] = global_ns();
     if (fail) return -1;
     int *rank = isc + 8;
